@@ -1,0 +1,340 @@
+"""Pins of the FP64 reference against facts fixed outside it: published known answers,
+closed forms, invariants, limits and brute force. A plausible slip in the reference
+(a dropped factor, a swapped operand, a wrong sign) fails at least one of these."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special, stats
+
+from conftest import read_golden
+from oracle import kinetics, sbs
+from paper_2509_03313_gb300 import workloads as W
+
+
+# ---------------------------------------------------------------- random numbers
+def test_philox_known_answers():
+    for row in read_golden("philox4x32_10_kat.txt"):
+        v = [int(x, 16) for x in row]
+        out = sbs.philox4x32_10(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_uniform_maps_extremes():
+    # (0, 1] and [0, 1) from the top 53 bits of a 64-bit word pair.
+    assert sbs.uniform_open0(0, 0) == math.ldexp(1.0, -53)
+    assert sbs.uniform_open0(0xFFFFFFFF, 0xFFFFFFFF) == 1.0
+    assert sbs.uniform_closed0(0, 0) == 0.0
+    assert sbs.uniform_closed0(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - math.ldexp(1.0, -53)
+    # The low 11 bits are dropped.
+    assert sbs.uniform_closed0(0, 0x7FF) == 0.0
+    assert sbs.uniform_closed0(0, 0x800) == math.ldexp(1.0, -53)
+
+
+def test_gaussians_are_standard_normal():
+    key = sbs.philox_key(12345, 3)
+    g = sbs.gaussians(np.arange(200_000), 7, key)
+    for a in range(3):
+        x = g[:, a]
+        assert abs(x.mean()) < 5 / math.sqrt(x.size)
+        assert abs(x.var() - 1.0) < 5 * math.sqrt(2.0 / x.size)
+        assert stats.kstest(x, "norm").pvalue > 1e-3
+    # Independent axes and independent steps.
+    assert abs(np.corrcoef(g[:, 0], g[:, 1])[0, 1]) < 0.02
+    assert abs(np.corrcoef(g[:, 0], g[:, 2])[0, 1]) < 0.02
+    g2 = sbs.gaussians(np.arange(200_000), 8, key)
+    assert abs(np.corrcoef(g[:, 0], g2[:, 0])[0, 1]) < 0.02
+
+
+def test_acceptance_uniform_is_uniform_and_symmetric_in_keying():
+    key = sbs.philox_key(99, 0)
+    u = sbs.acceptance_uniform(np.arange(100_000), np.arange(100_000) + 5, 3, key)
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    assert u.min() >= 0.0 and u.max() < 1.0
+
+
+# ---------------------------------------------------------------- Eq. 1 and Eq. 2
+def test_wrap_eq1_cases():
+    L = 10.0
+    x = np.array([4.999, 5.0, -5.0, -5.0001, 0.0, 15.0, -15.0, 27.5, -27.5, 5.0 + 1e-12])
+    y = sbs.wrap(x, L)
+    assert np.all(y >= -5.0) and np.all(y < 5.0)
+    np.testing.assert_allclose(y, [4.999, -5.0, -5.0, 4.9999, 0.0, -5.0, -5.0, -2.5, 2.5,
+                                   -5.0 + 1e-12], rtol=0, atol=1e-12)
+
+
+def test_minimum_image_eq2_cases():
+    L = 10.0
+    dx = np.array([4.9, 5.0, -5.0, -5.1, 9.0, -9.0, 0.0])
+    np.testing.assert_allclose(sbs.minimum_image(dx, L), [4.9, -5.0, -5.0, 4.9, -1.0, 1.0, 0.0],
+                               atol=1e-12)
+
+
+# ---------------------------------------------------------------- P2: free diffusion
+def test_msd_equals_6Dt_per_species():
+    L = 1000.0
+    n_per = 4000
+    wl_types = np.repeat(np.arange(7), n_per).astype(np.int32)
+    rng = np.random.default_rng(5)
+    xyz = rng.uniform(-L / 2, L / 2, size=(wl_types.size, 3))
+    o = sbs.SBSOracle(W.D_NM2_S, [], L, seed=17, dt_min=2e-9, dt_max=2e-9, record=False)
+    o.inject(wl_types, xyz, np.zeros(wl_types.size))
+    # All arrive at t = 0, so ids follow the input order.
+    ids0, p0 = np.arange(wl_types.size), xyz
+    disp = np.zeros_like(p0)
+    prev = p0
+    n_steps = 25
+    for _ in range(n_steps):
+        o.step_once(math.inf)
+        _, _, p = o.state()
+        disp += sbs.minimum_image(p - prev, L)
+        prev = p
+    t = n_steps * 2e-9
+    for ty in range(7):
+        m = wl_types[ids0] == ty
+        ratio = (disp[m] ** 2).sum(axis=1).mean() / (6.0 * W.D_NM2_S[ty] * t)
+        assert abs(ratio - 1.0) < 4 * 0.8165 / math.sqrt(n_per), (ty, ratio)
+        # Per axis variance 2 D t.
+        for a in range(3):
+            va = disp[m, a].var() / (2.0 * W.D_NM2_S[ty] * t)
+            assert abs(va - 1.0) < 5 * math.sqrt(2.0 / n_per)
+
+
+def test_zero_dose_and_inert_species():
+    o = sbs.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, 500.0, seed=1)
+    assert o.run_until(5e-9) == 5
+    assert o.species_steps == 0 and o.events_total.sum() == 0
+    # Only H2: nothing reacts, counts are constant.
+    rng = np.random.default_rng(2)
+    o = sbs.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, 500.0, seed=1)
+    o.inject(np.full(300, W.H2), rng.uniform(-250, 250, (300, 3)), np.zeros(300))
+    o.run_until(20e-9)
+    assert o.events_total.sum() == 0
+    assert o.counts()[W.H2] == 300
+
+
+# ---------------------------------------------------------------- time-step policy
+def test_log_dt_schedule_is_a_geometric_series():
+    g = W.LOG_GROWTH_20_PER_DECADE
+    o = sbs.SBSOracle(W.D_NM2_S, [], 5000.0, seed=0, dt_min=1e-12, dt_max=1.0, dt_growth=g)
+    o.inject([0], [[0.0, 0.0, 0.0]], [0.0])
+    o.run_until(1e-6)
+    steps = o.step_log
+    assert steps[-1][1] + steps[-1][2] == pytest.approx(1e-6, rel=1e-15)
+    for k, s in enumerate(steps[:-1]):
+        # t_k = dt_min (g^k - 1) / (g - 1), dt_k = dt_min g^k.
+        assert s[1] == pytest.approx(1e-12 * (g ** k - 1.0) / (g - 1.0), rel=1e-9)
+        assert s[2] == pytest.approx(1e-12 * g ** k, rel=1e-9)
+    # 20 steps per decade: about 20 * log10(1e-6 (g - 1) / 1e-12) steps.
+    assert abs(len(steps) - 20 * math.log10(1e6 * (g - 1) + 1)) <= 2
+
+
+def test_release_rounds_arrivals_up_and_resets_dt():
+    o = sbs.SBSOracle(W.D_NM2_S, [], 1000.0, seed=0, dt_min=1e-9, dt_max=4e-9, dt_growth=2.0)
+    o.inject([0, 1, 2], np.zeros((3, 3)), [0.0, 2.5e-9, 2.5e-9])
+    o.inject([3], np.zeros((1, 3)), [1.0e-9])
+    o.run_until(10e-9)
+    log = o.step_log
+    # Step 0 at t=0 releases one species; dt 1, then 2 (t=1 ns releases id 1, reset to 1),
+    # t=2 ns: dt 2 -> t=4 ns releases the two 2.5 ns species, reset.
+    assert [s[3] for s in log[:4]] == [1, 2, 2, 4]
+    assert [s[2] for s in log[:4]] == [1e-9, 1e-9, 2e-9, 1e-9]
+    ids, types, _ = o.state()
+    # ids by (arrival, caller order): 0 -> type 0, 1 -> type 3, 2 -> type 1, 3 -> type 2.
+    assert list(types[np.argsort(ids)]) == [0, 3, 1, 2]
+
+
+# ---------------------------------------------------------------- P5: brute force
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_pair_query_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    L = 100.0
+    pos = rng.uniform(-L / 2, L / 2, size=(500, 3))
+    pos[:20, 0] = -L / 2 + rng.uniform(0, 0.5, 20)   # crowd both faces
+    pos[20:40, 0] = L / 2 - rng.uniform(1e-9, 0.5, 20)
+    for r in (3.0, 9.5, 30.0):
+        a = {tuple(p) for p in sbs.all_pairs_within(pos, L, r)}
+        b = {tuple(p) for p in sbs.all_pairs_within_bruteforce(pos, L, r)}
+        assert a == b
+
+
+def _locally_dominant(id_lo, id_hi, d1sq):
+    """Independent algorithm: repeatedly commit every pair that is the smallest
+    remaining pair of both its species."""
+    keyed = {i: (d1sq[i], id_lo[i], id_hi[i]) for i in range(len(d1sq))}
+    alive = set(keyed)
+    kept = []
+    while alive:
+        best = {}
+        for i in alive:
+            for s in (id_lo[i], id_hi[i]):
+                if s not in best or keyed[i] < keyed[best[s]]:
+                    best[s] = i
+        chosen = [i for i in alive if best[id_lo[i]] == i and best[id_hi[i]] == i]
+        assert chosen
+        kept.extend(chosen)
+        used = {id_lo[i] for i in chosen} | {id_hi[i] for i in chosen}
+        alive = {i for i in alive if id_lo[i] not in used and id_hi[i] not in used}
+    return sorted(kept)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_greedy_matching_equals_locally_dominant_rounds(seed):
+    rng = np.random.default_rng(seed)
+    n_sp, n_c = 40, 120
+    a = rng.integers(0, n_sp, n_c)
+    b = rng.integers(0, n_sp, n_c)
+    m = a != b
+    lo, hi = np.minimum(a, b)[m], np.maximum(a, b)[m]
+    _, u = np.unique(np.stack([lo, hi], 1), axis=0, return_index=True)
+    lo, hi = lo[u], hi[u]
+    d = rng.integers(0, 5, lo.size).astype(np.float64)  # many exact ties
+    got = sorted(sbs.greedy_matching(lo, hi, d).tolist())
+    assert got == _locally_dominant(lo, hi, d)
+
+
+# ---------------------------------------------------------------- P1: conservation
+def test_charge_and_atoms_conserved_dense_mixture():
+    wl = W.uniform_2000(seed=3, L=200.0, n_steps=300)
+    o = sbs.from_workload(wl, seed=3)
+    c0 = o.p_types.copy()
+
+    def totals(counts, water):
+        return (int((counts * W.CHARGE).sum()), int((counts * W.N_H).sum()) + 2 * water,
+                int((counts * W.N_O).sum()) + water)
+
+    ref = totals(np.bincount(c0, minlength=7), 0)
+    for t in np.linspace(30e-9, 300e-9, 10):
+        o.run_until(t)
+        assert totals(o.counts(), o.water) == ref
+    assert o.events_total.sum() > 200
+    # Event log consistency: every reactant id appears at most once.
+    ev = o.events()
+    ids = np.concatenate([ev[:, 2], ev[:, 3]])
+    assert np.unique(ids).size == ids.size
+
+
+def test_products_sit_at_the_diffusion_weighted_encounter_point():
+    # e_aq + OH at 0.3 nm (inside R2 = 0.565 nm) with a negligible step: they react in
+    # step 0 and the OH- sits nearer the slower OH, D_e / (D_e + D_OH) of the way.
+    L = 100.0
+    xe = np.array([1.0, 2.0, 3.0])
+    xoh = xe + np.array([0.3, 0.0, 0.0])
+    o = sbs.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, L, seed=4, dt_min=1e-26, dt_max=1e-26)
+    o.inject([W.E_AQ, W.OH], np.stack([xe, xoh]), [0.0, 0.0])
+    o.step_once(1.0)
+    ids, types, pos = o.state()
+    assert list(types) == [W.OHM] and list(ids) == [2]
+    frac = np.linalg.norm(pos[0] - xe) / 0.3
+    assert frac == pytest.approx(W.D_NM2_S[W.E_AQ] / (W.D_NM2_S[W.E_AQ] + W.D_NM2_S[W.OH]),
+                                 abs=1e-6)
+    # A self reaction puts its product at the midpoint, across a periodic face too.
+    o = sbs.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, L, seed=4, dt_min=1e-26, dt_max=1e-26)
+    o.inject([W.OH, W.OH], [[49.95, 0, 0], [-49.95, 0, 0]], [0.0, 0.0])
+    o.step_once(1.0)
+    _, types, pos = o.state()
+    assert list(types) == [W.H2O2]
+    assert abs(abs(pos[0, 0]) - 50.0) < 1e-6
+
+
+# ---------------------------------------------------------------- P6: first passage
+def _pairs_on_lattice(n_side, spacing, r0, seed):
+    rng = np.random.default_rng(seed)
+    g = (np.arange(n_side) - n_side / 2 + 0.25) * spacing
+    cx, cy, cz = np.meshgrid(g, g, g, indexing="ij")
+    c = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], 1)
+    v = rng.normal(size=c.shape)
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    a = c - 0.5 * r0 * v
+    b = c + 0.5 * r0 * v
+    return a, b, n_side * spacing
+
+
+@pytest.mark.parametrize("dt", [1e-12, 1e-11])
+def test_first_passage_probability_of_one_pair(dt):
+    """P(react by t | r0) = (R/r0) erfc((r0 - R) / sqrt(4 D_AB t)) (Eq. PDF0, read with
+    the standard sign) for isolated A + B pairs."""
+    D = np.array([9.3e9, 5.3e9])
+    rx = [(0, 1, 11.0e10, (), 0)]
+    R = sbs.reaction_radius(11.0e10, 14.6e9)
+    r0 = 1.6
+    a, b, L = _pairs_on_lattice(22, 60.0, r0, seed=int(dt * 1e13))
+    n = a.shape[0]
+    o = sbs.SBSOracle(D, rx, L, seed=77, dt_min=dt, dt_max=dt, record=False)
+    o.inject(np.r_[np.zeros(n), np.ones(n)].astype(int), np.r_[a, b], np.zeros(2 * n))
+    for t in (0.1e-9, 0.5e-9):
+        o.run_until(t)
+        p_sim = o.events_total[0] / n
+        p_exact = (R / r0) * special.erfc((r0 - R) / math.sqrt(4 * 14.6e9 * t))
+        sigma = math.sqrt(p_exact * (1 - p_exact) / n)
+        assert abs(p_sim - p_exact) < 3 * sigma + 0.03 * p_exact, (t, p_sim, p_exact)
+
+
+# ---------------------------------------------------------------- P3: Smoluchowski rate
+def _ode_counts(D, rx, counts0, L, times):
+    c0 = kinetics.molar(counts0, L)
+    c = kinetics.integrate(c0, times, D, rx, transient=True)
+    return c / kinetics.molar(1.0, L)
+
+
+@pytest.mark.parametrize("dt", [5e-12, 1e-10])
+def test_smoluchowski_rate_A_plus_B(dt):
+    D = np.array([9.3e9, 5.3e9])
+    rx = [(0, 1, 11.0e10, (), 0)]
+    n, L = 1500, 200.0
+    rng = np.random.default_rng(11)
+    o = sbs.SBSOracle(D, rx, L, seed=5, dt_min=dt, dt_max=dt, record=False)
+    o.inject(np.r_[np.zeros(n), np.ones(n)].astype(int), rng.uniform(-L / 2, L / 2, (2 * n, 3)),
+             np.zeros(2 * n))
+    times = np.array([2e-9, 6e-9, 12e-9])
+    ode = _ode_counts(D, rx, [n, n], L, times)
+    for t, ref in zip(times, ode):
+        o.run_until(t)
+        got = o.counts()[0]
+        reacted_ref = n - ref[0]
+        sigma = math.sqrt(max(reacted_ref, 1.0))
+        assert abs((n - got) - reacted_ref) < 3 * sigma + 0.05 * reacted_ref, (t, got, ref[0])
+
+
+def test_smoluchowski_rate_self_reaction_uses_tabulated_2k():
+    # OH + OH -> H2O2 with the printed 2k: -d[OH]/dt = k_tab [OH]^2 (Eq. rateequation2).
+    D = np.array([2.2e9, 2.3e9])
+    rx = [(0, 0, 0.95e10, (1,), 0)]
+    n, L = 3000, 150.0
+    rng = np.random.default_rng(12)
+    o = sbs.SBSOracle(D, rx, L, seed=6, dt_min=2e-11, dt_max=2e-11, record=False)
+    o.inject(np.zeros(n, int), rng.uniform(-L / 2, L / 2, (n, 3)), np.zeros(n))
+    times = np.array([10e-9, 30e-9])
+    ode = _ode_counts(D, rx, [n, 0], L, times)
+    for t, ref in zip(times, ode):
+        o.run_until(t)
+        got = o.counts()
+        reacted_ref = n - ref[0]
+        sigma = math.sqrt(max(reacted_ref, 1.0))
+        assert abs((n - got[0]) - reacted_ref) < 3 * sigma + 0.05 * reacted_ref, (t, got, ref)
+        assert 2 * got[1] == n - got[0]
+
+
+# ---------------------------------------------------------------- P4: the ODE itself
+def test_ode_closed_forms():
+    k = 3.0e10
+    # A + B -> 0, [A]0 != [B]0: ln(([B]/[A]) ([A]0/[B]0)) = ([B]0 - [A]0) k t.
+    a0, b0 = 1e-4, 3e-4
+    ts = np.array([1e-7, 1e-6, 3e-6])
+    c = kinetics.integrate([a0, b0], ts, np.array([1e9, 1e9]), [(0, 1, k, (), 0)])
+    lhs = np.log((c[:, 1] / c[:, 0]) * (a0 / b0))
+    np.testing.assert_allclose(lhs, (b0 - a0) * k * ts, rtol=1e-6)
+    # A + A with printed 2k = k_tab: 1/[A] = 1/[A]0 + k_tab t.
+    c = kinetics.integrate([a0, 0.0], ts, np.array([1e9, 1e9]), [(0, 0, k, (1,), 0)])
+    np.testing.assert_allclose(1.0 / c[:, 0], 1.0 / a0 + k * ts, rtol=1e-6)
+    np.testing.assert_allclose(c[:, 1], 0.5 * (a0 - c[:, 0]), rtol=1e-6)
+
+
+def test_ode_full_table_conserves_and_agrees_across_schemes():
+    conc0 = kinetics.molar(W.MIX_COUNTS, 1000.0)
+    ts = np.logspace(-9, -3, 13)
+    y1 = kinetics.integrate(conc0, ts, W.D_NM2_S, W.WATER_REACTIONS, method="LSODA")
+    y2 = kinetics.integrate(conc0, ts, W.D_NM2_S, W.WATER_REACTIONS, method="Radau")
+    np.testing.assert_allclose(y1, y2, rtol=1e-5, atol=1e-15)
+    q = y1 @ W.CHARGE.astype(float)
+    np.testing.assert_allclose(q, q[0], rtol=0, atol=1e-12 * np.abs(conc0).sum())
