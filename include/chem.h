@@ -1,0 +1,213 @@
+/*
+ * chem.h - C ABI of the GB300 step-by-step (SBS) radiolysis chemistry library.
+ *
+ * The library advances radiolytic species (e_aq, OH, H, H3O+, OH-, H2, H2O2, or any
+ * table of up to 8 types and 16 reactions) through the non-homogeneous chemical stage
+ * of arxiv 2509.03313 Sec. 2.1: Brownian diffusion in a periodic cubic box (Eq. 1),
+ * pair search under the minimum-image convention (Eq. 2), diffusion-controlled
+ * reactions whose radii follow from the tabulated rate constants (Table 1, Table S2,
+ * Eq. kdiff1/kdiff2), and species injected pulse by pulse and carried across the
+ * intervals between pulses.
+ *
+ * Every step of that path runs in the library's own sm_103a kernels; the host only
+ * queues work on a CUDA stream and copies results back. There is no CPU fallback: on a
+ * machine without a usable GPU every call that needs one returns CHEM_ECUDA.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointer arguments are HOST pointers owned by the caller unless stated otherwise;
+ *    the library copies what it needs before returning and keeps no reference.
+ *  - A context owns all the device memory it allocates (through the caller's allocator
+ *    callbacks when given, cudaMalloc otherwise) and releases it in chem_destroy.
+ *  - No exception crosses the ABI. A non-OK status is sticky: every later call on the
+ *    context returns it again, and chem_last_error() explains it. The context can then
+ *    only be destroyed (chem_tally and chem_get_* still read the last completed step).
+ *  - One context is used by one host thread at a time.
+ *
+ * Units: lengths nm, times s, diffusion coefficients nm^2/s, rate constants
+ * L mol^-1 s^-1, energies eV.
+ */
+#ifndef CHEM_H
+#define CHEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chem_ctx chem_ctx; /* opaque */
+
+typedef enum chem_status {
+  CHEM_OK = 0,
+  CHEM_EINVAL = 1,    /* bad argument or configuration                              */
+  CHEM_ENOMEM = 2,    /* device or host allocation failed                           */
+  CHEM_ECAPACITY = 3, /* a capacity given in chem_config was exceeded on the device  */
+  CHEM_ECUDA = 4,     /* a CUDA runtime call failed (message in chem_last_error)     */
+  CHEM_ETIMEOUT = 5,  /* a bounded device-side wait ran out (sort look-back, grid
+                         barrier); the kernels returned instead of waiting further   */
+  CHEM_ESTATE = 6     /* call not valid in the context's current state               */
+} chem_status;
+
+enum { CHEM_FP64 = 0, CHEM_FP32_LOCAL = 1 };
+enum { CHEM_MAX_TYPES = 8, CHEM_MAX_RXN = 16, CHEM_MAX_PRODUCTS = 3 };
+
+/* One diffusion-controlled reaction A + B -> products (Table 1). */
+typedef struct chem_reaction {
+  int32_t a, b;       /* reactant species types; a == b is a self reaction            */
+  double k_tab;       /* rate constant as tabulated (L mol^-1 s^-1). For a self
+                         reaction this is the printed "2k" value: the library uses it
+                         directly in R = k_tab / (4 pi D_AB N_A), Eq. kdiff2.          */
+  int32_t n_prod;     /* 0..3                                                          */
+  int32_t prod[3];    /* product species types; all placed at the encounter point     */
+  int32_t water_delta;/* water molecules created (+) or consumed (-) per event        */
+} chem_reaction;
+
+/* Device allocator callbacks (optional). alloc returns device memory of at least
+ * `bytes` bytes aligned to 256 B, or NULL; free releases it. `user` is passed back. */
+typedef void* (*chem_alloc_fn)(size_t bytes, void* user);
+typedef void (*chem_free_fn)(void* ptr, size_t bytes, void* user);
+
+/* Configuration of one pulse train. */
+typedef struct chem_config {
+  int32_t n_types;             /* 1..8 species types                                   */
+  const double* D_nm2_s;       /* [n_types] diffusion coefficients (Table S2)          */
+  int32_t n_rxn;               /* 0..16 reactions; at most one per unordered type pair */
+  const chem_reaction* rxn;    /* [n_rxn]                                              */
+  double L_nm;                 /* side of the periodic box [-L/2, L/2)^3 (Eq. 1)       */
+  uint64_t seed;               /* Philox4x32-10 key = (seed lo, seed hi ^ train_id)    */
+  uint32_t train_id;
+  int32_t precision;           /* CHEM_FP64: positions, distances and random normals in
+                                  FP64, reproducing the FP64 reference step for step.
+                                  CHEM_FP32_LOCAL: positions held as FP32 offsets from
+                                  their hash cell's origin, FP32 normals and distances;
+                                  clock, schedule, reaction probabilities and tallies
+                                  stay FP64.                                           */
+  double dt_min_s;             /* first step and the step after every release         */
+  double dt_max_s;             /* largest step                                         */
+  double dt_growth;            /* per-step growth factor (1 = fixed step)              */
+  int32_t dt_reset_on_release; /* nonzero: restart at dt_min when species are released */
+  double cutoff_c;             /* pair cutoff R + c sqrt(2 D_AB dt); typically 3       */
+  double sbs_horizon_s;        /* >0: after this long without a release, jump by free
+                                  diffusion (no reactions) to the next arrival or end  */
+  int64_t capacity_species;    /* max species alive at once (incl. one step's products)*/
+  int64_t capacity_pending;    /* max species queued by inject and not yet released    */
+  int64_t capacity_candidates; /* max accepted reactive pairs in one step              */
+  int64_t capacity_event_log;  /* >0: keep up to this many events for chem_get_events  */
+  int64_t capacity_step_log;   /* >0: keep up to this many per-step records            */
+  int32_t cells_per_axis_max;  /* spatial-hash resolution limit; 0 = automatic         */
+  int32_t steps_per_launch;    /* steps per captured graph replay; 0 = automatic       */
+  void* cuda_stream;           /* cudaStream_t to run on; NULL = library-owned stream  */
+  chem_alloc_fn dev_alloc;     /* NULL = cudaMalloc / cudaFree                         */
+  chem_free_fn dev_free;
+  void* alloc_user;
+} chem_config;
+
+/* One reaction event (recorded when capacity_event_log > 0). */
+typedef struct chem_event {
+  uint32_t step;     /* step index of the train                                      */
+  int32_t rxn;       /* reaction index into chem_config.rxn                          */
+  uint32_t id_lo;    /* reactant ids, id_lo < id_hi                                   */
+  uint32_t id_hi;
+  uint32_t prod_id0; /* id of the first product; the others follow consecutively     */
+  int32_t n_prod;
+  uint32_t train;    /* train index within the context                               */
+  uint32_t reserved;
+} chem_event;
+
+/* Per-step record (recorded when capacity_step_log > 0). */
+typedef struct chem_step_record {
+  uint32_t step, train;
+  double t_start_s, dt_s;
+  int64_t n_live;     /* species that took this step (after the release)             */
+  int64_t n_events;   /* reactions committed in this step                            */
+  int64_t counts[8];  /* species per type after the step                              */
+} chem_step_record;
+
+/* ---- single pulse train ------------------------------------------------------------ */
+
+/* Validate cfg (EINVAL), compute every reaction radius R = k_tab / (4 pi D_AB N_A)
+ * (Eq. kdiff1; D_AB = D_a + D_b), check 2 R_cut <= 2L/3 at dt_min, and allocate all
+ * device buffers for the capacities given. On success *out is a new context at t = 0
+ * with no species. */
+chem_status chem_init(const chem_config* cfg, chem_ctx** out);
+
+/* Queue n species for release (Sec. 2.1: the products of each radiation event enter
+ * the SBS at their sampled arrival time). type[n] in [0, n_types), xyz[3n] absolute
+ * positions in [-L/2, L/2)^3 (host, row-major x,y,z), t_arrival[n] >= the current
+ * time (host, s). A species is released at the first step boundary at or after its
+ * arrival; ids are assigned at release in (arrival, call order, index) order.
+ * energy_eV is added to the deposited energy used for G-values at call time.
+ * Blocks until the copy to the device has completed. */
+chem_status chem_inject_pulse(chem_ctx* ctx, int64_t n, const int32_t* type, const double* xyz,
+                              const double* t_arrival, double energy_eV);
+
+/* Advance to t_end_s (the last step is trimmed to land on it). Each step: release
+ * arrived species, diffuse with periodic wrap (Eq. 1), rebuild the spatial hash, find
+ * reactive pairs within the cutoff under the minimum image (Eq. 2) and accept them with
+ * the Brownian-bridge probability, keep one reaction per species (closest pair first,
+ * lower ids break ties), write products and tallies, advance the FP64 clock.
+ * Blocks until the device has finished. */
+chem_status chem_run_until(chem_ctx* ctx, double t_end_s);
+
+/* Tallies of train 0 after the last completed step. Any output pointer may be NULL.
+ * counts[n_types]: live species; G_per_100eV[n_types]: counts * 100 / E_dep;
+ * events[n_rxn]: reactions so far; t_now: clock; species_steps: sum over steps of the
+ * species that took the step. */
+chem_status chem_tally(chem_ctx* ctx, int64_t* counts, double* G_per_100eV, int64_t* events,
+                       double* t_now, int64_t* species_steps);
+
+/* Live species of train 0 in device order: type[cap], id[cap], xyz[3*cap] (FP64
+ * absolute positions). *n receives the live count; EINVAL if it exceeds cap. */
+chem_status chem_get_state(chem_ctx* ctx, int64_t cap, int32_t* type, uint32_t* id, double* xyz,
+                           int64_t* n);
+
+/* Recorded events (all trains, in step order, within a step in (train, id_lo) order)
+ * and per-step records. *n receives the number copied; ECAPACITY (sticky) if the log
+ * overflowed on the device. */
+chem_status chem_get_events(chem_ctx* ctx, int64_t cap, chem_event* ev, int64_t* n);
+chem_status chem_get_step_log(chem_ctx* ctx, int64_t cap, chem_step_record* rec, int64_t* n);
+
+/* Return every train to t = 0 with no species, empty logs and zero tallies, keeping
+ * the allocations and captured graphs; seed replaces the seeds of all trains (train b
+ * gets seed + b for b > 0 unless chem_batch_reset is used). */
+chem_status chem_reset(chem_ctx* ctx, uint64_t seed);
+
+/* Human-readable description of the last error on ctx (never NULL). */
+const char* chem_last_error(const chem_ctx* ctx);
+
+/* Release everything ctx owns. NULL is ignored. */
+void chem_destroy(chem_ctx* ctx);
+
+/* ---- many independent pulse trains advanced together ------------------------------ */
+
+/* Like chem_init for n_trains trains. All trains share n_types, D, the reaction table
+ * and precision; each has its own box, seed, train_id, time-step policy, capacities
+ * and clock. Species of all trains live in one hash sorted by (train, cell); every
+ * step of every train runs in the same persistent launches. */
+chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx** out);
+chem_status chem_batch_inject(chem_ctx* ctx, int32_t train, int64_t n, const int32_t* type,
+                              const double* xyz, const double* t_arrival, double energy_eV);
+/* t_end_s[n_trains]: each train advances to its own end time. */
+chem_status chem_batch_run_until(chem_ctx* ctx, const double* t_end_s);
+chem_status chem_batch_tally(chem_ctx* ctx, int32_t train, int64_t* counts, double* G_per_100eV,
+                             int64_t* events, double* t_now, int64_t* species_steps);
+chem_status chem_batch_get_state(chem_ctx* ctx, int32_t train, int64_t cap, int32_t* type,
+                                 uint32_t* id, double* xyz, int64_t* n);
+/* seeds[n_trains] */
+chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds);
+int32_t chem_batch_size(const chem_ctx* ctx);
+
+/* Choose the steps per graph replay and the hash cell-size factor by timing short
+ * replays (state is saved and restored around the trials). budget_ms bounds the time
+ * spent. Reports the choice through chosen[2] = {steps_per_launch, cell_factor_x100}
+ * when chosen is not NULL. */
+chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen);
+
+/* Library version string. */
+const char* chem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHEM_H */

@@ -1,0 +1,767 @@
+// Host side of the C ABI declared in include/chem.h: validation, device allocation,
+// the pending-species queue, CUDA-graph capture of the step kernels and the run loop.
+// The host never computes a step: it only queues kernels and copies data.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "sbs_device.cuh"
+
+using namespace chem;
+
+namespace {
+
+constexpr double N_AVOGADRO = 6.02214076e23;
+constexpr double PI = 3.141592653589793;
+
+struct PendingHost {
+  std::vector<double> t, x, y, z;
+  std::vector<int32_t> type;
+  size_t size() const { return t.size(); }
+};
+
+struct TrainHost {
+  chem_config cfg;
+  double E_dep = 0.0;
+  PendingHost pend;   // mirror of the device queue [0, p_tail)
+};
+
+}  // namespace
+
+struct chem_ctx {
+  int B = 0;
+  int precision = CHEM_FP64;
+  std::vector<TrainHost> th;
+  Tables tables{};
+  Dev d{};
+  LaunchCfg lc{};
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  chem_alloc_fn alloc = nullptr;
+  chem_free_fn dfree = nullptr;
+  void* alloc_user = nullptr;
+  std::vector<std::pair<void*, size_t>> allocs;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  int steps_per_launch = 16;
+  bool persistent = false;
+  int cell_factor_x100 = 400;  // hash cells per species budget (x100)
+  Global* g_pinned = nullptr;  // host copy of the global counters
+  double* t_end_pinned = nullptr;
+  double* t_end_dev = nullptr;
+  std::string err;
+  chem_status status = CHEM_OK;
+};
+
+namespace {
+
+chem_status fail(chem_ctx* c, chem_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) {
+    if (c->status == CHEM_OK) {
+      c->status = s;
+      c->err = buf;
+    }
+  }
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, CHEM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+void* dev_alloc(chem_ctx* ctx, size_t bytes) {
+  bytes = (bytes + 255) & ~static_cast<size_t>(255);
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (ctx->alloc) {
+    p = ctx->alloc(bytes, ctx->alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) ctx->allocs.emplace_back(p, bytes);
+  return p;
+}
+
+void release_all(chem_ctx* ctx) {
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  ctx->graph = nullptr;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& a : ctx->allocs) {
+    if (ctx->dfree) ctx->dfree(a.first, a.second, ctx->alloc_user);
+    else cudaFree(a.first);
+  }
+  ctx->allocs.clear();
+  if (ctx->g_pinned) cudaFreeHost(ctx->g_pinned);
+  if (ctx->t_end_pinned) cudaFreeHost(ctx->t_end_pinned);
+  ctx->g_pinned = nullptr;
+  ctx->t_end_pinned = nullptr;
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  ctx->stream = nullptr;
+}
+
+int bits_for(uint64_t v) {
+  int b = 0;
+  while ((1ull << b) <= v) ++b;
+  return b;
+}
+
+chem_status validate(const chem_config* cfgs, int B) {
+  if (!cfgs || B < 1 || B > MAX_TRAINS) return CHEM_EINVAL;
+  const chem_config& c0 = cfgs[0];
+  for (int b = 0; b < B; ++b) {
+    const chem_config& c = cfgs[b];
+    if (c.n_types < 1 || c.n_types > CHEM_MAX_TYPES || !c.D_nm2_s) return CHEM_EINVAL;
+    if (c.n_rxn < 0 || c.n_rxn > CHEM_MAX_RXN || (c.n_rxn > 0 && !c.rxn)) return CHEM_EINVAL;
+    if (c.precision != CHEM_FP64 && c.precision != CHEM_FP32_LOCAL) return CHEM_EINVAL;
+    if (!(c.L_nm > 0.0) || !std::isfinite(c.L_nm)) return CHEM_EINVAL;
+    if (!(c.dt_min_s > 0.0) || !(c.dt_max_s >= c.dt_min_s) || !(c.dt_growth >= 1.0)) return CHEM_EINVAL;
+    if (!(c.cutoff_c >= 0.0) || !(c.sbs_horizon_s >= 0.0)) return CHEM_EINVAL;
+    if (c.capacity_species < 1 || c.capacity_species > (1ll << 30)) return CHEM_EINVAL;
+    if (c.capacity_pending < 0 || c.capacity_candidates < 0) return CHEM_EINVAL;
+    if (c.capacity_event_log < 0 || c.capacity_step_log < 0) return CHEM_EINVAL;
+    if (c.n_types != c0.n_types || c.n_rxn != c0.n_rxn || c.precision != c0.precision) return CHEM_EINVAL;
+    for (int t = 0; t < c.n_types; ++t) {
+      if (!(c.D_nm2_s[t] > 0.0) || c.D_nm2_s[t] != c0.D_nm2_s[t]) return CHEM_EINVAL;
+    }
+    for (int r = 0; r < c.n_rxn; ++r) {
+      const chem_reaction& x = c.rxn[r];
+      if (x.a < 0 || x.a >= c.n_types || x.b < 0 || x.b >= c.n_types) return CHEM_EINVAL;
+      if (!(x.k_tab > 0.0) || x.n_prod < 0 || x.n_prod > 3) return CHEM_EINVAL;
+      for (int q = 0; q < x.n_prod; ++q)
+        if (x.prod[q] < 0 || x.prod[q] >= c.n_types) return CHEM_EINVAL;
+      if (std::memcmp(&x, &c0.rxn[r], sizeof(chem_reaction)) != 0) return CHEM_EINVAL;
+    }
+  }
+  return CHEM_OK;
+}
+
+// Reaction radius from Eq. kdiff1 at steady state: k = 4 pi R D_AB N_A, k in L/mol/s
+// (1 L = 1e24 nm^3); for self reactions k_tab is the printed 2k (Eq. kdiff2).
+double reaction_radius(double k_tab, double D_AB) {
+  const double k_nm3_per_s = k_tab * 1e24 / N_AVOGADRO;
+  return k_nm3_per_s / (4.0 * PI * D_AB);
+}
+
+chem_status upload_trains(chem_ctx* ctx, const std::vector<Train>& h) {
+  CK(cudaMemcpyAsync(ctx->d.trains, h.data(), sizeof(Train) * h.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHEM_OK;
+}
+
+chem_status download_trains(chem_ctx* ctx, std::vector<Train>& h) {
+  h.resize(ctx->B);
+  CK(cudaMemcpyAsync(h.data(), ctx->d.trains, sizeof(Train) * ctx->B, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHEM_OK;
+}
+
+chem_status download_global(chem_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->g_pinned, ctx->d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHEM_OK;
+}
+
+void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
+  t.t = 0.0;
+  t.t_end = 0.0;
+  t.dt_cur = c.dt_min_s;
+  t.t_last_release = 0.0;
+  t.step = 0;
+  t.next_id = 0;
+  t.p_head = 0;
+  t.p_tail = 0;
+  t.species_steps = 0;
+  t.water = 0;
+  for (int i = 0; i < MAXT; ++i) t.counts[i] = 0;
+  for (int i = 0; i < MAXR; ++i) t.events[i] = 0;
+  t.n_ref = n_max;
+  t.h_ref = c.L_nm / n_max;
+  t.active = 0;
+  t.free_jump = 0;
+  t.key0 = static_cast<uint32_t>(c.seed & 0xFFFFFFFFull);
+  t.key1 = static_cast<uint32_t>(c.seed >> 32) ^ c.train_id;
+}
+
+chem_status capture_graph(chem_ctx* ctx) {
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  if (ctx->persistent) {
+    e = ctx->precision == CHEM_FP64
+            ? enqueue_persistent_f64(ctx->d, ctx->lc, ctx->steps_per_launch, ctx->stream)
+            : enqueue_persistent_f32l(ctx->d, ctx->lc, ctx->steps_per_launch, ctx->stream);
+  } else {
+    for (int s = 0; s < ctx->steps_per_launch && e == cudaSuccess; ++s)
+      e = ctx->precision == CHEM_FP64 ? enqueue_step_f64(ctx->d, ctx->lc, ctx->stream)
+                                      : enqueue_step_f32l(ctx->d, ctx->lc, ctx->stream);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(ctx, CHEM_ECUDA, "kernel launch during capture failed: %s", cudaGetErrorString(e));
+  }
+  CK(e2);
+  e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  ctx->graph_steps = ctx->steps_per_launch;
+  return CHEM_OK;
+}
+
+chem_status check_ctx(chem_ctx* ctx) {
+  if (!ctx) return CHEM_EINVAL;
+  return ctx->status;
+}
+
+chem_status run_loop(chem_ctx* ctx) {
+  if (!ctx->graph) {
+    chem_status s = capture_graph(ctx);
+    if (s) return s;
+  }
+  for (long long it = 0;; ++it) {
+    CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->g_pinned, ctx->d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const Global& g = *ctx->g_pinned;
+    if (g.status != 0) {
+      const char* what = g.status == CHEM_ECAPACITY ? "a device capacity was exceeded"
+                         : g.status == CHEM_ETIMEOUT ? "a bounded device wait timed out"
+                                                     : "device error";
+      return fail(ctx, static_cast<chem_status>(g.status), "%s (status %d)", what, g.status);
+    }
+    if (!g.any_active) break;
+    if (it > (1ll << 40)) return fail(ctx, CHEM_ESTATE, "run loop made no progress");
+  }
+  return CHEM_OK;
+}
+
+chem_status inject_one(chem_ctx* ctx, int b, int64_t n, const int32_t* type, const double* xyz,
+                       const double* t_arr, double energy_eV) {
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  if (b < 0 || b >= ctx->B) return CHEM_EINVAL;
+  if (n < 0 || (n > 0 && (!type || !xyz || !t_arr))) return CHEM_EINVAL;
+  std::vector<Train> tr;
+  s = download_trains(ctx, tr);
+  if (s) return s;
+  Train& t = tr[b];
+  TrainHost& h = ctx->th[b];
+  const double L = t.L, halfL = t.halfL;
+  for (int64_t i = 0; i < n; ++i) {
+    if (type[i] < 0 || type[i] >= ctx->tables.n_types) return CHEM_EINVAL;
+    if (!(t_arr[i] >= t.t) || !std::isfinite(t_arr[i])) return CHEM_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+      const double v = xyz[3 * i + a];
+      if (!(v >= -halfL && v < halfL)) return CHEM_EINVAL;
+    }
+  }
+  (void)L;
+  // drop what the device already released, merge the new species stably by arrival
+  PendingHost& p = h.pend;
+  const size_t head = t.p_head;
+  PendingHost m;
+  const size_t keep = p.size() - head;
+  const size_t tot = keep + static_cast<size_t>(n);
+  if (tot > t.pend_cap) return fail(ctx, CHEM_ECAPACITY, "pending queue of train %d would hold %zu > %u",
+                                    b, tot, t.pend_cap);
+  std::vector<size_t> order(tot);
+  for (size_t i = 0; i < tot; ++i) order[i] = i;
+  auto tval = [&](size_t i) { return i < keep ? p.t[head + i] : t_arr[i - keep]; };
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return tval(a) < tval(c); });
+  m.t.resize(tot); m.x.resize(tot); m.y.resize(tot); m.z.resize(tot); m.type.resize(tot);
+  for (size_t k = 0; k < tot; ++k) {
+    const size_t i = order[k];
+    if (i < keep) {
+      m.t[k] = p.t[head + i]; m.x[k] = p.x[head + i]; m.y[k] = p.y[head + i]; m.z[k] = p.z[head + i];
+      m.type[k] = p.type[head + i];
+    } else {
+      const size_t j = i - keep;
+      m.t[k] = t_arr[j]; m.x[k] = xyz[3 * j]; m.y[k] = xyz[3 * j + 1]; m.z[k] = xyz[3 * j + 2];
+      m.type[k] = type[j];
+    }
+  }
+  p = std::move(m);
+  if (tot) {
+    const size_t off = t.pend_base;
+    CK(cudaMemcpyAsync(ctx->d.pt + off, p.t.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.px + off, p.x.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.py + off, p.y.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.pz + off, p.z.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.p_type + off, p.type.data(), tot * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  t.p_head = 0;
+  t.p_tail = static_cast<uint32_t>(tot);
+  h.E_dep += energy_eV;
+  return upload_trains(ctx, tr);
+}
+
+chem_status tally_one(chem_ctx* ctx, int b, int64_t* counts, double* G, int64_t* events,
+                      double* t_now, int64_t* species_steps) {
+  if (!ctx) return CHEM_EINVAL;
+  if (b < 0 || b >= ctx->B) return CHEM_EINVAL;
+  std::vector<Train> tr;
+  chem_status s = download_trains(ctx, tr);
+  if (s) return s;
+  const Train& t = tr[b];
+  const double E = ctx->th[b].E_dep;
+  for (int i = 0; i < ctx->tables.n_types; ++i) {
+    if (counts) counts[i] = t.counts[i];
+    if (G) G[i] = E > 0.0 ? static_cast<double>(t.counts[i]) * 100.0 / E : 0.0;
+  }
+  for (int r = 0; r < ctx->tables.n_rxn; ++r)
+    if (events) events[r] = t.events[r];
+  if (t_now) *t_now = t.t;
+  if (species_steps) *species_steps = t.species_steps;
+  return ctx->status;
+}
+
+chem_status state_one(chem_ctx* ctx, int b, int64_t cap, int32_t* type, uint32_t* id, double* xyz,
+                      int64_t* n_out) {
+  if (!ctx) return CHEM_EINVAL;
+  if (b < 0 || b >= ctx->B || cap < 0) return CHEM_EINVAL;
+  chem_status s = download_global(ctx);
+  if (s) return s;
+  std::vector<Train> tr;
+  s = download_trains(ctx, tr);
+  if (s) return s;
+  const uint32_t n = ctx->g_pinned->n_total;
+  std::vector<uint8_t> dead(n);
+  std::vector<uint32_t> cell(n), tid(n);
+  std::vector<double> x(n), y(n), z(n);
+  std::vector<float4> v4;
+  if (n) {
+    CK(cudaMemcpy(dead.data(), ctx->d.dead, n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cell.data(), ctx->d.cell_sorted, n * 4, cudaMemcpyDeviceToHost));
+    if (ctx->precision == CHEM_FP64) {
+      CK(cudaMemcpy(tid.data(), ctx->d.stid, n * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(x.data(), ctx->d.sx, n * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(y.data(), ctx->d.sy, n * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(z.data(), ctx->d.sz, n * 8, cudaMemcpyDeviceToHost));
+    } else {
+      v4.resize(n);
+      CK(cudaMemcpy(v4.data(), ctx->d.s4, n * 16, cudaMemcpyDeviceToHost));
+    }
+  }
+  int64_t k = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (dead[i]) continue;
+    // train of the slot from its cell
+    int tb = 0;
+    for (int q = ctx->B - 1; q >= 0; --q)
+      if (tr[q].cell_base <= cell[i]) { tb = q; break; }
+    if (tb != b) continue;
+    const Train& t = tr[b];
+    uint32_t tt;
+    double px, py, pz;
+    if (ctx->precision == CHEM_FP64) {
+      tt = tid[i]; px = x[i]; py = y[i]; pz = z[i];
+    } else {
+      std::memcpy(&tt, &v4[i].w, 4);
+      const uint32_t loc = cell[i] - t.cell_base;
+      const uint32_t nr = static_cast<uint32_t>(t.n_ref);
+      const double h = t.h_ref;
+      const int ix = static_cast<int>(loc % nr), iy = static_cast<int>((loc / nr) % nr),
+                iz = static_cast<int>(loc / (nr * nr));
+      auto wrapb = [&](double q) {
+        q -= t.L * std::floor((q + t.halfL) / t.L);
+        if (q >= t.halfL) q -= t.L;
+        if (q < -t.halfL) q += t.L;
+        return q;
+      };
+      px = wrapb(ix * h - t.halfL + v4[i].x);
+      py = wrapb(iy * h - t.halfL + v4[i].y);
+      pz = wrapb(iz * h - t.halfL + v4[i].z);
+    }
+    if (k < cap) {
+      if (type) type[k] = static_cast<int32_t>(tt & 7u);
+      if (id) id[k] = tt >> 3;
+      if (xyz) { xyz[3 * k] = px; xyz[3 * k + 1] = py; xyz[3 * k + 2] = pz; }
+    }
+    ++k;
+  }
+  if (n_out) *n_out = k;
+  if (k > cap) return CHEM_EINVAL;
+  return ctx->status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* chem_version(void) { return "chemgb 0.1 (sm_103a)"; }
+
+const char* chem_last_error(const chem_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.empty() ? "" : ctx->err.c_str();
+}
+
+void chem_destroy(chem_ctx* ctx) {
+  if (!ctx) return;
+  release_all(ctx);
+  delete ctx;
+}
+
+chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx** out) {
+  if (!out) return CHEM_EINVAL;
+  *out = nullptr;
+  chem_status vs = validate(cfgs, n_trains);
+  if (vs) return vs;
+  chem_ctx* ctx = new chem_ctx();
+  const chem_config& c0 = cfgs[0];
+  ctx->B = n_trains;
+  ctx->precision = c0.precision;
+  ctx->alloc = c0.dev_alloc;
+  ctx->dfree = c0.dev_free;
+  ctx->alloc_user = c0.alloc_user;
+  if ((ctx->alloc == nullptr) != (ctx->dfree == nullptr)) {
+    delete ctx;
+    return CHEM_EINVAL;
+  }
+  ctx->th.resize(n_trains);
+  for (int b = 0; b < n_trains; ++b) ctx->th[b].cfg = cfgs[b];
+  if (c0.steps_per_launch > 0) ctx->steps_per_launch = c0.steps_per_launch;
+  ctx->persistent = n_trains > 1;
+
+  // ---- chemistry tables
+  Tables& T = ctx->tables;
+  std::memset(&T, 0, sizeof(T));
+  T.n_types = c0.n_types;
+  T.n_rxn = c0.n_rxn;
+  for (int t = 0; t < T.n_types; ++t) {
+    T.D[t] = c0.D_nm2_s[t];
+    T.Df[t] = static_cast<float>(c0.D_nm2_s[t]);
+  }
+  std::memset(T.pair_rxn, -1, sizeof(T.pair_rxn));
+  for (int r = 0; r < T.n_rxn; ++r) {
+    const chem_reaction& x = c0.rxn[r];
+    if (T.pair_rxn[x.a][x.b] >= 0) {
+      delete ctx;
+      return CHEM_EINVAL;  // two reactions for one type pair
+    }
+    T.pair_rxn[x.a][x.b] = T.pair_rxn[x.b][x.a] = static_cast<int8_t>(r);
+    T.reactive_mask[x.a] |= 1u << x.b;
+    T.reactive_mask[x.b] |= 1u << x.a;
+    T.D_AB[r] = T.D[x.a] + T.D[x.b];
+    T.R[r] = reaction_radius(x.k_tab, T.D_AB[r]);
+    T.Rf[r] = static_cast<float>(T.R[r]);
+    T.D_ABf[r] = static_cast<float>(T.D_AB[r]);
+    T.n_prod[r] = x.n_prod;
+    for (int q = 0; q < 3; ++q) T.prod[r][q] = q < x.n_prod ? x.prod[q] : 0;
+    T.water[r] = x.water_delta;
+  }
+
+  // ---- per-train constants and global sizes
+  std::vector<Train> tr(n_trains);
+  uint64_t cap = 0, pend = 0, cells = 0, cand = 0, evlog = 0, steplog = 0;
+  int tbits = bits_for(static_cast<uint64_t>(n_trains - 1));
+  for (int b = 0; b < n_trains; ++b) {
+    const chem_config& c = cfgs[b];
+    Train& t = tr[b];
+    std::memset(&t, 0, sizeof(Train));
+    t.L = c.L_nm;
+    t.halfL = 0.5 * c.L_nm;
+    t.dt_min = c.dt_min_s;
+    t.dt_max = c.dt_max_s;
+    t.dt_growth = c.dt_growth;
+    t.c = c.cutoff_c;
+    t.horizon = c.sbs_horizon_s;
+    t.reset_on_release = c.dt_reset_on_release ? 1 : 0;
+    // dt cap: every cutoff R + c sqrt(2 D_AB dt) stays <= L/3
+    double dt_L = std::numeric_limits<double>::infinity();
+    for (int r = 0; r < T.n_rxn; ++r) {
+      const double room = c.L_nm / 3.0 - T.R[r];
+      if (!(room > 0.0)) {
+        delete ctx;
+        return CHEM_EINVAL;
+      }
+      if (c.cutoff_c > 0.0) {
+        const double q = room / c.cutoff_c;
+        dt_L = std::min(dt_L, q * q / (2.0 * T.D_AB[r]));
+      }
+    }
+    t.dt_L = dt_L;
+    int n_max = c.cells_per_axis_max;
+    if (n_max <= 0) {
+      const double budget = static_cast<double>(c.capacity_species) * ctx->cell_factor_x100 / 100.0;
+      n_max = static_cast<int>(std::floor(std::cbrt(budget)));
+      n_max = std::max(3, std::min(n_max, 256));
+    }
+    if (n_max < 3 || n_max > 1024) {
+      delete ctx;
+      return CHEM_EINVAL;
+    }
+    t.n_max = n_max;
+    t.cell_base = static_cast<uint32_t>(cells);
+    cells += static_cast<uint64_t>(n_max) * n_max * n_max;
+    t.pend_base = static_cast<uint32_t>(pend);
+    t.pend_cap = static_cast<uint32_t>(c.capacity_pending);
+    pend += static_cast<uint64_t>(c.capacity_pending);
+    t.id_limit = (tbits + 29 <= 32) ? (1u << 29) - 1u : (1u << (32 - tbits)) - 1u;
+    init_train_dynamic(t, c, n_max);
+    cap += static_cast<uint64_t>(c.capacity_species);
+    cand += static_cast<uint64_t>(c.capacity_candidates);
+    evlog += static_cast<uint64_t>(c.capacity_event_log);
+    steplog += static_cast<uint64_t>(c.capacity_step_log);
+  }
+  if (cap >= (1ull << 31) || cells >= (1ull << 31) || pend >= (1ull << 31) || cand >= (1ull << 31)) {
+    delete ctx;
+    return CHEM_EINVAL;
+  }
+  if (cand == 0) cand = 1;
+
+  // ---- stream, device properties, launch shapes
+  if (c0.cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(c0.cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      chem_status s = fail(ctx, CHEM_ECUDA, "no usable CUDA device");
+      *out = ctx;
+      return s;
+    }
+    ctx->own_stream = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ctx->sms <= 0) {
+    *out = ctx;
+    return fail(ctx, CHEM_ECUDA, "no usable CUDA device");
+  }
+  int sort_occ = 0, pers_occ = 0;
+  if (sort_pass_occupancy(&sort_occ) != cudaSuccess || sort_occ < 1) {
+    *out = ctx;
+    return fail(ctx, CHEM_ECUDA, "sort kernel not loadable: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  cudaError_t pe = ctx->precision == CHEM_FP64 ? persistent_occupancy_f64(&pers_occ)
+                                               : persistent_occupancy_f32l(&pers_occ);
+  if (pe != cudaSuccess || pers_occ < 1) {
+    *out = ctx;
+    return fail(ctx, CHEM_ECUDA, "step kernel not loadable: %s", cudaGetErrorString(pe));
+  }
+  ctx->lc.stream_blocks = ctx->sms * 4;
+  ctx->lc.search_blocks = ctx->sms * 8;
+  ctx->lc.sort_blocks = ctx->sms * sort_occ;
+  ctx->lc.persistent_blocks = ctx->sms * pers_occ;
+
+  // ---- device allocations
+  Dev& d = ctx->d;
+  d.cap = static_cast<uint32_t>(cap);
+  d.cap_cand = static_cast<uint32_t>(cand);
+  d.cap_ev_log = static_cast<uint32_t>(evlog);
+  d.cap_step_log = static_cast<uint32_t>(steplog);
+  d.cap_pend = static_cast<uint32_t>(pend);
+  d.n_trains = static_cast<uint32_t>(n_trains);
+  d.total_cells = static_cast<uint32_t>(cells);
+  d.sentinel = static_cast<uint32_t>(cells);
+  d.passes = (bits_for(cells) + 7) / 8;
+  if (d.passes < 1) d.passes = 1;
+  if (d.passes > MAX_PASSES) {
+    *out = ctx;
+    return fail(ctx, CHEM_EINVAL, "too many hash cells");
+  }
+  d.precision = ctx->precision;
+  d.max_tiles = static_cast<uint32_t>(cap / SORT_TILE + 2);
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void* p = dev_alloc(ctx, bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  if (ctx->precision == CHEM_FP64) {
+    d.sx = static_cast<double*>(A(cap * 8)); d.sy = static_cast<double*>(A(cap * 8));
+    d.sz = static_cast<double*>(A(cap * 8)); d.stid = static_cast<uint32_t*>(A(cap * 4));
+    d.tx = static_cast<double*>(A(cap * 8)); d.ty = static_cast<double*>(A(cap * 8));
+    d.tz = static_cast<double*>(A(cap * 8)); d.ttid = static_cast<uint32_t*>(A(cap * 4));
+  } else {
+    d.s4 = static_cast<float4*>(A(cap * 16));
+    d.t4 = static_cast<float4*>(A(cap * 16));
+  }
+  d.cell_sorted = static_cast<uint32_t*>(A(cap * 4));
+  {
+    uint32_t* sortbuf = static_cast<uint32_t*>(A(cap * 16));  // keys0|keys1|vals0|vals1
+    d.keys0 = sortbuf;
+    d.keys1 = sortbuf + cap;
+    d.vals0 = sortbuf + 2 * cap;
+    d.vals1 = sortbuf + 3 * cap;
+  }
+  d.dead = static_cast<uint8_t*>(A(cap));
+  d.cell_info = static_cast<int4*>(A((cells + 1) * 16));
+  d.lookback = static_cast<unsigned long long*>(A(static_cast<size_t>(d.max_tiles) * RADIX * 8));
+  d.cand = static_cast<Cand*>(A(cand * sizeof(Cand)));
+  const uint64_t evn = std::max<uint64_t>(cand, RADIX);
+  d.ev_list = static_cast<uint32_t*>(A(evn * 4));
+  d.alive0 = static_cast<uint32_t*>(A(evn * 4));
+  d.alive1 = static_cast<uint32_t*>(A(evn * 4));
+  d.ev_k0 = static_cast<uint32_t*>(A(evn * 4));
+  d.ev_k1 = static_cast<uint32_t*>(A(evn * 4));
+  d.ev_v0 = static_cast<uint32_t*>(A(evn * 4));
+  d.ev_v1 = static_cast<uint32_t*>(A(evn * 4));
+  d.ev_log = static_cast<chem_event*>(A(std::max<uint64_t>(evlog, 1) * sizeof(chem_event)));
+  d.step_log = static_cast<chem_step_record*>(A(std::max<uint64_t>(steplog, 1) * sizeof(chem_step_record)));
+  const uint64_t pn = std::max<uint64_t>(pend, 1);
+  d.p_type = static_cast<int32_t*>(A(pn * 4));
+  d.px = static_cast<double*>(A(pn * 8)); d.py = static_cast<double*>(A(pn * 8));
+  d.pz = static_cast<double*>(A(pn * 8)); d.pt = static_cast<double*>(A(pn * 8));
+  d.trains = static_cast<Train*>(A(sizeof(Train) * n_trains));
+  Tables* tables_dev = static_cast<Tables*>(A(sizeof(Tables)));
+  d.tables = tables_dev;
+  d.g = static_cast<Global*>(A(sizeof(Global)));
+  *out = ctx;
+  if (!ok) return fail(ctx, CHEM_ENOMEM, "device allocation failed");
+  if (cudaMallocHost(&ctx->g_pinned, sizeof(Global)) != cudaSuccess ||
+      cudaMallocHost(&ctx->t_end_pinned, sizeof(double) * n_trains) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, CHEM_ENOMEM, "pinned host allocation failed");
+  }
+  ctx->t_end_dev = static_cast<double*>(A(sizeof(double) * n_trains));
+  if (!ok) return fail(ctx, CHEM_ENOMEM, "device allocation failed");
+  CK(cudaMemsetAsync(d.dead, 0, cap, ctx->stream));
+  CK(cudaMemsetAsync(d.cell_info, 0xFF, (cells + 1) * 16, ctx->stream));
+  CK(cudaMemsetAsync(d.lookback, 0, static_cast<size_t>(d.max_tiles) * RADIX * 8, ctx->stream));
+  CK(cudaMemsetAsync(d.g, 0, sizeof(Global), ctx->stream));
+  CK(cudaMemcpyAsync(tables_dev, &T, sizeof(Tables), cudaMemcpyHostToDevice, ctx->stream));
+  return upload_trains(ctx, tr);
+}
+
+chem_status chem_init(const chem_config* cfg, chem_ctx** out) { return chem_batch_init(cfg, 1, out); }
+
+chem_status chem_batch_inject(chem_ctx* ctx, int32_t train, int64_t n, const int32_t* type,
+                              const double* xyz, const double* t_arrival, double energy_eV) {
+  return inject_one(ctx, train, n, type, xyz, t_arrival, energy_eV);
+}
+
+chem_status chem_inject_pulse(chem_ctx* ctx, int64_t n, const int32_t* type, const double* xyz,
+                              const double* t_arrival, double energy_eV) {
+  return inject_one(ctx, 0, n, type, xyz, t_arrival, energy_eV);
+}
+
+chem_status chem_batch_run_until(chem_ctx* ctx, const double* t_end_s) {
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  if (!t_end_s) return CHEM_EINVAL;
+  for (int b = 0; b < ctx->B; ++b) {
+    if (!std::isfinite(t_end_s[b])) return CHEM_EINVAL;
+    ctx->t_end_pinned[b] = t_end_s[b];
+  }
+  CK(cudaMemcpyAsync(ctx->t_end_dev, ctx->t_end_pinned, sizeof(double) * ctx->B, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(enqueue_set_t_end(ctx->d, ctx->t_end_dev, ctx->stream));
+  return run_loop(ctx);
+}
+
+chem_status chem_run_until(chem_ctx* ctx, double t_end_s) {
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  std::vector<double> t(ctx->B, t_end_s);
+  return chem_batch_run_until(ctx, t.data());
+}
+
+chem_status chem_batch_tally(chem_ctx* ctx, int32_t train, int64_t* counts, double* G, int64_t* events,
+                             double* t_now, int64_t* species_steps) {
+  return tally_one(ctx, train, counts, G, events, t_now, species_steps);
+}
+
+chem_status chem_tally(chem_ctx* ctx, int64_t* counts, double* G, int64_t* events, double* t_now,
+                       int64_t* species_steps) {
+  return tally_one(ctx, 0, counts, G, events, t_now, species_steps);
+}
+
+chem_status chem_batch_get_state(chem_ctx* ctx, int32_t train, int64_t cap, int32_t* type, uint32_t* id,
+                                 double* xyz, int64_t* n) {
+  return state_one(ctx, train, cap, type, id, xyz, n);
+}
+
+chem_status chem_get_state(chem_ctx* ctx, int64_t cap, int32_t* type, uint32_t* id, double* xyz,
+                           int64_t* n) {
+  return state_one(ctx, 0, cap, type, id, xyz, n);
+}
+
+chem_status chem_get_events(chem_ctx* ctx, int64_t cap, chem_event* ev, int64_t* n) {
+  if (!ctx || cap < 0) return CHEM_EINVAL;
+  chem_status s = download_global(ctx);
+  if (s) return s;
+  const uint64_t have = std::min<uint64_t>(ctx->g_pinned->ev_log_n, ctx->d.cap_ev_log);
+  const uint64_t k = std::min<uint64_t>(have, static_cast<uint64_t>(cap));
+  if (k && ev) CK(cudaMemcpy(ev, ctx->d.ev_log, k * sizeof(chem_event), cudaMemcpyDeviceToHost));
+  if (n) *n = static_cast<int64_t>(have);
+  return ctx->status;
+}
+
+chem_status chem_get_step_log(chem_ctx* ctx, int64_t cap, chem_step_record* rec, int64_t* n) {
+  if (!ctx || cap < 0) return CHEM_EINVAL;
+  chem_status s = download_global(ctx);
+  if (s) return s;
+  const uint64_t have = std::min<uint64_t>(ctx->g_pinned->step_log_n, ctx->d.cap_step_log);
+  const uint64_t k = std::min<uint64_t>(have, static_cast<uint64_t>(cap));
+  if (k && rec) CK(cudaMemcpy(rec, ctx->d.step_log, k * sizeof(chem_step_record), cudaMemcpyDeviceToHost));
+  if (n) *n = static_cast<int64_t>(have);
+  return ctx->status;
+}
+
+chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds) {
+  if (!ctx) return CHEM_EINVAL;
+  if (ctx->status == CHEM_ECUDA) return ctx->status;
+  std::vector<Train> tr;
+  chem_status s = download_trains(ctx, tr);
+  if (s) return s;
+  for (int b = 0; b < ctx->B; ++b) {
+    TrainHost& h = ctx->th[b];
+    if (seeds) h.cfg.seed = seeds[b];
+    h.E_dep = 0.0;
+    h.pend = PendingHost();
+    init_train_dynamic(tr[b], h.cfg, tr[b].n_max);
+  }
+  CK(cudaMemsetAsync(ctx->d.g, 0, sizeof(Global), ctx->stream));
+  CK(cudaMemsetAsync(ctx->d.dead, 0, ctx->d.cap, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d.cell_info, 0xFF, (static_cast<size_t>(ctx->d.total_cells) + 1) * 16, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d.lookback, 0, static_cast<size_t>(ctx->d.max_tiles) * RADIX * 8, ctx->stream));
+  s = upload_trains(ctx, tr);
+  if (s) return s;
+  ctx->status = CHEM_OK;
+  ctx->err.clear();
+  return CHEM_OK;
+}
+
+chem_status chem_reset(chem_ctx* ctx, uint64_t seed) {
+  if (!ctx) return CHEM_EINVAL;
+  std::vector<uint64_t> seeds(ctx->B);
+  for (int b = 0; b < ctx->B; ++b) seeds[b] = seed + static_cast<uint64_t>(b);
+  return chem_batch_reset(ctx, seeds.data());
+}
+
+int32_t chem_batch_size(const chem_ctx* ctx) { return ctx ? ctx->B : 0; }
+
+chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
+  if (!ctx) return CHEM_EINVAL;
+  (void)budget_ms;
+  if (chosen) {
+    chosen[0] = ctx->steps_per_launch;
+    chosen[1] = ctx->cell_factor_x100;
+  }
+  return ctx->status;
+}
+
+}  // extern "C"

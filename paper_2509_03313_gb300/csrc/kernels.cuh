@@ -1,0 +1,138 @@
+// Kernels of one SBS step: one kernel per phase (captured into a CUDA graph of several
+// steps), and a persistent cooperative kernel that runs the same phases for several
+// steps of every train with grid barriers in between.
+#pragma once
+#include "launch.h"
+#include "phases.cuh"
+
+namespace chem {
+
+union PhaseSmem {
+  BeginSmem begin;
+  uint32_t hist[MAX_PASSES][RADIX];
+  SortSmem sort;
+  ReactSmem react;
+};
+
+// Grid-wide barrier of the persistent kernel. The wait is bounded: past the limit the
+// kernel raises CHEM_ETIMEOUT, and once any error is raised the barrier stops waiting
+// (every phase then skips its work), so a launch always ends.
+__device__ __forceinline__ void grid_sync(const Dev& d) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Global* g = d.g;
+    const uint32_t gen = ld_acquire_u32(&g->bar_gen);
+    __threadfence();
+    const uint32_t arrived = atomicAdd(&g->bar_count, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      g->bar_count = 0;
+      __threadfence();
+      atomicAdd(&g->bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(&g->bar_gen) == gen) {
+        if (*reinterpret_cast<volatile int*>(&g->status) != 0) break;
+        if (clock64() - t0 > SPIN_LIMIT_CYCLES) {
+          raise_status(g, CHEM_ETIMEOUT);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <bool F32L>
+__global__ void __launch_bounds__(256) k_release(const __grid_constant__ Dev d) {
+  phase_release<F32L>(d);
+}
+
+template <bool F32L>
+__global__ void __launch_bounds__(256) k_diffuse(const __grid_constant__ Dev d) {
+  __shared__ uint32_t hist[MAX_PASSES][RADIX];
+  phase_diffuse<F32L>(d, hist);
+}
+
+template <bool F32L>
+__global__ void __launch_bounds__(256) k_gather(const __grid_constant__ Dev d) {
+  phase_gather<F32L>(d);
+}
+
+template <bool F32L>
+__global__ void __launch_bounds__(256) k_search(const __grid_constant__ Dev d) {
+  phase_search<F32L>(d);
+}
+
+template <bool F32L>
+__global__ void __launch_bounds__(REACT_THREADS) k_react(const __grid_constant__ Dev d) {
+  __shared__ ReactSmem sm;
+  phase_react<F32L>(d, sm);
+}
+
+template <bool F32L>
+__global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev d, int n_steps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PhaseSmem& sm = *reinterpret_cast<PhaseSmem*>(smem_raw);
+  for (int step = 0; step < n_steps; ++step) {
+    if (blockIdx.x == 0) phase_begin(d, sm.begin);
+    grid_sync(d);
+    phase_release<F32L>(d);
+    grid_sync(d);
+    phase_diffuse<F32L>(d, sm.hist);
+    grid_sync(d);
+    for (int p = 0; p < d.passes; ++p) {
+      phase_sort_pass(d, p, sm.sort);
+      grid_sync(d);
+    }
+    phase_gather<F32L>(d);
+    grid_sync(d);
+    phase_search<F32L>(d);
+    grid_sync(d);
+    if (blockIdx.x == 0) phase_react<F32L>(d, sm.react);
+    grid_sync(d);
+  }
+}
+
+template <bool F32L>
+cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s) {
+  cudaError_t e = enqueue_begin(d, s);
+  if (e != cudaSuccess) return e;
+  k_release<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
+  k_diffuse<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
+  for (int p = 0; p < d.passes; ++p) {
+    e = enqueue_sort_pass(d, p, lc.sort_blocks, s);
+    if (e != cudaSuccess) return e;
+  }
+  k_gather<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
+  k_search<F32L><<<lc.search_blocks, 256, 0, s>>>(d);
+  k_react<F32L><<<1, REACT_THREADS, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+template <bool F32L>
+cudaError_t enqueue_persistent(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(lc.persistent_blocks);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = sizeof(PhaseSmem);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_persistent<F32L>, d, n_steps);
+}
+
+template <bool F32L>
+cudaError_t persistent_occupancy(int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_persistent<F32L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sizeof(PhaseSmem)));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_persistent<F32L>, 256,
+                                                       sizeof(PhaseSmem));
+}
+
+}  // namespace chem

@@ -1,0 +1,55 @@
+// FP64-mode kernels and the precision-independent ones (step begin, sort passes).
+// Built with --fmad=false: together with the explicit _rn intrinsics in phases.cuh
+// this keeps the FP64 mode's rounding identical to the FP64 reference's.
+#include "kernels.cuh"
+
+namespace chem {
+
+__global__ void __launch_bounds__(256) k_begin(const __grid_constant__ Dev d) {
+  __shared__ BeginSmem sb;
+  phase_begin(d, sb);
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_pass(const __grid_constant__ Dev d, int pass) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  phase_sort_pass(d, pass, *reinterpret_cast<SortSmem*>(smem_raw));
+}
+
+__global__ void k_set_t_end(const __grid_constant__ Dev d, const double* t_end) {
+  for (uint32_t b = threadIdx.x; b < d.n_trains; b += blockDim.x) d.trains[b].t_end = t_end[b];
+}
+
+cudaError_t enqueue_begin(const Dev& d, cudaStream_t s) {
+  k_begin<<<1, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_sort_pass(const Dev& d, int pass, int blocks, cudaStream_t s) {
+  k_sort_pass<<<blocks, SORT_THREADS, sizeof(SortSmem), s>>>(d, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t sort_pass_occupancy(int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sizeof(SortSmem)));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sort_pass, SORT_THREADS,
+                                                       sizeof(SortSmem));
+}
+
+cudaError_t enqueue_set_t_end(const Dev& d, const double* t_end_dev, cudaStream_t s) {
+  k_set_t_end<<<1, 256, 0, s>>>(d, t_end_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s) {
+  return enqueue_phases<false>(d, lc, s);
+}
+
+cudaError_t enqueue_persistent_f64(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s) {
+  return enqueue_persistent<false>(d, lc, n_steps, s);
+}
+
+cudaError_t persistent_occupancy_f64(int* blocks_per_sm) { return persistent_occupancy<false>(blocks_per_sm); }
+
+}  // namespace chem

@@ -1,0 +1,17 @@
+// FP32-local-mode kernels: positions as FP32 offsets from their hash cell's origin,
+// FP32 normals and distances; clock, schedule, reaction probabilities and tallies FP64.
+#include "kernels.cuh"
+
+namespace chem {
+
+cudaError_t enqueue_step_f32l(const Dev& d, const LaunchCfg& lc, cudaStream_t s) {
+  return enqueue_phases<true>(d, lc, s);
+}
+
+cudaError_t enqueue_persistent_f32l(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s) {
+  return enqueue_persistent<true>(d, lc, n_steps, s);
+}
+
+cudaError_t persistent_occupancy_f32l(int* blocks_per_sm) { return persistent_occupancy<true>(blocks_per_sm); }
+
+}  // namespace chem

@@ -1,0 +1,192 @@
+// Device-side data layout and helpers of the SBS chemistry library (sm_103a).
+//
+// Layout in HBM (one context = B >= 1 independent pulse trains):
+//  * species state S, sorted by global hash cell (cell_base[train] + local cell):
+//      FP64 mode        SoA  double x[cap], y[cap], z[cap]; uint32 tid[cap]
+//      FP32-local mode  AoS  float4 {off_x, off_y, off_z, bits(tid)} per slot; the
+//                       offsets are relative to the origin of the slot's hash cell
+//    tid = (id << 3) | type. A scratch copy T of the same layout receives the diffused
+//    species in S order before the sort.
+//  * cell_sorted[cap]: global cell of every slot of S (train = cell -> train lookup)
+//  * radix scratch keys[2][cap], vals[2][cap] (reused as the matching arrays)
+//  * cell_info[total_cells]: int4 {first slot, end slot, epoch stamp, 0}. An entry is
+//    valid only when its stamp equals the current step epoch, so nothing is cleared.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/chem.h"
+
+namespace chem {
+
+constexpr int MAXT = CHEM_MAX_TYPES;
+constexpr int MAXR = CHEM_MAX_RXN;
+constexpr int MAX_TRAINS = 256;
+constexpr int RADIX = 256;
+constexpr int MAX_PASSES = 4;
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 15;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 3840 keys per tile
+constexpr int REACT_THREADS = 1024;
+constexpr double END_SLACK = 1.0 + 1e-6;    // last-step trim slack (relative)
+constexpr double CELL_SLACK = 1.0 + 1e-6;   // hash cell >= cutoff * CELL_SLACK
+constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+// Chemistry shared by all trains of a context (Table 1, Table S2).
+struct Tables {
+  int n_types, n_rxn;
+  double D[MAXT];
+  float Df[MAXT];
+  int8_t pair_rxn[MAXT][MAXT];  // reaction index of a type pair, -1 if none
+  uint32_t reactive_mask[MAXT]; // bit j set when types (i, j) react
+  double R[MAXR], D_AB[MAXR];   // radius (nm) and D_A + D_B
+  float Rf[MAXR], D_ABf[MAXR];
+  int n_prod[MAXR];
+  int prod[MAXR][3];
+  int water[MAXR];
+  double w_lo[MAXR];            // unused placeholder for alignment
+};
+
+// Per-train state. Constants are written at init; the clock and tallies live here on
+// the device in FP64 / int64 and are read back by the host only on request.
+struct Train {
+  // constants
+  double L, halfL, dt_min, dt_max, dt_growth, dt_L, c, horizon;
+  uint32_t key0, key1;
+  int reset_on_release;
+  int n_max;               // cells per axis limit
+  uint32_t cell_base;      // first global cell of this train
+  uint32_t pend_base;      // first pending slot of this train
+  uint32_t pend_cap;
+  uint32_t id_limit;       // ids must stay below this
+  // clock and tallies
+  double t, t_end, dt_cur, t_last_release;
+  uint32_t step, next_id;
+  uint32_t p_head, p_tail; // pending queue [p_head, p_tail) relative to pend_base
+  long long species_steps, water;
+  long long counts[MAXT];
+  long long events[MAXR];
+  // grid that cell_sorted of this train refers to (FP32-local offsets too)
+  int n_ref;
+  double h_ref;
+  // per step, written by the begin phase
+  int active, free_jump;
+  double dt, t_next, t_start;
+  int n;                   // cells per axis this step
+  double h, inv_h;
+  float hf, inv_hf;
+  double rc2[MAXR];
+  float rc2f[MAXR];
+  double sig[MAXT];        // sqrt(2 D dt) per type
+  float sigf[MAXT];
+  uint32_t rel_n, rel_off, rel_id0, rel_p0;
+  long long n_live_step;
+  uint32_t n_events_step;
+  uint32_t pad_;
+};
+
+// Context-wide counters.
+struct Global {
+  uint32_t n_total;      // slots in use: sorted live + appended products/releases
+  uint32_t n_dead;       // dead marks among them (removed by the next sort)
+  uint32_t n_live;       // after the gather: live slots [0, n_live)
+  uint32_t n_released;
+  uint32_t n_cand, n_events, n_products;
+  uint32_t epoch;        // per-step stamp, also the look-back epoch base
+  int status;            // chem_status raised on the device
+  uint32_t any_active;
+  uint32_t ev_log_n, step_log_n;
+  uint32_t hist[MAX_PASSES][RADIX];
+  uint32_t tile_ctr[MAX_PASSES];
+  uint32_t bar_count, bar_gen;  // grid barrier of the persistent launch
+  uint32_t err_where;
+  uint32_t pad_[3];
+};
+
+// Accepted reactive pair.
+struct Cand {
+  uint32_t s_lo, s_hi;   // slots in S (lo = lower id)
+  uint32_t id_lo, id_hi;
+  uint32_t rxn_train;    // rxn | train << 8
+  uint32_t pad;
+  double d1sq;           // squared end-of-step separation (FP64 mode: exact FP64)
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+  uint32_t cap, cap_cand, cap_ev_log, cap_step_log, cap_pend;
+  uint32_t n_trains, total_cells, sentinel;
+  int passes, precision;
+  double* sx; double* sy; double* sz; uint32_t* stid;
+  double* tx; double* ty; double* tz; uint32_t* ttid;
+  float4* s4; float4* t4;
+  uint32_t* cell_sorted;
+  uint32_t* keys0; uint32_t* keys1; uint32_t* vals0; uint32_t* vals1;
+  uint8_t* dead;
+  int4* cell_info;
+  unsigned long long* lookback;
+  uint32_t max_tiles;
+  Cand* cand;
+  uint32_t* ev_list;     // committed candidate indices (cap_cand)
+  uint32_t* alive0; uint32_t* alive1;
+  uint32_t* ev_k0; uint32_t* ev_k1; uint32_t* ev_v0; uint32_t* ev_v1;
+  chem_event* ev_log;
+  chem_step_record* step_log;
+  int32_t* p_type; double* px; double* py; double* pz; double* pt;
+  Train* trains;
+  const Tables* tables;
+  Global* g;
+};
+
+// ------------------------------------------------------------------ small helpers
+__device__ __forceinline__ void raise_status(Global* g, int code) {
+  atomicCAS(&g->status, 0, code);
+}
+
+__device__ __forceinline__ uint32_t tid_type(uint32_t tid) { return tid & 7u; }
+__device__ __forceinline__ uint32_t tid_id(uint32_t tid) { return tid >> 3; }
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Train owning a global cell: largest b with cell_base[b] <= cell (bases ascending).
+__device__ __forceinline__ int train_of_cell(const Train* tr, int n_trains, uint32_t cell) {
+  int lo = 0, hi = n_trains - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (tr[mid].cell_base <= cell) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: 10 rounds of two 32x32->64 multiplies; the high
+// halves are XORed with the other words and the round key, the key is bumped by the
+// Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ unsigned long long u53(uint32_t hi, uint32_t lo) {
+  return ((static_cast<unsigned long long>(hi) << 32) | lo) >> 11;
+}
+
+}  // namespace chem
