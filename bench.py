@@ -1,0 +1,350 @@
+"""Benchmark of the SBS chemical stage on one GB300 (or N independent replicas).
+
+Workload: single pulse of synthetic proton tracks, 5 um periodic cube, 200 straight
+tracks of Gaussian spurs (sigma 2 nm), ~1e6 species arriving at t = 0, log-growing dt
+from 1 ps (20 steps per decade) to 1 us. One benchmark step is one whole trajectory
+(every SBS step from 1 ps to 1 us: release, diffusion, hash, sort, pair search,
+matching, products, tallies) with a fresh seed.
+
+Prints one JSON line. ``value`` is species-steps/s of the FP32-local form with the
+species already resident in HBM (CUDA events around chem_run_until on the library's
+stream, L2 flushed before every timed trajectory); the FP64 form, the matched G-values
+and the end-to-end number through host buffers are reported beside it.
+
+``--impl reference`` times the FP64 reference on the host cores instead (bounded
+sample of the same workload: a few SBS steps of the ~1e6-species trajectory per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "species-steps/s (diffuse+search+react) FP32-local vs FP64 at matched G(H2O2)"
+UNIT = "species-steps/s"
+WORKLOAD = ("single pulse of 200 synthetic proton tracks (Gaussian spurs, sigma 2 nm), "
+            "5 um periodic cube, ~1e6 species at t=0, log dt 1 ps -> 1 us (20 steps/decade)")
+# Algorithmic bytes per species and launch of each phase kernel: one read + one write of
+# the state where the phase rewrites it, one read where it only reads it; sort passes
+# read and write one (key, value) pair.
+STATE_BYTES = {"fp32l": 16, "fp64": 28}
+PHASE_BYTES = {"diffuse": lambda s: 2 * s, "gather": lambda s: 2 * s, "search": lambda s: s,
+               "sort": lambda s: 16, "release": lambda s: 0, "begin": lambda s: 0, "react": lambda s: 0}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ------------------------------------------------------------------- CPU reference arm
+def _oracle_worker(args):
+    seed, n_species, n_steps = args
+    from oracle import sbs
+    from paper_2509_03313_gb300 import workloads as W
+    wl = W.single_pulse_tracks(seed, n_species=n_species)
+    o = sbs.from_workload(wl, seed=seed, record=False)
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        o.step_once(wl.t_end)
+    return o.species_steps, time.perf_counter() - t0
+
+
+def oracle_rate(n_proc: int, n_species: int, n_steps: int):
+    """Aggregate species-steps/s of n_proc independent reference runs (one per core)."""
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(n_proc) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, [(1000 + i, n_species, n_steps) for i in range(n_proc)])
+        wall = time.perf_counter() - t0
+    ss = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return ss / busy, ss, busy, wall
+
+
+def run_reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    n_proc = max(1, min(cores, args.ref_procs or cores))
+    # warm-up and timed steps: each step = n_proc workers x 1 SBS step of the trajectory
+    rate, ss, busy, wall = oracle_rate(n_proc, args.species, args.warmup + args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * busy / max(1, args.warmup + args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "species": args.species, "L_nm": 5000.0,
+                       "sample": f"first {args.warmup + args.steps} SBS steps (1 ps onwards) of "
+                                 f"{n_proc} independent trajectories, one per process"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": n_proc, "kind": "oracle",
+                             "sample": f"{n_proc} processes x {args.warmup + args.steps} SBS steps of "
+                                       f"the {args.species}-species trajectory"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- GPU arm helpers
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def make_ctx(chem, wl, precision, seed, cap, stream, alloc, profiling=False):
+    s = wl.schedule
+    cfg, keep = chem.make_config(
+        wl.L, wl.D, wl.reactions, seed=seed, precision=precision, dt_min=s.dt_min, dt_max=s.dt_max,
+        dt_growth=s.dt_growth, reset_on_release=s.reset_on_release, cutoff_c=s.cutoff_c,
+        capacity_species=cap, capacity_pending=cap, capacity_candidates=max(1 << 16, cap // 4),
+        stream=stream, allocator=alloc)
+    ctx = chem.chem_init(cfg)
+    if profiling:
+        chem.chem_set_profiling(ctx, True)
+    return ctx, keep
+
+
+def trajectory(chem, ctx, pulse, seed, t_end, torch, stream, flush, timed_events):
+    """Reset, inject (host -> device, outside the timed region), flush L2, time the run."""
+    chem.chem_reset(ctx, seed)
+    chem.chem_inject_pulse(ctx, pulse.types, pulse.xyz, pulse.t_arrival, pulse.energy_eV)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        a, b = timed_events
+        a.record(stream)
+    chem.chem_run_until(ctx, t_end)
+    with torch.cuda.stream(stream):
+        b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) * 1e-3
+
+
+def run_gpu_arm(args):
+    import torch
+
+    from paper_2509_03313_gb300 import chem, workloads as W
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    alloc = chem.torch_allocator(dev, stream)
+    # CPU baseline first (spawned workers, before heavy GPU work), rank 0 only, N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        n_proc = max(1, min(cores, args.ref_procs or cores))
+        rate, ss, busy, wall = oracle_rate(n_proc, args.species, args.cpu_steps)
+        cpu = {"value": rate, "unit": UNIT, "cores": n_proc, "kind": "oracle",
+               "sample": f"{n_proc} processes x first {args.cpu_steps} SBS steps (1 ps onwards) of "
+                         f"independent {args.species}-species trajectories; {busy:.1f} s"}
+    seed0 = 10_000 * (rank + 1)
+    wl = W.single_pulse_tracks(seed0, n_species=args.species)
+    pulse = wl.pulses[0]
+    cap = int(pulse.n * 1.3) + 4096
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    peak, peak_src = measured_peaks()
+    results = {}
+    modes = [("fp32l", chem.CHEM_FP32_LOCAL, args.steps)]
+    if not args.no_fp64:
+        modes.append(("fp64", chem.CHEM_FP64, max(1, args.fp64_steps)))
+    for name, prec, k_steps in modes:
+        ctx, keep = make_ctx(chem, wl, prec, seed0, cap, stream.cuda_stream, alloc,
+                             profiling=not args.no_phase_events)
+        try:
+            for w in range(args.warmup):
+                trajectory(chem, ctx, pulse, seed0 + 7 + w, wl.t_end, torch, stream, flush, ev)
+            if not args.no_phase_events:
+                chem.chem_set_profiling(ctx, True)  # zero the phase timers after warm-up
+            st0 = chem.chem_get_stats(ctx)
+            times, ss, g_h2o2, g_oh, g_e = [], 0, [], [], []
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            with ClockSampler(dev) as clk:
+                for k in range(k_steps):
+                    dt = trajectory(chem, ctx, pulse, seed0 + 100 + k, wl.t_end, torch, stream, flush, ev)
+                    tal = chem.chem_tally(ctx, 7, 9)
+                    times.append(dt)
+                    ss += tal["species_steps"]
+                    g_h2o2.append(tal["G"][W.H2O2]); g_oh.append(tal["G"][W.OH]); g_e.append(tal["G"][W.E_AQ])
+            torch.cuda.synchronize()
+            st1 = chem.chem_get_stats(ctx)
+            # end to end through the public API with host buffers
+            e2e_t, e2e_ss = [], 0
+            h2d_per = pulse.n * (4 + 8 * 4)
+            for k in range(max(1, k_steps // 2)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                chem.chem_reset(ctx, seed0 + 500 + k)
+                chem.chem_inject_pulse(ctx, pulse.types, pulse.xyz, pulse.t_arrival, pulse.energy_eV)
+                chem.chem_run_until(ctx, wl.t_end)
+                tal = chem.chem_tally(ctx, 7, 9)
+                e2e_t.append(time.perf_counter() - t0)
+                e2e_ss += tal["species_steps"]
+        finally:
+            chem.chem_destroy(ctx)
+        tot = float(np.sum(times))
+        per_phase = {}
+        for ph in ("diffuse", "sort", "gather", "search", "react", "begin", "release"):
+            ms = st1["phase_ms"][ph]
+            nl = st1["phase_launches"][ph]
+            per_phase[ph] = {"ms_total": ms, "launches": nl}
+        results[name] = dict(times=times, ss=ss, tot=tot, G_H2O2=g_h2o2, G_OH=g_oh, G_e=g_e,
+                             launches=st1["kernel_launches"] - st0["kernel_launches"],
+                             phases=per_phase, clocks=clk.summary(), e2e_t=e2e_t, e2e_ss=e2e_ss,
+                             h2d=h2d_per, d2h=8 * 7 + 8 * 7 + 8 * 9 + 16)
+    # aggregate over ranks (replicas): sum of species-steps over the max time
+    r = results["fp32l"]
+    ss_all, t_max = r["ss"], r["tot"]
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([float(r["ss"]), r["tot"]], dtype=torch.float64, device=dev)
+        a = tt.clone(); dist.all_reduce(a[0:1], op=dist.ReduceOp.SUM)
+        b = tt.clone(); dist.all_reduce(b[1:2], op=dist.ReduceOp.MAX)
+        ss_all, t_max = float(a[0]), float(b[1])
+    if rank != 0:
+        return 0
+    value = ss_all / t_max
+    # roofline of the dominant phase kernel of the FP32-local run
+    phases = r["phases"]
+    dom = max(phases, key=lambda p: phases[p]["ms_total"])
+    sb = STATE_BYTES["fp32l"]
+    dom_bytes = PHASE_BYTES[dom](sb) * r["ss"] * (1 if dom != "sort" else 1)
+    n_launch = max(1, phases[dom]["launches"])
+    if dom == "sort":
+        # species-steps per pass launch: every pass moves every species once
+        dom_bytes = PHASE_BYTES["sort"](sb) * r["ss"] * (phases["sort"]["launches"] / max(1, phases["diffuse"]["launches"]))
+    achieved = dom_bytes / max(1e-12, phases[dom]["ms_total"] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * r["tot"] / len(r["times"]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "species": int(pulse.n), "L_nm": wl.L,
+                   "t_end_s": wl.t_end, "sbs_steps_per_trajectory": int(round(r["ss"] / len(r["times"]) / pulse.n)) if pulse.n else 0,
+                   "mode": "FP32-local positions, FP64 clock/probabilities/tallies",
+                   "l2": "flushed (256 MiB write) before every timed trajectory",
+                   "phase_events": not args.no_phase_events,
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "e2e": {"value": (r["e2e_ss"] / sum(r["e2e_t"])) if r["e2e_t"] else None, "unit": UNIT,
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
+                "includes": "chem_reset + chem_inject_pulse (host arrays) + chem_run_until + chem_tally"},
+        "gpu_launches": int(r["launches"]),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_src,
+                     "algorithmic_bytes": f"{PHASE_BYTES[dom](sb)} B per species per launch",
+                     "avg_launch_ms": phases[dom]["ms_total"] / n_launch},
+        "phases_ms": {p: round(v["ms_total"], 3) for p, v in phases.items()},
+        "clocks": r["clocks"],
+        "G_per_100eV_fp32l": {"H2O2": float(np.mean(r["G_H2O2"])), "OH": float(np.mean(r["G_OH"])),
+                              "e_aq": float(np.mean(r["G_e"]))},
+    }
+    if "fp64" in results:
+        f = results["fp64"]
+        v64 = f["ss"] / f["tot"]
+        line["fp64"] = {"value": v64, "unit": UNIT, "ms_per_step": 1e3 * f["tot"] / len(f["times"]),
+                        "steps": len(f["times"]),
+                        "phases_ms": {p: round(v["ms_total"], 3) for p, v in f["phases"].items()},
+                        "G_per_100eV": {"H2O2": float(np.mean(f["G_H2O2"])), "OH": float(np.mean(f["G_OH"])),
+                                        "e_aq": float(np.mean(f["G_e"]))}}
+        line["speedup_fp32l_over_fp64"] = value / v64
+        g32, g64 = np.array(r["G_H2O2"]), np.array(f["G_H2O2"])
+        line["G_H2O2_match"] = {"fp32l_mean": float(g32.mean()), "fp64_mean": float(g64.mean()),
+                                "rel_diff": float(abs(g32.mean() - g64.mean()) / g64.mean()),
+                                "sigma_rel": float(math.sqrt(g32.var(ddof=1) / len(g32) + g64.var(ddof=1) / len(g64)) / g64.mean())
+                                if len(g32) > 1 and len(g64) > 1 else None}
+    line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--species", type=int, default=1_000_000)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--ref-procs", type=int, default=0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-phase-events", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference_arm(args)
+    return run_gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

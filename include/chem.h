@@ -204,6 +204,26 @@ int32_t chem_batch_size(const chem_ctx* ctx);
  * when chosen is not NULL. */
 chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen);
 
+/* Counters of a context since chem_init (host side, exact). Phase indices:
+ * 0 step begin, 1 release, 2 diffusion + hash keys, 3 radix sort (all passes),
+ * 4 gather + cell ranges, 5 pair search, 6 matching + products + tallies,
+ * 7 persistent step kernel (batched contexts). phase_ms and phase_launches are only
+ * accumulated while profiling is on (chem_set_profiling), from CUDA events recorded
+ * inside the captured graph around each kernel, over the steps that advanced a train. */
+typedef struct chem_stats {
+  int64_t graph_replays;    /* graph launches                                         */
+  int64_t kernel_launches;  /* library kernels launched (graph nodes counted per replay)*/
+  int64_t steps_launched;   /* SBS steps launched, including no-op steps past the end  */
+  int64_t bytes_h2d;        /* bytes copied host -> device                             */
+  int64_t bytes_d2h;        /* bytes copied device -> host                             */
+  double phase_ms[8];       /* summed device time per phase                            */
+  int64_t phase_launches[8];/* kernel launches per phase behind phase_ms               */
+} chem_stats;
+chem_status chem_get_stats(const chem_ctx* ctx, chem_stats* out);
+/* on != 0: re-capture the step graph with CUDA events around every phase kernel (adds
+ * one event-record node per kernel boundary). on == 0 removes them. Resets phase_ms. */
+chem_status chem_set_profiling(chem_ctx* ctx, int32_t on);
+
 /* Library version string. */
 const char* chem_version(void);
 

@@ -61,6 +61,15 @@ class chem_step_record(ctypes.Structure):
                 ("counts", ctypes.c_int64 * 8)]
 
 
+class chem_stats(ctypes.Structure):
+    _fields_ = [("graph_replays", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("steps_launched", ctypes.c_int64), ("bytes_h2d", ctypes.c_int64),
+                ("bytes_d2h", ctypes.c_int64), ("phase_ms", ctypes.c_double * 8),
+                ("phase_launches", ctypes.c_int64 * 8)]
+
+
+PHASES = ("begin", "release", "diffuse", "sort", "gather", "search", "react", "persistent")
+
 EVENT_DTYPE = np.dtype([("step", np.uint32), ("rxn", np.int32), ("id_lo", np.uint32),
                         ("id_hi", np.uint32), ("prod_id0", np.uint32), ("n_prod", np.int32),
                         ("train", np.uint32), ("reserved", np.uint32)])
@@ -73,7 +82,7 @@ EXPORTS = ["chem_init", "chem_inject_pulse", "chem_run_until", "chem_tally", "ch
            "chem_get_events", "chem_get_step_log", "chem_reset", "chem_last_error", "chem_destroy",
            "chem_batch_init", "chem_batch_inject", "chem_batch_run_until", "chem_batch_tally",
            "chem_batch_get_state", "chem_batch_reset", "chem_batch_size", "chem_autotune",
-           "chem_version"]
+           "chem_version", "chem_get_stats", "chem_set_profiling"]
 
 
 class ChemError(RuntimeError):
@@ -108,6 +117,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "chem_batch_size": (i32, [vp]),
         "chem_autotune": (i32, [vp, dbl, vp]),
         "chem_version": (ctypes.c_char_p, []),
+        "chem_get_stats": (i32, [vp, P(chem_stats)]),
+        "chem_set_profiling": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -348,6 +359,19 @@ def chem_last_error(ctx) -> str:
 def chem_destroy(ctx):
     if ctx:
         lib().chem_destroy(ctx)
+
+
+def chem_get_stats(ctx) -> dict:
+    st = chem_stats()
+    _check(ctx, lib().chem_get_stats(ctx, ctypes.byref(st)))
+    return dict(graph_replays=st.graph_replays, kernel_launches=st.kernel_launches,
+                steps_launched=st.steps_launched, bytes_h2d=st.bytes_h2d, bytes_d2h=st.bytes_d2h,
+                phase_ms={PHASES[i]: st.phase_ms[i] for i in range(8)},
+                phase_launches={PHASES[i]: st.phase_launches[i] for i in range(8)})
+
+
+def chem_set_profiling(ctx, on: bool):
+    _check(ctx, lib().chem_set_profiling(ctx, 1 if on else 0))
 
 
 def chem_version() -> str:

@@ -56,6 +56,9 @@ struct chem_ctx {
   Global* g_pinned = nullptr;  // host copy of the global counters
   double* t_end_pinned = nullptr;
   double* t_end_dev = nullptr;
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;  // 2 * N_PHASES per captured step when profiling
+  chem_stats stats{};
   std::string err;
   chem_status status = CHEM_OK;
 };
@@ -111,6 +114,8 @@ void release_all(chem_ctx* ctx) {
   if (ctx->t_end_pinned) cudaFreeHost(ctx->t_end_pinned);
   ctx->g_pinned = nullptr;
   ctx->t_end_pinned = nullptr;
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  ctx->events.clear();
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   ctx->stream = nullptr;
 }
@@ -159,6 +164,7 @@ double reaction_radius(double k_tab, double D_AB) {
 }
 
 chem_status upload_trains(chem_ctx* ctx, const std::vector<Train>& h) {
+  ctx->stats.bytes_h2d += static_cast<int64_t>(sizeof(Train) * h.size());
   CK(cudaMemcpyAsync(ctx->d.trains, h.data(), sizeof(Train) * h.size(), cudaMemcpyHostToDevice,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -167,6 +173,7 @@ chem_status upload_trains(chem_ctx* ctx, const std::vector<Train>& h) {
 
 chem_status download_trains(chem_ctx* ctx, std::vector<Train>& h) {
   h.resize(ctx->B);
+  ctx->stats.bytes_d2h += static_cast<int64_t>(sizeof(Train) * ctx->B);
   CK(cudaMemcpyAsync(h.data(), ctx->d.trains, sizeof(Train) * ctx->B, cudaMemcpyDeviceToHost,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -174,6 +181,7 @@ chem_status download_trains(chem_ctx* ctx, std::vector<Train>& h) {
 }
 
 chem_status download_global(chem_ctx* ctx) {
+  ctx->stats.bytes_d2h += sizeof(Global);
   CK(cudaMemcpyAsync(ctx->g_pinned, ctx->d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return CHEM_OK;
@@ -200,10 +208,19 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
   t.key1 = static_cast<uint32_t>(c.seed >> 32) ^ c.train_id;
 }
 
+int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 6 + ctx->d.passes; }
+
 chem_status capture_graph(chem_ctx* ctx) {
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
+  }
+  const size_t n_ev = (ctx->profiling && !ctx->persistent)
+                          ? static_cast<size_t>(ctx->steps_per_launch) * 2 * N_PHASES : 0;
+  while (ctx->events.size() < n_ev) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    ctx->events.push_back(e);
   }
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
@@ -213,9 +230,11 @@ chem_status capture_graph(chem_ctx* ctx) {
             ? enqueue_persistent_f64(ctx->d, ctx->lc, ctx->steps_per_launch, ctx->stream)
             : enqueue_persistent_f32l(ctx->d, ctx->lc, ctx->steps_per_launch, ctx->stream);
   } else {
-    for (int s = 0; s < ctx->steps_per_launch && e == cudaSuccess; ++s)
-      e = ctx->precision == CHEM_FP64 ? enqueue_step_f64(ctx->d, ctx->lc, ctx->stream)
-                                      : enqueue_step_f32l(ctx->d, ctx->lc, ctx->stream);
+    for (int s = 0; s < ctx->steps_per_launch && e == cudaSuccess; ++s) {
+      cudaEvent_t* ev = n_ev ? &ctx->events[static_cast<size_t>(s) * 2 * N_PHASES] : nullptr;
+      e = ctx->precision == CHEM_FP64 ? enqueue_step_f64(ctx->d, ctx->lc, ctx->stream, ev)
+                                      : enqueue_step_f32l(ctx->d, ctx->lc, ctx->stream, ev);
+    }
   }
   cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
   if (e != cudaSuccess) {
@@ -240,11 +259,36 @@ chem_status run_loop(chem_ctx* ctx) {
     chem_status s = capture_graph(ctx);
     if (s) return s;
   }
+  {
+    chem_status s0 = download_global(ctx);
+    if (s0) return s0;
+  }
+  uint32_t active_before = ctx->g_pinned->steps_active;
   for (long long it = 0;; ++it) {
     CK(cudaGraphLaunch(ctx->graph, ctx->stream));
     CK(cudaMemcpyAsync(ctx->g_pinned, ctx->d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const Global& g = *ctx->g_pinned;
+    ctx->stats.graph_replays += 1;
+    ctx->stats.steps_launched += ctx->graph_steps;
+    ctx->stats.kernel_launches += ctx->persistent ? 1 : static_cast<int64_t>(ctx->graph_steps) * kernels_per_step(ctx);
+    ctx->stats.bytes_d2h += sizeof(Global);
+    const uint32_t stepped = g.steps_active - active_before;
+    active_before = g.steps_active;
+    if (ctx->persistent) {
+      ctx->stats.phase_launches[PH_PERSISTENT] += 1;
+    } else if (!ctx->events.empty()) {
+      for (uint32_t st = 0; st < stepped && st < static_cast<uint32_t>(ctx->graph_steps); ++st) {
+        for (int ph = 0; ph < PH_PERSISTENT; ++ph) {
+          float ms = 0.f;
+          cudaEvent_t* ev = &ctx->events[static_cast<size_t>(st) * 2 * N_PHASES];
+          if (cudaEventElapsedTime(&ms, ev[2 * ph], ev[2 * ph + 1]) == cudaSuccess) {
+            ctx->stats.phase_ms[ph] += ms;
+            ctx->stats.phase_launches[ph] += ph == PH_SORT ? ctx->d.passes : 1;
+          }
+        }
+      }
+    }
     if (g.status != 0) {
       const char* what = g.status == CHEM_ECAPACITY ? "a device capacity was exceeded"
                          : g.status == CHEM_ETIMEOUT ? "a bounded device wait timed out"
@@ -304,6 +348,7 @@ chem_status inject_one(chem_ctx* ctx, int b, int64_t n, const int32_t* type, con
   }
   p = std::move(m);
   if (tot) {
+    ctx->stats.bytes_h2d += static_cast<int64_t>(tot * (4 * sizeof(double) + sizeof(int32_t)));
     const size_t off = t.pend_base;
     CK(cudaMemcpyAsync(ctx->d.pt + off, p.t.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->d.px + off, p.x.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
@@ -669,6 +714,8 @@ chem_status chem_batch_run_until(chem_ctx* ctx, const double* t_end_s) {
   CK(cudaMemcpyAsync(ctx->t_end_dev, ctx->t_end_pinned, sizeof(double) * ctx->B, cudaMemcpyHostToDevice,
                      ctx->stream));
   CK(enqueue_set_t_end(ctx->d, ctx->t_end_dev, ctx->stream));
+  ctx->stats.bytes_h2d += static_cast<int64_t>(sizeof(double) * ctx->B);
+  ctx->stats.kernel_launches += 1;
   return run_loop(ctx);
 }
 
@@ -753,6 +800,23 @@ chem_status chem_reset(chem_ctx* ctx, uint64_t seed) {
 }
 
 int32_t chem_batch_size(const chem_ctx* ctx) { return ctx ? ctx->B : 0; }
+
+chem_status chem_get_stats(const chem_ctx* ctx, chem_stats* out) {
+  if (!ctx || !out) return CHEM_EINVAL;
+  *out = ctx->stats;
+  return ctx->status;
+}
+
+chem_status chem_set_profiling(chem_ctx* ctx, int32_t on) {
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  ctx->profiling = on != 0;
+  for (int i = 0; i < 8; ++i) {
+    ctx->stats.phase_ms[i] = 0.0;
+    ctx->stats.phase_launches[i] = 0;
+  }
+  return capture_graph(ctx);
+}
 
 chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   if (!ctx) return CHEM_EINVAL;

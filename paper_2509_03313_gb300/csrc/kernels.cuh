@@ -95,19 +95,36 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev 
   }
 }
 
+// One step as one kernel per phase. With ev != nullptr, CUDA events are recorded
+// before and after each phase (ev[2 * phase], ev[2 * phase + 1]).
 template <bool F32L>
-cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s) {
+cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev) {
+  auto mark = [&](int i) { if (ev) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal); };
+  mark(2 * PH_BEGIN);
   cudaError_t e = enqueue_begin(d, s);
   if (e != cudaSuccess) return e;
+  mark(2 * PH_BEGIN + 1);
+  mark(2 * PH_RELEASE);
   k_release<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
+  mark(2 * PH_RELEASE + 1);
+  mark(2 * PH_DIFFUSE);
   k_diffuse<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
+  mark(2 * PH_DIFFUSE + 1);
+  mark(2 * PH_SORT);
   for (int p = 0; p < d.passes; ++p) {
     e = enqueue_sort_pass(d, p, lc.sort_blocks, s);
     if (e != cudaSuccess) return e;
   }
+  mark(2 * PH_SORT + 1);
+  mark(2 * PH_GATHER);
   k_gather<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
+  mark(2 * PH_GATHER + 1);
+  mark(2 * PH_SEARCH);
   k_search<F32L><<<lc.search_blocks, 256, 0, s>>>(d);
+  mark(2 * PH_SEARCH + 1);
+  mark(2 * PH_REACT);
   k_react<F32L><<<1, REACT_THREADS, 0, s>>>(d);
+  mark(2 * PH_REACT + 1);
   return cudaGetLastError();
 }
 

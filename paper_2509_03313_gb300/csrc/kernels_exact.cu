@@ -42,8 +42,8 @@ cudaError_t enqueue_set_t_end(const Dev& d, const double* t_end_dev, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s) {
-  return enqueue_phases<false>(d, lc, s);
+cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev) {
+  return enqueue_phases<false>(d, lc, s, ev);
 }
 
 cudaError_t enqueue_persistent_f64(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s) {

@@ -6,6 +6,10 @@ namespace chem {
 
 struct Dev;
 
+// Phase indices of chem_stats.phase_ms.
+enum Phase { PH_BEGIN = 0, PH_RELEASE, PH_DIFFUSE, PH_SORT, PH_GATHER, PH_SEARCH, PH_REACT,
+             PH_PERSISTENT, N_PHASES };
+
 struct LaunchCfg {
   int stream_blocks;      // grid of the grid-stride phases (release, diffuse, gather)
   int search_blocks;      // grid of the pair search
@@ -17,13 +21,13 @@ struct LaunchCfg {
 cudaError_t enqueue_begin(const Dev& d, cudaStream_t s);
 cudaError_t enqueue_sort_pass(const Dev& d, int pass, int blocks, cudaStream_t s);
 cudaError_t sort_pass_occupancy(int* blocks_per_sm);
-cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t enqueue_persistent_f64(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s);
 cudaError_t persistent_occupancy_f64(int* blocks_per_sm);
 cudaError_t enqueue_set_t_end(const Dev& d, const double* t_end_dev, cudaStream_t s);
 
 // kernels_f32l.cu (FP32-local mode)
-cudaError_t enqueue_step_f32l(const Dev& d, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t enqueue_step_f32l(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t enqueue_persistent_f32l(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s);
 cudaError_t persistent_occupancy_f32l(int* blocks_per_sm);
 

@@ -846,6 +846,9 @@ __device__ void phase_react(const Dev& d, ReactSmem& sm) {
   }
   __syncthreads();
   if (tid == 0) {
+    bool stepped = false;
+    for (uint32_t b = 0; b < d.n_trains; ++b) stepped |= d.trains[b].active != 0;
+    if (ok && stepped) d.g->steps_active += 1;
     if (ok) {
       d.g->n_products = sm.carry;
       d.g->n_total = n_live + sm.carry;

@@ -100,7 +100,8 @@ struct Global {
   uint32_t tile_ctr[MAX_PASSES];
   uint32_t bar_count, bar_gen;  // grid barrier of the persistent launch
   uint32_t err_where;
-  uint32_t pad_[3];
+  uint32_t steps_active;  // steps in which at least one train advanced
+  uint32_t pad_[2];
 };
 
 // Accepted reactive pair.
