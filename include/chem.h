@@ -224,6 +224,42 @@ chem_status chem_get_stats(const chem_ctx* ctx, chem_stats* out);
  * one event-record node per kernel boundary). on == 0 removes them. Resets phase_ms. */
 chem_status chem_set_profiling(chem_ctx* ctx, int32_t on);
 
+/* ---- allocation-free single step ---------------------------------------------------
+ * The paper has no counterpart to this entry point. It serves callers that cannot let a
+ * library allocate device memory: code running under another framework's memory pool
+ * that owns the whole device, real-time loops that must never allocate, and hosts whose
+ * allocator must not be re-entered from inside a library call. It advances ONE FP64 SBS
+ * step (diffusion, hash and radix sort, pair search, matching, products) of one small
+ * train whose species the caller keeps in its own device buffers, exactly as a context
+ * created by chem_init with dt_min = dt_max = dt_s would take that step.
+ *
+ * Memory: it calls no cudaMalloc, cudaFree or allocator callback. All working memory is
+ * one file-scope __device__ array of about 3.2 MB sized for CHEM_NOALLOC_MAX_SPECIES
+ * species; every GPU that loads this library holds that array until the process exits.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture. Every call on a device shares the array and finds the previous call's
+ * contents there (the call clears what must start empty), so calls that overlap on the
+ * GPU race: issue one at a time per device.
+ *
+ * Arguments: cfg gives the chemistry, box, seed/train_id, cutoff_c and the stream
+ * (cfg->cuda_stream, NULL = legacy default stream); precision must be CHEM_FP64 and the
+ * capacity, allocator and dt-policy fields are ignored. step, t_s, dt_s: the step index
+ * (Philox counter), its start time and length (dt_s must not exceed the L/3 cutoff cap);
+ * next_id: first id for products. Inputs (DEVICE): id[n], type[n], xyz[3n]. Outputs
+ * (DEVICE): id_out/type_out/xyz_out with room for CHEM_NOALLOC_MAX_SPECIES species,
+ * *n_out species after the step, *next_id_out, events_out[CHEM_NOALLOC_MAX_SPECIES/2]
+ * and *n_events_out. Blocks until the step has finished on the stream.
+ * Returns CHEM_ECAPACITY when n exceeds CHEM_NOALLOC_MAX_SPECIES or the step would need
+ * more room than the fixed array has (candidates, products), CHEM_EINVAL for bad
+ * arguments, CHEM_ECUDA when a CUDA call fails. */
+enum { CHEM_NOALLOC_MAX_SPECIES = 16384 };
+chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, double t_s, double dt_s,
+                              uint32_t next_id, int32_t n, const uint32_t* id, const int32_t* type,
+                              const double* xyz, uint32_t* id_out, int32_t* type_out,
+                              double* xyz_out, int32_t* n_out, uint32_t* next_id_out,
+                              chem_event* events_out, int32_t* n_events_out);
+
 /* Library version string. */
 const char* chem_version(void);
 

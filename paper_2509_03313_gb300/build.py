@@ -23,6 +23,7 @@ UNITS = {
     "chem_api.cu": ["--fmad=false"],
     "kernels_exact.cu": ["--fmad=false"],
     "kernels_f32l.cu": [],
+    "noalloc.cu": ["--fmad=false"],
 }
 
 

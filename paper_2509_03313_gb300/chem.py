@@ -82,7 +82,7 @@ EXPORTS = ["chem_init", "chem_inject_pulse", "chem_run_until", "chem_tally", "ch
            "chem_get_events", "chem_get_step_log", "chem_reset", "chem_last_error", "chem_destroy",
            "chem_batch_init", "chem_batch_inject", "chem_batch_run_until", "chem_batch_tally",
            "chem_batch_get_state", "chem_batch_reset", "chem_batch_size", "chem_autotune",
-           "chem_version", "chem_get_stats", "chem_set_profiling"]
+           "chem_version", "chem_get_stats", "chem_set_profiling", "chem_step_noalloc"]
 
 
 class ChemError(RuntimeError):
@@ -119,6 +119,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "chem_version": (ctypes.c_char_p, []),
         "chem_get_stats": (i32, [vp, P(chem_stats)]),
         "chem_set_profiling": (i32, [vp, i32]),
+        "chem_step_noalloc": (i32, [P(chem_config), ctypes.c_uint32, dbl, dbl, ctypes.c_uint32, i32,
+                                    vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -372,6 +374,21 @@ def chem_get_stats(ctx) -> dict:
 
 def chem_set_profiling(ctx, on: bool):
     _check(ctx, lib().chem_set_profiling(ctx, 1 if on else 0))
+
+
+CHEM_NOALLOC_MAX_SPECIES = 16384
+
+
+def chem_step_noalloc(cfg: chem_config, step: int, t_s: float, dt_s: float, next_id: int, n: int,
+                      id_ptr: int, type_ptr: int, xyz_ptr: int, id_out: int, type_out: int,
+                      xyz_out: int, n_out: int, next_id_out: int, events_out: int,
+                      n_events_out: int) -> int:
+    """One FP64 step on caller-owned DEVICE buffers (integer device addresses); returns
+    the chem_status."""
+    vp = ctypes.c_void_p
+    return int(lib().chem_step_noalloc(ctypes.byref(cfg), step, t_s, dt_s, next_id, n, vp(id_ptr),
+                                       vp(type_ptr), vp(xyz_ptr), vp(id_out), vp(type_out), vp(xyz_out),
+                                       vp(n_out), vp(next_id_out), vp(events_out), vp(n_events_out)))
 
 
 def chem_version() -> str:
