@@ -208,7 +208,7 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
   t.key1 = static_cast<uint32_t>(c.seed >> 32) ^ c.train_id;
 }
 
-int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 6 + ctx->d.passes; }
+int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 7 + ctx->d.passes + MAX_PASSES; }
 
 chem_status capture_graph(chem_ctx* ctx) {
   if (ctx->graph) {
@@ -621,6 +621,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
   d.n_trains = static_cast<uint32_t>(n_trains);
   d.total_cells = static_cast<uint32_t>(cells);
   d.sentinel = static_cast<uint32_t>(cells);
+  d.train_bits = bits_for(static_cast<uint64_t>(n_trains - 1));
   d.passes = (bits_for(cells) + 7) / 8;
   if (d.passes < 1) d.passes = 1;
   if (d.passes > MAX_PASSES) {
@@ -640,10 +641,15 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     d.sz = static_cast<double*>(A(cap * 8)); d.stid = static_cast<uint32_t*>(A(cap * 4));
     d.tx = static_cast<double*>(A(cap * 8)); d.ty = static_cast<double*>(A(cap * 8));
     d.tz = static_cast<double*>(A(cap * 8)); d.ttid = static_cast<uint32_t*>(A(cap * 4));
+    d.tdx = static_cast<double*>(A(cap * 8)); d.tdy = static_cast<double*>(A(cap * 8));
+    d.tdz = static_cast<double*>(A(cap * 8));
   } else {
     d.s4 = static_cast<float4*>(A(cap * 16));
     d.t4 = static_cast<float4*>(A(cap * 16));
+    d.td4 = static_cast<float4*>(A(cap * 16));
   }
+  d.cap_items = static_cast<uint32_t>(cap + cap / ITEM_HOME + 64);
+  d.items = static_cast<uint32_t*>(A(static_cast<size_t>(d.cap_items) * 4));
   d.cell_sorted = static_cast<uint32_t*>(A(cap * 4));
   {
     uint32_t* sortbuf = static_cast<uint32_t*>(A(cap * 16));  // keys0|keys1|vals0|vals1

@@ -9,9 +9,12 @@ namespace chem {
 
 union PhaseSmem {
   BeginSmem begin;
+  MatchSmem match;
+  ProductsSmem products;
+  SearchSmem<true> search32;
+  SearchSmem<false> search64;
   uint32_t hist[MAX_PASSES][RADIX];
   SortSmem sort;
-  ReactSmem react;
 };
 
 // Grid-wide barrier of the persistent kernel. The wait is bounded: past the limit the
@@ -62,13 +65,14 @@ __global__ void __launch_bounds__(256) k_gather(const __grid_constant__ Dev d) {
 
 template <bool F32L>
 __global__ void __launch_bounds__(256) k_search(const __grid_constant__ Dev d) {
-  phase_search<F32L>(d);
+  __shared__ SearchSmem<F32L> sm;
+  phase_search<F32L>(d, sm);
 }
 
 template <bool F32L>
-__global__ void __launch_bounds__(REACT_THREADS) k_react(const __grid_constant__ Dev d) {
-  __shared__ ReactSmem sm;
-  phase_react<F32L>(d, sm);
+__global__ void __launch_bounds__(REACT_THREADS) k_products(const __grid_constant__ Dev d) {
+  __shared__ ProductsSmem sm;
+  phase_products<F32L>(d, sm);
 }
 
 template <bool F32L>
@@ -88,9 +92,16 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev 
     }
     phase_gather<F32L>(d);
     grid_sync(d);
-    phase_search<F32L>(d);
+    if constexpr (F32L) phase_search<true>(d, sm.search32);
+    else phase_search<false>(d, sm.search64);
     grid_sync(d);
-    if (blockIdx.x == 0) phase_react<F32L>(d, sm.react);
+    if (blockIdx.x == 0) phase_match(d, sm.match);
+    grid_sync(d);
+    for (int p = 0; p < MAX_PASSES; ++p) {
+      phase_event_sort_pass(d, p, sm.sort);
+      grid_sync(d);
+    }
+    if (blockIdx.x == 0) phase_products<F32L>(d, sm.products);
     grid_sync(d);
   }
 }
@@ -123,7 +134,12 @@ cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cu
   k_search<F32L><<<lc.search_blocks, 256, 0, s>>>(d);
   mark(2 * PH_SEARCH + 1);
   mark(2 * PH_REACT);
-  k_react<F32L><<<1, REACT_THREADS, 0, s>>>(d);
+  enqueue_match(d, s);
+  for (int p = 0; p < MAX_PASSES; ++p) {
+    e = enqueue_event_sort_pass(d, p, lc.sort_blocks, s);
+    if (e != cudaSuccess) return e;
+  }
+  k_products<F32L><<<1, REACT_THREADS, 0, s>>>(d);
   mark(2 * PH_REACT + 1);
   return cudaGetLastError();
 }

@@ -15,6 +15,26 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_pass(const __grid_constan
   phase_sort_pass(d, pass, *reinterpret_cast<SortSmem*>(smem_raw));
 }
 
+__global__ void __launch_bounds__(REACT_THREADS) k_match(const __grid_constant__ Dev d) {
+  __shared__ MatchSmem sm;
+  phase_match(d, sm);
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_event_sort_pass(const __grid_constant__ Dev d, int pass) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  phase_event_sort_pass(d, pass, *reinterpret_cast<SortSmem*>(smem_raw));
+}
+
+cudaError_t enqueue_event_sort_pass(const Dev& d, int pass, int blocks, cudaStream_t s) {
+  k_event_sort_pass<<<blocks, SORT_THREADS, sizeof(SortSmem), s>>>(d, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_match(const Dev& d, cudaStream_t s) {
+  k_match<<<1, REACT_THREADS, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
 __global__ void k_set_t_end(const __grid_constant__ Dev d, const double* t_end) {
   for (uint32_t b = threadIdx.x; b < d.n_trains; b += blockDim.x) d.trains[b].t_end = t_end[b];
 }
@@ -32,6 +52,9 @@ cudaError_t enqueue_sort_pass(const Dev& d, int pass, int blocks, cudaStream_t s
 cudaError_t sort_pass_occupancy(int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sizeof(SortSmem)));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_event_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(sizeof(SortSmem)));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sort_pass, SORT_THREADS,
                                                        sizeof(SortSmem));

@@ -31,7 +31,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(25
 
 // Byte layout of the scratch array.
 struct Layout {
-  size_t sx, sy, sz, stid, tx, ty, tz, ttid, cell_sorted, sortbuf, dead, cell_info, lookback, cand,
+  size_t sx, sy, sz, stid, tx, ty, tz, ttid, tdx, tdy, tdz, items, cell_sorted, sortbuf, dead, cell_info, lookback, cand,
       ev_list, alive0, alive1, ev_k0, ev_k1, ev_v0, ev_v1, ev_log, step_log, pend, trains, tables,
       global, total;
 };
@@ -43,6 +43,8 @@ constexpr Layout make_layout() {
   const size_t M = NA_MAX_SPECIES, C = NA_MAX_CAND;
   L.sx = take(M * 8); L.sy = take(M * 8); L.sz = take(M * 8); L.stid = take(M * 4);
   L.tx = take(M * 8); L.ty = take(M * 8); L.tz = take(M * 8); L.ttid = take(M * 4);
+  L.tdx = take(M * 8); L.tdy = take(M * 8); L.tdz = take(M * 8);
+  L.items = take((M + M / ITEM_HOME + 64) * 4);
   L.cell_sorted = take(M * 4);
   L.sortbuf = take(M * 16);
   L.dead = take(M);
@@ -66,7 +68,7 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = LAYOUT.total;
 
 }  // namespace
 
-// The shared working memory of chem_step_noalloc (about 3.2 MB).
+// The shared working memory of chem_step_noalloc (about 3.5 MB).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -266,6 +268,11 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   d.ty = reinterpret_cast<double*>(b + LAYOUT.ty);
   d.tz = reinterpret_cast<double*>(b + LAYOUT.tz);
   d.ttid = reinterpret_cast<uint32_t*>(b + LAYOUT.ttid);
+  d.tdx = reinterpret_cast<double*>(b + LAYOUT.tdx);
+  d.tdy = reinterpret_cast<double*>(b + LAYOUT.tdy);
+  d.tdz = reinterpret_cast<double*>(b + LAYOUT.tdz);
+  d.items = reinterpret_cast<uint32_t*>(b + LAYOUT.items);
+  d.cap_items = NA_MAX_SPECIES + NA_MAX_SPECIES / ITEM_HOME + 64;
   d.cell_sorted = reinterpret_cast<uint32_t*>(b + LAYOUT.cell_sorted);
   uint32_t* sortbuf = reinterpret_cast<uint32_t*>(b + LAYOUT.sortbuf);
   d.keys0 = sortbuf;

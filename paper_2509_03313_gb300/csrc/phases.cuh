@@ -160,6 +160,8 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
         const double rc = __dadd_rn(tb.R[r], __dmul_rn(tr.c, sqrt(__dmul_rn(__dmul_rn(2.0, tb.D_AB[r]), dt))));
         tr.rc2[r] = __dmul_rn(rc, rc);
         tr.rc2f[r] = static_cast<float>(tr.rc2[r]);
+        tr.ddt[r] = __dmul_rn(tb.D_AB[r], dt);
+        tr.inv_ddt_f[r] = static_cast<float>(__ddiv_rn(1.0, tr.ddt[r]));
         rcmax = fmax(rcmax, rc);
       }
       for (int ty = 0; ty < tb.n_types; ++ty) {
@@ -217,13 +219,18 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     }
     for (int p = 0; p < MAX_PASSES; ++p) g->tile_ctr[p] = 0;
     g->n_cand = 0;
+    g->n_items = 0;
     g->n_events = 0;
     g->n_products = 0;
     g->n_dead = 0;
     g->epoch += 1;
     g->any_active = s_any;
   }
-  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&d.g->hist[0][0])[i] = 0u;
+  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) {
+    (&d.g->hist[0][0])[i] = 0u;
+    (&d.g->ev_hist[0][0])[i] = 0u;
+  }
+  if (threadIdx.x < MAX_PASSES) d.g->ev_tile_ctr[threadIdx.x] = 0u;
   __syncthreads();
 }
 
@@ -332,10 +339,12 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
           double g0, g1, g2;
           gauss3_f64(tid_id(tid), tr.step, tr.key0, tr.key1, g0, g1, g2);
           const double sig = tr.sig[ty];
-          const double x = wrap_box(__dadd_rn(d.sx[s], __dmul_rn(sig, g0)), tr.L, tr.halfL);
-          const double y = wrap_box(__dadd_rn(d.sy[s], __dmul_rn(sig, g1)), tr.L, tr.halfL);
-          const double z = wrap_box(__dadd_rn(d.sz[s], __dmul_rn(sig, g2)), tr.L, tr.halfL);
+          const double ex = __dmul_rn(sig, g0), ey = __dmul_rn(sig, g1), ez = __dmul_rn(sig, g2);
+          const double x = wrap_box(__dadd_rn(d.sx[s], ex), tr.L, tr.halfL);
+          const double y = wrap_box(__dadd_rn(d.sy[s], ey), tr.L, tr.halfL);
+          const double z = wrap_box(__dadd_rn(d.sz[s], ez), tr.L, tr.halfL);
           d.tx[s] = x; d.ty[s] = y; d.tz[s] = z; d.ttid[s] = tid;
+          d.tdx[s] = ex; d.tdy[s] = ey; d.tdz[s] = ez;
           const int n = tr.n;
           const int ix = cell_index(x, tr.halfL, tr.inv_h, n);
           const int iy = cell_index(y, tr.halfL, tr.inv_h, n);
@@ -353,9 +362,11 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
           int ix = static_cast<int>(loc % nr), iy = static_cast<int>((loc / nr) % nr),
               iz = static_cast<int>(loc / (static_cast<uint32_t>(nr) * nr));
           const int n = tr.n;
+          const float ex = sig * g0, ey = sig * g1, ez = sig * g2;
+          d.td4[s] = make_float4(ex, ey, ez, 0.f);
           float ox, oy, oz;
           if (nr == n) {
-            ox = v.x + sig * g0; oy = v.y + sig * g1; oz = v.z + sig * g2;
+            ox = v.x + ex; oy = v.y + ey; oz = v.z + ez;
             const float fx = floorf(ox * tr.inv_hf), fy = floorf(oy * tr.inv_hf), fz = floorf(oz * tr.inv_hf);
             ox -= fx * tr.hf; oy -= fy * tr.hf; oz -= fz * tr.hf;
             ix = wrap_cell(ix + static_cast<int>(fx), n);
@@ -364,9 +375,9 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
           } else {
             // the hash grid changed this step: go through FP64 absolute positions
             const double hr = tr.h_ref;
-            double ax = wrap_box((ix * hr - tr.halfL) + v.x + static_cast<double>(sig * g0), tr.L, tr.halfL);
-            double ay = wrap_box((iy * hr - tr.halfL) + v.y + static_cast<double>(sig * g1), tr.L, tr.halfL);
-            double az = wrap_box((iz * hr - tr.halfL) + v.z + static_cast<double>(sig * g2), tr.L, tr.halfL);
+            double ax = wrap_box((ix * hr - tr.halfL) + v.x + static_cast<double>(ex), tr.L, tr.halfL);
+            double ay = wrap_box((iy * hr - tr.halfL) + v.y + static_cast<double>(ey), tr.L, tr.halfL);
+            double az = wrap_box((iz * hr - tr.halfL) + v.z + static_cast<double>(ez), tr.L, tr.halfL);
             ix = cell_index(ax, tr.halfL, tr.inv_h, n);
             iy = cell_index(ay, tr.halfL, tr.inv_h, n);
             iz = cell_index(az, tr.halfL, tr.inv_h, n);
@@ -403,7 +414,7 @@ static __device__ void phase_sort_pass(const Dev& d, int pass, SortSmem& sm) {
   uint32_t* kout = (pass & 1) ? d.keys0 : d.keys1;
   uint32_t* vout = (pass & 1) ? d.vals0 : d.vals1;
   onesweep_pass(kin, vin, kout, vout, d.g->n_total, 8 * pass, d.g->hist[pass], &d.g->tile_ctr[pass],
-                d.lookback, d.g->epoch * MAX_PASSES + pass, d.g, sm);
+                d.lookback, d.g->epoch * 2 * MAX_PASSES + pass, d.g, sm);
 }
 
 // ======================================================================== gather
@@ -431,8 +442,18 @@ __device__ void phase_gather(const Dev& d) {
     }
     d.cell_sorted[s] = key;
     int* ci = reinterpret_cast<int*>(&d.cell_info[key]);
-    if (s == 0 || kf[s - 1] != key) { ci[0] = static_cast<int>(s); ci[2] = static_cast<int>(epoch); }
+    const bool first = (s == 0 || kf[s - 1] != key);
+    if (first) { ci[0] = static_cast<int>(s); ci[2] = static_cast<int>(epoch); }
     if (s + 1 == n_live || kf[s + 1] != key) ci[1] = static_cast<int>(s + 1);
+    // pair-search work item: a cell's first slot and every ITEM_HOME-th slot
+    if (first || (s % ITEM_HOME) == 0) {
+      const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, key);
+      if (d.trains[b].active && !d.trains[b].free_jump) {
+        const uint32_t it = atomicAdd(&d.g->n_items, 1u);
+        if (it < d.cap_items) d.items[it] = s;
+        else raise_status(d.g, CHEM_ECAPACITY);
+      }
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) d.g->n_live = n_live;
 }
@@ -441,137 +462,266 @@ __device__ void phase_gather(const Dev& d) {
 // For every unordered pair of live species whose types react (Table 1), separated by
 // less than the reaction's cutoff under the minimum image (Eq. 2), evaluate the
 // encounter probability and keep the pair if its uniform falls below it.
+//
+// One warp per work item: up to ITEM_HOME home species of one cell, staged in shared
+// memory. The own cell (slots after the item's first slot) and the 13 forward cells of
+// the half shell are flattened into one neighbour list; lanes stride over it (coalesced
+// loads) and each lane tests its neighbour against every home species (shared-memory
+// broadcast). With at least 3 cells per axis each unordered pair is visited once.
+
+// Half-shell offsets: 0 = own cell, 1..9 dz = +1, 10..12 (dz, dy) = (0, +1), 13 (0, 0, +1).
+__device__ __forceinline__ void fwd_offset(int k, int& dx, int& dy, int& dz) {
+  if (k == 0) { dx = dy = dz = 0; return; }
+  if (k <= 9) { const int q = k - 1; dz = 1; dy = q / 3 - 1; dx = q % 3 - 1; return; }
+  if (k <= 12) { dz = 0; dy = 1; dx = k - 11; return; }
+  dz = 0; dy = 0; dx = 1;
+}
+
 template <bool F32L>
-__device__ void phase_search(const Dev& d) {
+struct SearchWarpSmem;
+
+template <>
+struct SearchWarpSmem<true> {
+  float4 pos[ITEM_HOME];   // offsets + tid bits
+  float4 dl[ITEM_HOME];    // this step's displacement
+};
+
+template <>
+struct SearchWarpSmem<false> {
+  double x[ITEM_HOME], y[ITEM_HOME], z[ITEM_HOME];
+  double ex[ITEM_HOME], ey[ITEM_HOME], ez[ITEM_HOME];
+  uint32_t tid[ITEM_HOME];
+};
+
+template <bool F32L>
+struct SearchSmem {
+  SearchWarpSmem<F32L> w[8];
+};
+
+__device__ __forceinline__ void emit_candidate(const Dev& d, uint32_t s_lo, uint32_t s_hi, uint32_t id_lo,
+                                               uint32_t id_hi, int r, int b, double d1sq) {
+  const uint32_t c = atomicAdd(&d.g->n_cand, 1u);
+  if (c >= d.cap_cand) { raise_status(d.g, CHEM_ECAPACITY); return; }
+  Cand cd;
+  cd.s_lo = s_lo; cd.s_hi = s_hi; cd.id_lo = id_lo; cd.id_hi = id_hi;
+  cd.rxn_train = static_cast<uint32_t>(r) | (static_cast<uint32_t>(b) << 8);
+  cd.pad = 0;
+  cd.d1sq = d1sq;
+  d.cand[c] = cd;
+}
+
+// Accept iff u < p with p evaluated in FP64 from the FP32 squared distances:
+// p = 1 when d0 <= R or d1 <= R, else exp(-(d0 - R)(d1 - R) / (D_AB dt)). An FP32
+// estimate decides whenever it lies farther from u than twice its error bound (FP32
+// rounding of d0, d1, R and of the products, cancellation in d - R, and __expf);
+// otherwise the FP64 value decides, so the outcome is always that of the FP64 test.
+__device__ __forceinline__ bool accept_f32(float d0sq, float d1sq, int r, const Tables& tb, const Train& tr,
+                                          uint32_t id_lo, uint32_t id_hi) {
+  const float d1f = sqrtf(d1sq), d0f = sqrtf(d0sq);
+  const float Rf = tb.Rf[r];
+  const double u = pair_uniform(id_lo, id_hi, tr.step, tr.key0, tr.key1);
+  if (d1f < Rf * 0.999f || d0f < Rf * 0.999f) return true;  // p = 1 > u
+  if (d1f > Rf * 1.001f && d0f > Rf * 1.001f) {
+    const float a = d0f - Rf, b = d1f - Rf, inv = tr.inv_ddt_f[r];
+    const float x = a * b * inv;
+    if (x > 60.f) {
+      if (u != 0.0) return false;  // p < 1e-26 < 2^-53 <= u
+    } else {
+      const float p = __expf(-x);
+      const float err = 1.2e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x);
+      const double band = 2.0 * static_cast<double>(err) * p + 1e-300;
+      if (u > static_cast<double>(p) + band) return false;
+      if (u < static_cast<double>(p) - band) return true;
+    }
+  }
+  const double d0 = sqrt(static_cast<double>(d0sq)), d1 = sqrt(static_cast<double>(d1sq));
+  return u < bridge_p(d0, d1, tb.R[r], tr.ddt[r]);
+}
+
+template <bool F32L>
+__device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
   if (status_of(d)) return;
-  const uint32_t n_live = d.g->n_total - d.g->n_dead;
+  const uint32_t n_items = min(d.g->n_items, d.cap_items);
   const uint32_t epoch = d.g->epoch;
+  const uint32_t* vf = (d.passes & 1) ? d.vals1 : d.vals0;
   const Tables& tb = *d.tables;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_live; s += stride) {
-    const uint32_t cell = d.cell_sorted[s];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint32_t warps_total = gridDim.x * (blockDim.x >> 5);
+  SearchWarpSmem<F32L>& hs = sm.w[wib];
+  for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + wib; it < n_items; it += warps_total) {
+    const uint32_t s0 = d.items[it];
+    const uint32_t cell = d.cell_sorted[s0];
     const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
     const Train& tr = d.trains[b];
-    if (!tr.active || tr.free_jump) continue;
-    uint32_t tid_i;
-    double xi = 0, yi = 0, zi = 0;
-    float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (F32L) { vi = d.s4[s]; tid_i = __float_as_uint(vi.w); }
-    else { xi = d.sx[s]; yi = d.sy[s]; zi = d.sz[s]; tid_i = d.stid[s]; }
-    const uint32_t ti = tid_type(tid_i);
-    const uint32_t rmask = tb.reactive_mask[ti];
-    if (!rmask) continue;
-    const uint32_t id_i = tid_id(tid_i);
+    const int4 ci = d.cell_info[cell];
+    const uint32_t s_end = min(static_cast<uint32_t>(ci.y), (s0 / ITEM_HOME + 1) * ITEM_HOME);
+    const uint32_t nh = s_end - s0;
+    // stage the home species; OR of the types they react with
+    uint32_t want = 0;
+    for (uint32_t h = lane; h < nh; h += 32) {
+      const uint32_t s = s0 + h;
+      const uint32_t ti = vf[s];
+      uint32_t t;
+      if (F32L) {
+        const float4 v = d.s4[s];
+        reinterpret_cast<SearchWarpSmem<true>&>(hs).pos[h] = v;
+        reinterpret_cast<SearchWarpSmem<true>&>(hs).dl[h] = d.td4[ti];
+        t = __float_as_uint(v.w);
+      } else {
+        auto& hd = reinterpret_cast<SearchWarpSmem<false>&>(hs);
+        hd.x[h] = d.sx[s]; hd.y[h] = d.sy[s]; hd.z[h] = d.sz[s];
+        hd.ex[h] = d.tdx[ti]; hd.ey[h] = d.tdy[ti]; hd.ez[h] = d.tdz[ti];
+        t = d.stid[s];
+        hd.tid[h] = t;
+      }
+      want |= tb.reactive_mask[tid_type(t)];
+    }
+    want = __reduce_or_sync(0xffffffffu, want);
+    __syncwarp();
+    if (!want) continue;
+    // neighbour ranges of the half shell
     const int n = tr.n;
     const uint32_t loc = cell - tr.cell_base;
     const int ix = static_cast<int>(loc % n), iy = static_cast<int>((loc / n) % n),
               iz = static_cast<int>(loc / (static_cast<uint32_t>(n) * n));
-    for (int dz = -1; dz <= 1; ++dz) {
-      const int cz = wrap_cell(iz + dz, n);
-      for (int dy = -1; dy <= 1; ++dy) {
-        const int cy = wrap_cell(iy + dy, n);
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int cx = wrap_cell(ix + dx, n);
-          const uint32_t nc = tr.cell_base + static_cast<uint32_t>((cz * n + cy) * n + cx);
-          const int4 ci = d.cell_info[nc];
-          if (static_cast<uint32_t>(ci.z) != epoch) continue;
-          const uint32_t j0 = max(static_cast<uint32_t>(ci.x), s + 1);
-          for (uint32_t j = j0; j < static_cast<uint32_t>(ci.y); ++j) {
-            uint32_t tid_j;
-            double xj = 0, yj = 0, zj = 0;
-            float4 vj;
-            if (F32L) { vj = d.s4[j]; tid_j = __float_as_uint(vj.w); }
-            else { tid_j = d.stid[j]; }
-            const uint32_t tj = tid_type(tid_j);
-            if (!((rmask >> tj) & 1u)) continue;
-            const int r = tb.pair_rxn[ti][tj];
-            const uint32_t id_j = tid_id(tid_j);
-            const bool i_lo = id_i < id_j;
-            double d1sq, rx1, ry1, rz1;
-            if (F32L) {
-              float fx = dx * tr.hf + (vj.x - vi.x);
-              float fy = dy * tr.hf + (vj.y - vi.y);
-              float fz = dz * tr.hf + (vj.z - vi.z);
-              if (!i_lo) { fx = -fx; fy = -fy; fz = -fz; }
-              const float f2 = fx * fx + fy * fy + fz * fz;
-              if (!(f2 < tr.rc2f[r])) continue;
-              d1sq = f2; rx1 = fx; ry1 = fy; rz1 = fz;
-            } else {
-              xj = d.sx[j]; yj = d.sy[j]; zj = d.sz[j];
-              if (i_lo) {
-                rx1 = min_image(__dsub_rn(xj, xi), tr.L, tr.halfL);
-                ry1 = min_image(__dsub_rn(yj, yi), tr.L, tr.halfL);
-                rz1 = min_image(__dsub_rn(zj, zi), tr.L, tr.halfL);
-              } else {
-                rx1 = min_image(__dsub_rn(xi, xj), tr.L, tr.halfL);
-                ry1 = min_image(__dsub_rn(yi, yj), tr.L, tr.halfL);
-                rz1 = min_image(__dsub_rn(zi, zj), tr.L, tr.halfL);
-              }
-              d1sq = sq3(rx1, ry1, rz1);
-              if (!(d1sq < tr.rc2[r])) continue;
-            }
-            const uint32_t id_lo = i_lo ? id_i : id_j, id_hi = i_lo ? id_j : id_i;
-            const uint32_t t_lo = i_lo ? ti : tj, t_hi = i_lo ? tj : ti;
-            // this step's displacements, regenerated from the counter-based stream
-            double r0x, r0y, r0z;
-            if (F32L) {
-              float a0, a1, a2, c0, c1, c2;
-              gauss3_f32(id_lo, tr.step, tr.key0, tr.key1, a0, a1, a2);
-              gauss3_f32(id_hi, tr.step, tr.key0, tr.key1, c0, c1, c2);
-              const float sl = tr.sigf[t_lo];
-              const float sh = tr.sigf[t_hi];
-              r0x = static_cast<float>(rx1) - (sh * c0 - sl * a0);
-              r0y = static_cast<float>(ry1) - (sh * c1 - sl * a1);
-              r0z = static_cast<float>(rz1) - (sh * c2 - sl * a2);
-            } else {
-              double a0, a1, a2, c0, c1, c2;
-              gauss3_f64(id_lo, tr.step, tr.key0, tr.key1, a0, a1, a2);
-              gauss3_f64(id_hi, tr.step, tr.key0, tr.key1, c0, c1, c2);
-              const double sl = tr.sig[t_lo];
-              const double sh = tr.sig[t_hi];
-              r0x = __dsub_rn(rx1, __dsub_rn(__dmul_rn(sh, c0), __dmul_rn(sl, a0)));
-              r0y = __dsub_rn(ry1, __dsub_rn(__dmul_rn(sh, c1), __dmul_rn(sl, a1)));
-              r0z = __dsub_rn(rz1, __dsub_rn(__dmul_rn(sh, c2), __dmul_rn(sl, a2)));
-            }
-            const double d1 = sqrt(d1sq);
-            const double d0 = sqrt(sq3(r0x, r0y, r0z));
-            const double p = bridge_p(d0, d1, tb.R[r], __dmul_rn(tb.D_AB[r], tr.dt));
-            const double u = pair_uniform(id_lo, id_hi, tr.step, tr.key0, tr.key1);
-            if (!(u < p)) continue;
-            const uint32_t c = atomicAdd(&d.g->n_cand, 1u);
-            if (c >= d.cap_cand) { raise_status(d.g, CHEM_ECAPACITY); continue; }
-            Cand cd;
-            cd.s_lo = i_lo ? s : j;
-            cd.s_hi = i_lo ? j : s;
-            cd.id_lo = id_lo;
-            cd.id_hi = id_hi;
-            cd.rxn_train = static_cast<uint32_t>(r) | (static_cast<uint32_t>(b) << 8);
-            cd.pad = 0;
-            cd.d1sq = d1sq;
-            d.cand[c] = cd;
-          }
+    uint32_t rs = 0, rl = 0;
+    if (lane < N_FWD) {
+      if (lane == 0) {
+        rs = s0 + 1;
+        rl = static_cast<uint32_t>(ci.y) - rs;
+      } else {
+        int ox, oy, oz;
+        fwd_offset(lane, ox, oy, oz);
+        const uint32_t nc = tr.cell_base + static_cast<uint32_t>(
+            (wrap_cell(iz + oz, n) * n + wrap_cell(iy + oy, n)) * n + wrap_cell(ix + ox, n));
+        const int4 nci = d.cell_info[nc];
+        if (static_cast<uint32_t>(nci.z) == epoch) {
+          rs = static_cast<uint32_t>(nci.x);
+          rl = static_cast<uint32_t>(nci.y - nci.x);
         }
       }
     }
+    uint32_t incl = rl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t excl = incl - rl;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, N_FWD - 1);
+    uint32_t ex_k[N_FWD];
+#pragma unroll
+    for (int q = 0; q < N_FWD; ++q) ex_k[q] = __shfl_sync(0xffffffffu, excl, q);
+    for (uint32_t f0 = 0; f0 < total; f0 += 32) {
+      const uint32_t f = f0 + lane;
+      const bool valid = f < total;
+      int k = 0;
+#pragma unroll
+      for (int q = 1; q < N_FWD; ++q) k += (ex_k[q] <= f) ? 1 : 0;
+      const uint32_t j_start = __shfl_sync(0xffffffffu, rs, k);
+      const uint32_t j_off = __shfl_sync(0xffffffffu, excl, k);
+      if (!valid) continue;
+      const uint32_t j = j_start + (f - j_off);
+      int odx, ody, odz;
+      fwd_offset(k, odx, ody, odz);
+      uint32_t tid_j;
+      float4 vj = make_float4(0.f, 0.f, 0.f, 0.f);
+      double xj = 0, yj = 0, zj = 0;
+      if (F32L) { vj = d.s4[j]; tid_j = __float_as_uint(vj.w); }
+      else { tid_j = d.stid[j]; }
+      const uint32_t tj = tid_type(tid_j);
+      if (!((want >> tj) & 1u)) continue;
+      if (!F32L) { xj = d.sx[j]; yj = d.sy[j]; zj = d.sz[j]; }
+      const uint32_t id_j = tid_id(tid_j);
+      const uint32_t jmask = tb.reactive_mask[tj];
+      const float cx = odx * tr.hf, cy = ody * tr.hf, cz = odz * tr.hf;
+      for (uint32_t h = 0; h < nh; ++h) {
+        if (k == 0 && j <= s0 + h) break;  // own cell: only later slots (slots ascend with h)
+        uint32_t tid_i;
+        if (F32L) tid_i = __float_as_uint(reinterpret_cast<SearchWarpSmem<true>&>(hs).pos[h].w);
+        else tid_i = reinterpret_cast<SearchWarpSmem<false>&>(hs).tid[h];
+        const uint32_t ti = tid_type(tid_i);
+        if (!((jmask >> ti) & 1u)) continue;
+        const int r = tb.pair_rxn[ti][tj];
+        const uint32_t id_i = tid_id(tid_i);
+        const bool i_lo = id_i < id_j;
+        if (F32L) {
+          const SearchWarpSmem<true>& hf = reinterpret_cast<const SearchWarpSmem<true>&>(hs);
+          const float4 vi = hf.pos[h];
+          float fx = cx + (vj.x - vi.x), fy = cy + (vj.y - vi.y), fz = cz + (vj.z - vi.z);
+          const float f2 = fx * fx + fy * fy + fz * fz;
+          if (!(f2 < tr.rc2f[r])) continue;
+          if (!i_lo) { fx = -fx; fy = -fy; fz = -fz; }
+          const float4 di = hf.dl[h];
+          const float4 dj = d.td4[vf[j]];
+          const float4 dlo = i_lo ? di : dj, dhi = i_lo ? dj : di;
+          const float r0x = fx - (dhi.x - dlo.x), r0y = fy - (dhi.y - dlo.y), r0z = fz - (dhi.z - dlo.z);
+          const float d0sq = r0x * r0x + r0y * r0y + r0z * r0z;
+          const uint32_t id_lo = i_lo ? id_i : id_j, id_hi = i_lo ? id_j : id_i;
+          if (!accept_f32(d0sq, f2, r, tb, tr, id_lo, id_hi)) continue;
+          const uint32_t si = s0 + h;
+          emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, static_cast<double>(f2));
+        } else {
+          const SearchWarpSmem<false>& hd = reinterpret_cast<const SearchWarpSmem<false>&>(hs);
+          const double xi = hd.x[h], yi = hd.y[h], zi = hd.z[h];
+          double rx1, ry1, rz1;
+          if (i_lo) {
+            rx1 = min_image(__dsub_rn(xj, xi), tr.L, tr.halfL);
+            ry1 = min_image(__dsub_rn(yj, yi), tr.L, tr.halfL);
+            rz1 = min_image(__dsub_rn(zj, zi), tr.L, tr.halfL);
+          } else {
+            rx1 = min_image(__dsub_rn(xi, xj), tr.L, tr.halfL);
+            ry1 = min_image(__dsub_rn(yi, yj), tr.L, tr.halfL);
+            rz1 = min_image(__dsub_rn(zi, zj), tr.L, tr.halfL);
+          }
+          const double d1sq = sq3(rx1, ry1, rz1);
+          if (!(d1sq < tr.rc2[r])) continue;
+          const uint32_t tj_idx = vf[j];
+          const double ejx = d.tdx[tj_idx], ejy = d.tdy[tj_idx], ejz = d.tdz[tj_idx];
+          const double elx = i_lo ? hd.ex[h] : ejx, ely = i_lo ? hd.ey[h] : ejy, elz = i_lo ? hd.ez[h] : ejz;
+          const double ehx = i_lo ? ejx : hd.ex[h], ehy = i_lo ? ejy : hd.ey[h], ehz = i_lo ? ejz : hd.ez[h];
+          const double r0x = __dsub_rn(rx1, __dsub_rn(ehx, elx));
+          const double r0y = __dsub_rn(ry1, __dsub_rn(ehy, ely));
+          const double r0z = __dsub_rn(rz1, __dsub_rn(ehz, elz));
+          const double d1 = sqrt(d1sq);
+          const double d0 = sqrt(sq3(r0x, r0y, r0z));
+          const uint32_t id_lo = i_lo ? id_i : id_j, id_hi = i_lo ? id_j : id_i;
+          const double p = bridge_p(d0, d1, tb.R[r], tr.ddt[r]);
+          const double u = pair_uniform(id_lo, id_hi, tr.step, tr.key0, tr.key1);
+          if (!(u < p)) continue;
+          const uint32_t si = s0 + h;
+          emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, d1sq);
+        }
+      }
+    }
+    __syncwarp();
   }
 }
 
 // ======================================================================== react
-// One CTA of REACT_THREADS threads.
-//  1. matching: rounds of locally-dominant selection; a pair is committed when it is the
-//     smallest (d1^2, id_lo, id_hi) remaining pair of both its species. This equals the
-//     greedy walk over pairs sorted by that key (closest first, lower ids first).
-//  2. events ordered by (train, id_lo); product ids assigned in that order.
-//  3. products written at the diffusion-weighted encounter point; tallies; logs.
-//  4. end of step per train: FP64 clock, step counter, dt growth, step record.
-struct ReactSmem {
-  uint32_t n_alive, n_next, n_ev, carry;
+// One reaction per species (Sec. 2.3: reactants react on encounter), in three phases:
+//  1. phase_match (one CTA): rounds of locally-dominant selection; a pair is committed
+//     when it is the smallest (d1^2, id_lo, id_hi) remaining pair of both its species,
+//     which equals the greedy walk over pairs sorted by that key (closest first, lower
+//     ids first). Emits every event with its key (train, id_lo) and digit histograms.
+//  2. the event keys are ordered by the Onesweep passes (all CTAs);
+//  3. phase_products (one CTA): product ids in (train, id_lo) order, products at the
+//     diffusion-weighted encounter point (Table 1 right-hand sides), tallies summed in
+//     shared memory, logs, and the end of the step (FP64 clock, step counter, dt growth).
+struct MatchSmem {
+  uint32_t n_alive, n_next, n_ev;
+  uint32_t hist[MAX_PASSES][RADIX];
+};
+
+struct ProductsSmem {
+  uint32_t carry, any;
+  uint32_t warp_tot[REACT_THREADS / 32];
   uint32_t first_pref[MAX_TRAINS];
   uint32_t prods_tr[MAX_TRAINS];
   uint32_t evs_tr[MAX_TRAINS];
-  uint32_t warp_tot[REACT_THREADS / 32];
-  unsigned long long small_keys[REACT_THREADS];
-  uint32_t any;
+  int dcount[MAX_TRAINS][MAXT];
+  int devents[MAX_TRAINS][MAXR];
+  int dwater[MAX_TRAINS];
 };
 
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_tot,
@@ -595,27 +745,25 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_t
   return x - v + add;
 }
 
-__device__ __forceinline__ unsigned long long ev_key(const Dev& d, uint32_t c) {
-  const Cand& cd = d.cand[c];
-  return (static_cast<unsigned long long>(cd.rxn_train >> 8) << 32) | cd.id_lo;
+__device__ __forceinline__ uint32_t event_key(const Dev& d, const Cand& cd) {
+  const uint32_t b = cd.rxn_train >> 8;
+  return d.train_bits ? ((b << (32 - d.train_bits)) | cd.id_lo) : cd.id_lo;
 }
 
-template <bool F32L>
-__device__ void phase_react(const Dev& d, ReactSmem& sm) {
+static __device__ void phase_match(const Dev& d, MatchSmem& sm) {
   const int tid = threadIdx.x;
   const int nt = blockDim.x;
   const bool ok = status_of(d) == 0;
-  const Tables& tb = *d.tables;
   unsigned long long* bd = reinterpret_cast<unsigned long long*>(d.keys0);
   unsigned long long* bp = bd + d.cap;
   uint32_t n_c = min(d.g->n_cand, d.cap_cand);
   if (!ok) n_c = 0;
-  if (tid == 0) { sm.n_alive = n_c; sm.n_ev = 0; sm.any = 0; }
+  if (tid == 0) { sm.n_alive = n_c; sm.n_ev = 0; }
+  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&sm.hist[0][0])[i] = 0u;
   for (uint32_t i = tid; i < n_c; i += nt) d.alive0[i] = i;
   __syncthreads();
   uint32_t* alive = d.alive0;
   uint32_t* nxt = d.alive1;
-  // ---- 1. matching rounds (each round commits at least the smallest remaining pair)
   for (uint32_t round = 0; sm.n_alive > 0; ++round) {
     if (round > n_c) {
       if (tid == 0) raise_status(d.g, CHEM_ESTATE);
@@ -651,7 +799,12 @@ __device__ void phase_react(const Dev& d, ReactSmem& sm) {
       if (bd[cd.s_lo] == kd && bp[cd.s_lo] == kp && bd[cd.s_hi] == kd && bp[cd.s_hi] == kp) {
         d.dead[cd.s_lo] = 1;
         d.dead[cd.s_hi] = 1;
-        d.ev_list[atomicAdd(&sm.n_ev, 1u)] = c;
+        const uint32_t e = atomicAdd(&sm.n_ev, 1u);
+        const uint32_t key = event_key(d, cd);
+        d.ev_k0[e] = key;
+        d.ev_v0[e] = c;
+#pragma unroll
+        for (int p = 0; p < MAX_PASSES; ++p) atomicAdd(&sm.hist[p][(key >> (8 * p)) & 255u], 1u);
       }
     }
     if (tid == 0) sm.n_next = 0;
@@ -666,64 +819,37 @@ __device__ void phase_react(const Dev& d, ReactSmem& sm) {
     uint32_t* tmp = alive; alive = nxt; nxt = tmp;
     __syncthreads();
   }
-  // ---- 2. order events by (train, id_lo); keys are unique
-  const uint32_t E = sm.n_ev;
-  uint32_t* order;  // order[k] = candidate index of the k-th event
-  if (E <= static_cast<uint32_t>(nt)) {
-    if (static_cast<uint32_t>(tid) < E) sm.small_keys[tid] = ev_key(d, d.ev_list[tid]);
-    __syncthreads();
-    uint32_t rank = 0;
-    if (static_cast<uint32_t>(tid) < E) {
-      const unsigned long long k = sm.small_keys[tid];
-      for (uint32_t q = 0; q < E; ++q) rank += (sm.small_keys[q] < k);
-    }
-    __syncthreads();
-    if (static_cast<uint32_t>(tid) < E) d.ev_v1[rank] = d.ev_list[tid];
-    order = d.ev_v1;
-  } else {
-    // LSD radix over the 64-bit key (train | id_lo), 8 bits per pass, stable per pass:
-    // each pass walks the events in tiles of blockDim, ranking within a tile by
-    // counting equal digits at lower positions, with running digit offsets.
-    uint32_t* ord_in = d.ev_v0;
-    uint32_t* ord_out = d.ev_v1;
-    for (uint32_t i = tid; i < E; i += nt) ord_in[i] = d.ev_list[i];
-    __syncthreads();
-    uint32_t* digit_base = d.ev_k0;  // [256] scratch
-    uint32_t* digit_run = d.ev_k1;   // [256]
-    int top_bit = 32 + 8;            // trains < 256
-    for (int shift = 0; shift < top_bit; shift += 8) {
-      for (int i = tid; i < RADIX; i += nt) digit_base[i] = 0;
-      __syncthreads();
-      for (uint32_t i = tid; i < E; i += nt)
-        atomicAdd(&digit_base[(ev_key(d, ord_in[i]) >> shift) & 255u], 1u);
-      __syncthreads();
-      if (tid == 0) {
-        uint32_t s = 0;
-        for (int q = 0; q < RADIX; ++q) { const uint32_t c = digit_base[q]; digit_run[q] = s; s += c; }
-      }
-      __syncthreads();
-      for (uint32_t t0 = 0; t0 < E; t0 += nt) {
-        const uint32_t i = t0 + tid;
-        const bool valid = i < E;
-        const uint32_t dg = valid ? static_cast<uint32_t>((ev_key(d, ord_in[i]) >> shift) & 255u) : 0u;
-        if (valid) sm.small_keys[tid] = dg;
-        __syncthreads();
-        uint32_t rk = 0;
-        if (valid) for (int q = 0; q < tid; ++q) rk += (sm.small_keys[q] == dg);
-        if (valid) ord_out[digit_run[dg] + rk] = ord_in[i];
-        __syncthreads();
-        if (valid) atomicAdd(&digit_run[dg], 1u);
-        __syncthreads();
-      }
-      uint32_t* t = ord_in; ord_in = ord_out; ord_out = t;
-      __syncthreads();
-    }
-    order = ord_in;
-  }
+  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&d.g->ev_hist[0][0])[i] = (&sm.hist[0][0])[i];
+  if (tid == 0) d.g->n_events = sm.n_ev;
   __syncthreads();
-  // ---- 3. products: exclusive prefix of product counts in event order
-  for (uint32_t b = tid; b < d.n_trains; b += nt) { sm.first_pref[b] = 0xFFFFFFFFu; sm.prods_tr[b] = 0; sm.evs_tr[b] = 0; }
-  if (tid == 0) sm.carry = 0;
+}
+
+// One Onesweep pass over the event keys (ev_k0/ev_v0 -> ev_k1/ev_v1 and back).
+static __device__ void phase_event_sort_pass(const Dev& d, int pass, SortSmem& sm) {
+  if (status_of(d)) return;
+  const uint32_t* kin = (pass & 1) ? d.ev_k1 : d.ev_k0;
+  const uint32_t* vin = (pass & 1) ? d.ev_v1 : d.ev_v0;
+  uint32_t* kout = (pass & 1) ? d.ev_k0 : d.ev_k1;
+  uint32_t* vout = (pass & 1) ? d.ev_v0 : d.ev_v1;
+  onesweep_pass(kin, vin, kout, vout, d.g->n_events, 8 * pass, d.g->ev_hist[pass],
+                &d.g->ev_tile_ctr[pass], d.lookback, d.g->epoch * 2 * MAX_PASSES + MAX_PASSES + pass,
+                d.g, sm);
+}
+
+template <bool F32L>
+__device__ void phase_products(const Dev& d, ProductsSmem& sm) {
+  const int tid = threadIdx.x;
+  const int nt = blockDim.x;
+  const bool ok = status_of(d) == 0;
+  const Tables& tb = *d.tables;
+  const uint32_t E = ok ? d.g->n_events : 0u;
+  const uint32_t* order = d.ev_v0;  // after an even number of passes
+  for (uint32_t b = tid; b < d.n_trains; b += nt) {
+    sm.first_pref[b] = 0xFFFFFFFFu; sm.prods_tr[b] = 0; sm.evs_tr[b] = 0; sm.dwater[b] = 0;
+    for (int q = 0; q < MAXT; ++q) sm.dcount[b][q] = 0;
+    for (int q = 0; q < MAXR; ++q) sm.devents[b][q] = 0;
+  }
+  if (tid == 0) { sm.carry = 0; sm.any = 0; }
   __syncthreads();
   const uint32_t n_live = d.g->n_total - d.g->n_dead;
   for (uint32_t t0 = 0; t0 < E; t0 += nt) {
@@ -792,12 +918,11 @@ __device__ void phase_react(const Dev& d, ReactSmem& sm) {
             d.dead[slot0 + q] = 0;
           }
         }
-        atomicAdd(reinterpret_cast<unsigned long long*>(&tr.counts[tlo]), static_cast<unsigned long long>(-1ll));
-        atomicAdd(reinterpret_cast<unsigned long long*>(&tr.counts[thi]), static_cast<unsigned long long>(-1ll));
-        for (uint32_t q = 0; q < np; ++q)
-          atomicAdd(reinterpret_cast<unsigned long long*>(&tr.counts[tb.prod[r][q]]), 1ull);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&tr.events[r]), 1ull);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&tr.water), static_cast<unsigned long long>(static_cast<long long>(tb.water[r])));
+        atomicSub(&sm.dcount[b][tlo], 1);
+        atomicSub(&sm.dcount[b][thi], 1);
+        for (uint32_t q = 0; q < np; ++q) atomicAdd(&sm.dcount[b][tb.prod[r][q]], 1);
+        atomicAdd(&sm.devents[b][r], 1);
+        if (tb.water[r]) atomicAdd(&sm.dwater[b], tb.water[r]);
         atomicAdd(&sm.prods_tr[b], np);
         atomicAdd(&sm.evs_tr[b], 1u);
         if (d.cap_ev_log) {
@@ -817,10 +942,13 @@ __device__ void phase_react(const Dev& d, ReactSmem& sm) {
     if (tid == 0) sm.carry += tot;
     __syncthreads();
   }
-  // ---- 4. end of step
+  // end of step
   for (uint32_t b = tid; b < d.n_trains; b += nt) {
     Train& tr = d.trains[b];
     if (tr.active && ok) {
+      for (int q = 0; q < tb.n_types; ++q) tr.counts[q] += sm.dcount[b][q];
+      for (int q = 0; q < tb.n_rxn; ++q) tr.events[q] += sm.devents[b][q];
+      tr.water += sm.dwater[b];
       tr.next_id += sm.prods_tr[b];
       tr.n_events_step = sm.evs_tr[b];
       tr.species_steps += tr.n_live_step;
@@ -852,7 +980,6 @@ __device__ void phase_react(const Dev& d, ReactSmem& sm) {
     if (ok) {
       d.g->n_products = sm.carry;
       d.g->n_total = n_live + sm.carry;
-      d.g->n_events = E;
       if (d.cap_ev_log) d.g->ev_log_n += E;
     }
     d.g->any_active = sm.any;

@@ -28,6 +28,8 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 15;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 3840 keys per tile
 constexpr int REACT_THREADS = 1024;
+constexpr int ITEM_HOME = 64;   // home species per pair-search work item (one cell)
+constexpr int N_FWD = 14;       // own cell + 13 forward neighbour cells (half shell)
 constexpr double END_SLACK = 1.0 + 1e-6;    // last-step trim slack (relative)
 constexpr double CELL_SLACK = 1.0 + 1e-6;   // hash cell >= cutoff * CELL_SLACK
 constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
@@ -79,6 +81,8 @@ struct Train {
   float rc2f[MAXR];
   double sig[MAXT];        // sqrt(2 D dt) per type
   float sigf[MAXT];
+  double ddt[MAXR];        // D_AB dt per reaction (bridge denominator)
+  float inv_ddt_f[MAXR];   // 1 / (D_AB dt) in FP32 (first tier of the acceptance test)
   uint32_t rel_n, rel_off, rel_id0, rel_p0;
   long long n_live_step;
   uint32_t n_events_step;
@@ -101,7 +105,10 @@ struct Global {
   uint32_t bar_count, bar_gen;  // grid barrier of the persistent launch
   uint32_t err_where;
   uint32_t steps_active;  // steps in which at least one train advanced
-  uint32_t pad_[2];
+  uint32_t n_items;       // pair-search work items emitted by the gather
+  uint32_t ev_tile_ctr[MAX_PASSES];
+  uint32_t ev_hist[MAX_PASSES][RADIX];  // digit histograms of the event keys
+  uint32_t pad_[1];
 };
 
 // Accepted reactive pair.
@@ -118,9 +125,14 @@ struct Dev {
   uint32_t cap, cap_cand, cap_ev_log, cap_step_log, cap_pend;
   uint32_t n_trains, total_cells, sentinel;
   int passes, precision;
+  int train_bits;        // bits of (n_trains - 1): event key = train << (32 - bits) | id_lo
   double* sx; double* sy; double* sz; uint32_t* stid;
   double* tx; double* ty; double* tz; uint32_t* ttid;
   float4* s4; float4* t4;
+  double* tdx; double* tdy; double* tdz;  // FP64 displacement of this step, T order
+  float4* td4;                            // FP32-local displacement of this step, T order
+  uint32_t* items;                        // pair-search work items (first home slot)
+  uint32_t cap_items;
   uint32_t* cell_sorted;
   uint32_t* keys0; uint32_t* keys1; uint32_t* vals0; uint32_t* vals1;
   uint8_t* dead;
