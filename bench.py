@@ -205,7 +205,7 @@ def run_gpu_arm(args):
                "sample": f"{n_proc} processes x first {args.cpu_steps} SBS steps (1 ps onwards) of "
                          f"independent {args.species}-species trajectories; {busy:.1f} s"}
     seed0 = 10_000 * (rank + 1)
-    wl = W.single_pulse_tracks(seed0, n_species=args.species)
+    wl = W.single_pulse_tracks(seed0, n_species=args.species, n_tracks=args.tracks)
     pulse = wl.pulses[0]
     cap = int(pulse.n * 1.3) + 4096
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -276,6 +276,7 @@ def run_gpu_arm(args):
     # roofline of the dominant phase kernel of the FP32-local run
     phases = r["phases"]
     dom = max(phases, key=lambda p: phases[p]["ms_total"])
+    have_phases = phases[dom]["ms_total"] > 0.0
     sb = STATE_BYTES["fp32l"]
     dom_bytes = PHASE_BYTES[dom](sb) * r["ss"] * (1 if dom != "sort" else 1)
     n_launch = max(1, phases[dom]["launches"])
@@ -298,7 +299,7 @@ def run_gpu_arm(args):
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
                 "includes": "chem_reset + chem_inject_pulse (host arrays) + chem_run_until + chem_tally"},
         "gpu_launches": int(r["launches"]),
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+        "roofline": None if not have_phases else {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "peak_source": peak_src,
                      "algorithmic_bytes": f"{PHASE_BYTES[dom](sb)} B per species per launch",
@@ -334,6 +335,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--species", type=int, default=1_000_000)
+    ap.add_argument("--tracks", type=int, default=200,
+                    help="number of tracks (species per track = species / tracks)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--ref-procs", type=int, default=0)

@@ -234,7 +234,7 @@ chem_status chem_set_profiling(chem_ctx* ctx, int32_t on);
  * created by chem_init with dt_min = dt_max = dt_s would take that step.
  *
  * Memory: it calls no cudaMalloc, cudaFree or allocator callback. All working memory is
- * one file-scope __device__ array of about 3.5 MB sized for CHEM_NOALLOC_MAX_SPECIES
+ * one file-scope __device__ array of about 3.6 MB sized for CHEM_NOALLOC_MAX_SPECIES
  * species; every GPU that loads this library holds that array until the process exits.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any

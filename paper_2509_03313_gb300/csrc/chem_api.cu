@@ -52,7 +52,8 @@ struct chem_ctx {
   int graph_steps = 0;
   int steps_per_launch = 16;
   bool persistent = false;
-  int cell_factor_x100 = 400;  // hash cells per species budget (x100)
+  int cell_factor_x100 = 1600;  // hash cells per species (x100) of the runtime grid limit
+  int item_home = ITEM_HOME;     // home species per pair-search work item
   Global* g_pinned = nullptr;  // host copy of the global counters
   double* t_end_pinned = nullptr;
   double* t_end_dev = nullptr;
@@ -180,6 +181,14 @@ chem_status download_trains(chem_ctx* ctx, std::vector<Train>& h) {
   return CHEM_OK;
 }
 
+chem_status init_global(chem_ctx* ctx) {
+  CK(cudaMemsetAsync(ctx->d.g, 0, sizeof(Global), ctx->stream));
+  const uint32_t ih = static_cast<uint32_t>(ctx->item_home);
+  CK(cudaMemcpyAsync(&ctx->d.g->item_home, &ih, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return CHEM_OK;
+}
+
 chem_status download_global(chem_ctx* ctx) {
   ctx->stats.bytes_d2h += sizeof(Global);
   CK(cudaMemcpyAsync(ctx->g_pinned, ctx->d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
@@ -200,15 +209,16 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
   t.water = 0;
   for (int i = 0; i < MAXT; ++i) t.counts[i] = 0;
   for (int i = 0; i < MAXR; ++i) t.events[i] = 0;
-  t.n_ref = n_max;
-  t.h_ref = c.L_nm / n_max;
+  (void)n_max;
+  t.n_ref = 0;  // chosen by the first step
+  t.h_ref = 0.0;
   t.active = 0;
   t.free_jump = 0;
   t.key0 = static_cast<uint32_t>(c.seed & 0xFFFFFFFFull);
   t.key1 = static_cast<uint32_t>(c.seed >> 32) ^ c.train_id;
 }
 
-int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 7 + ctx->d.passes + MAX_PASSES; }
+int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 10 + ctx->d.passes + MAX_PASSES; }
 
 chem_status capture_graph(chem_ctx* ctx) {
   if (ctx->graph) {
@@ -425,10 +435,10 @@ chem_status state_one(chem_ctx* ctx, int b, int64_t cap, int32_t* type, uint32_t
     } else {
       std::memcpy(&tt, &v4[i].w, 4);
       const uint32_t loc = cell[i] - t.cell_base;
-      const uint32_t nr = static_cast<uint32_t>(t.n_ref);
+      const uint32_t m = (1u << t.cb) - 1u;
       const double h = t.h_ref;
-      const int ix = static_cast<int>(loc % nr), iy = static_cast<int>((loc / nr) % nr),
-                iz = static_cast<int>(loc / (nr * nr));
+      const int ix = static_cast<int>(loc & m), iy = static_cast<int>((loc >> t.cb) & m),
+                iz = static_cast<int>(loc >> (2 * t.cb));
       auto wrapb = [&](double q) {
         q -= t.L * std::floor((q + t.halfL) / t.L);
         if (q >= t.halfL) q -= t.L;
@@ -547,30 +557,37 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
       }
     }
     t.dt_L = dt_L;
-    int n_max = c.cells_per_axis_max;
-    if (n_max <= 0) {
-      const double budget = static_cast<double>(c.capacity_species) * ctx->cell_factor_x100 / 100.0;
-      n_max = static_cast<int>(std::floor(std::cbrt(budget)));
-      n_max = std::max(3, std::min(n_max, 256));
+    // hash resolution: the table is allocated for n_alloc cells per axis; the runtime
+    // limit n_max (<= n_alloc) is what the autotuner varies
+    int n_alloc = c.cells_per_axis_max, n_max = c.cells_per_axis_max;
+    if (n_alloc <= 0) {
+      const double cap_sp = static_cast<double>(c.capacity_species);
+      n_alloc = static_cast<int>(std::floor(std::cbrt(cap_sp * 64.0)));
+      n_alloc = std::max(3, std::min(n_alloc, 512));
+      n_max = static_cast<int>(std::floor(std::cbrt(cap_sp * ctx->cell_factor_x100 / 100.0)));
+      n_max = std::max(3, std::min(n_max, n_alloc));
     }
-    if (n_max < 3 || n_max > 1024) {
+    if (n_alloc < 3 || n_alloc > 1024) {
       delete ctx;
       return CHEM_EINVAL;
     }
     t.n_max = n_max;
+    t.n_alloc = n_alloc;
+    t.cb = bits_for(static_cast<uint64_t>(n_alloc - 1));
+    t.inv_L = 1.0 / c.L_nm;
     t.cell_base = static_cast<uint32_t>(cells);
-    cells += static_cast<uint64_t>(n_max) * n_max * n_max;
+    cells += 1ull << (3 * t.cb);
     t.pend_base = static_cast<uint32_t>(pend);
     t.pend_cap = static_cast<uint32_t>(c.capacity_pending);
     pend += static_cast<uint64_t>(c.capacity_pending);
     t.id_limit = (tbits + 29 <= 32) ? (1u << 29) - 1u : (1u << (32 - tbits)) - 1u;
-    init_train_dynamic(t, c, n_max);
+    init_train_dynamic(t, c, n_alloc);
     cap += static_cast<uint64_t>(c.capacity_species);
     cand += static_cast<uint64_t>(c.capacity_candidates);
     evlog += static_cast<uint64_t>(c.capacity_event_log);
     steplog += static_cast<uint64_t>(c.capacity_step_log);
   }
-  if (cap >= (1ull << 31) || cells >= (1ull << 31) || pend >= (1ull << 31) || cand >= (1ull << 31)) {
+  if (cap >= (1ull << 31) || cells >= (1ull << 32) - 2 || pend >= (1ull << 31) || cand >= (1ull << 24)) {
     delete ctx;
     return CHEM_EINVAL;
   }
@@ -607,7 +624,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     return fail(ctx, CHEM_ECUDA, "step kernel not loadable: %s", cudaGetErrorString(pe));
   }
   ctx->lc.stream_blocks = ctx->sms * 4;
-  ctx->lc.search_blocks = ctx->sms * 8;
+  ctx->lc.search_blocks = ctx->sms * 4;  // resident CTAs (launch bounds 256 x 4); items are stolen
   ctx->lc.sort_blocks = ctx->sms * sort_occ;
   ctx->lc.persistent_blocks = ctx->sms * pers_occ;
 
@@ -659,6 +676,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     d.vals1 = sortbuf + 3 * cap;
   }
   d.dead = static_cast<uint8_t*>(A(cap));
+  d.touch = static_cast<uint32_t*>(A(cap * 4));
   d.cell_info = static_cast<int4*>(A((cells + 1) * 16));
   d.lookback = static_cast<unsigned long long*>(A(static_cast<size_t>(d.max_tiles) * RADIX * 8));
   d.cand = static_cast<Cand*>(A(cand * sizeof(Cand)));
@@ -690,10 +708,12 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
   ctx->t_end_dev = static_cast<double*>(A(sizeof(double) * n_trains));
   if (!ok) return fail(ctx, CHEM_ENOMEM, "device allocation failed");
   CK(cudaMemsetAsync(d.dead, 0, cap, ctx->stream));
+  CK(cudaMemsetAsync(d.touch, 0, cap * 4, ctx->stream));
   CK(cudaMemsetAsync(d.cell_info, 0xFF, (cells + 1) * 16, ctx->stream));
   CK(cudaMemsetAsync(d.lookback, 0, static_cast<size_t>(d.max_tiles) * RADIX * 8, ctx->stream));
-  CK(cudaMemsetAsync(d.g, 0, sizeof(Global), ctx->stream));
   CK(cudaMemcpyAsync(tables_dev, &T, sizeof(Tables), cudaMemcpyHostToDevice, ctx->stream));
+  chem_status gs = init_global(ctx);
+  if (gs) return gs;
   return upload_trains(ctx, tr);
 }
 
@@ -785,10 +805,12 @@ chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds) {
     if (seeds) h.cfg.seed = seeds[b];
     h.E_dep = 0.0;
     h.pend = PendingHost();
-    init_train_dynamic(tr[b], h.cfg, tr[b].n_max);
+    init_train_dynamic(tr[b], h.cfg, tr[b].n_alloc);
   }
-  CK(cudaMemsetAsync(ctx->d.g, 0, sizeof(Global), ctx->stream));
+  s = init_global(ctx);
+  if (s) return s;
   CK(cudaMemsetAsync(ctx->d.dead, 0, ctx->d.cap, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d.touch, 0, static_cast<size_t>(ctx->d.cap) * 4, ctx->stream));
   CK(cudaMemsetAsync(ctx->d.cell_info, 0xFF, (static_cast<size_t>(ctx->d.total_cells) + 1) * 16, ctx->stream));
   CK(cudaMemsetAsync(ctx->d.lookback, 0, static_cast<size_t>(ctx->d.max_tiles) * RADIX * 8, ctx->stream));
   s = upload_trains(ctx, tr);

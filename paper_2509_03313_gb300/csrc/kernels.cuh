@@ -10,7 +10,9 @@ namespace chem {
 union PhaseSmem {
   BeginSmem begin;
   MatchSmem match;
+  ScanSmem scan;
   ProductsSmem products;
+  EndSmem end;
   SearchSmem<true> search32;
   SearchSmem<false> search64;
   uint32_t hist[MAX_PASSES][RADIX];
@@ -64,13 +66,13 @@ __global__ void __launch_bounds__(256) k_gather(const __grid_constant__ Dev d) {
 }
 
 template <bool F32L>
-__global__ void __launch_bounds__(256) k_search(const __grid_constant__ Dev d) {
+__global__ void __launch_bounds__(256, 4) k_search(const __grid_constant__ Dev d) {
   __shared__ SearchSmem<F32L> sm;
   phase_search<F32L>(d, sm);
 }
 
 template <bool F32L>
-__global__ void __launch_bounds__(REACT_THREADS) k_products(const __grid_constant__ Dev d) {
+__global__ void __launch_bounds__(256) k_products(const __grid_constant__ Dev d) {
   __shared__ ProductsSmem sm;
   phase_products<F32L>(d, sm);
 }
@@ -95,13 +97,19 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev 
     if constexpr (F32L) phase_search<true>(d, sm.search32);
     else phase_search<false>(d, sm.search64);
     grid_sync(d);
-    if (blockIdx.x == 0) phase_match(d, sm.match);
+    phase_match_fast(d, sm.match);
+    grid_sync(d);
+    if (blockIdx.x == 0) phase_match_rounds(d, sm.match);
     grid_sync(d);
     for (int p = 0; p < MAX_PASSES; ++p) {
       phase_event_sort_pass(d, p, sm.sort);
       grid_sync(d);
     }
-    if (blockIdx.x == 0) phase_products<F32L>(d, sm.products);
+    if (blockIdx.x == 0) phase_products_scan(d, sm.scan);
+    grid_sync(d);
+    phase_products<F32L>(d, sm.products);
+    grid_sync(d);
+    if (blockIdx.x == 0) phase_end_step(d, sm.end);
     grid_sync(d);
   }
 }
@@ -134,12 +142,11 @@ cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cu
   k_search<F32L><<<lc.search_blocks, 256, 0, s>>>(d);
   mark(2 * PH_SEARCH + 1);
   mark(2 * PH_REACT);
-  enqueue_match(d, s);
-  for (int p = 0; p < MAX_PASSES; ++p) {
-    e = enqueue_event_sort_pass(d, p, lc.sort_blocks, s);
-    if (e != cudaSuccess) return e;
-  }
-  k_products<F32L><<<1, REACT_THREADS, 0, s>>>(d);
+  e = enqueue_react_head(d, lc, s);
+  if (e != cudaSuccess) return e;
+  k_products<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
+  e = enqueue_end_step(d, s);
+  if (e != cudaSuccess) return e;
   mark(2 * PH_REACT + 1);
   return cudaGetLastError();
 }

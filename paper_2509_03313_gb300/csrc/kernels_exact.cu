@@ -15,9 +15,14 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_pass(const __grid_constan
   phase_sort_pass(d, pass, *reinterpret_cast<SortSmem*>(smem_raw));
 }
 
-__global__ void __launch_bounds__(REACT_THREADS) k_match(const __grid_constant__ Dev d) {
+__global__ void __launch_bounds__(256) k_match_fast(const __grid_constant__ Dev d) {
   __shared__ MatchSmem sm;
-  phase_match(d, sm);
+  phase_match_fast(d, sm);
+}
+
+__global__ void __launch_bounds__(REACT_THREADS) k_match_rounds(const __grid_constant__ Dev d) {
+  __shared__ MatchSmem sm;
+  phase_match_rounds(d, sm);
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) k_event_sort_pass(const __grid_constant__ Dev d, int pass) {
@@ -25,13 +30,29 @@ __global__ void __launch_bounds__(SORT_THREADS) k_event_sort_pass(const __grid_c
   phase_event_sort_pass(d, pass, *reinterpret_cast<SortSmem*>(smem_raw));
 }
 
-cudaError_t enqueue_event_sort_pass(const Dev& d, int pass, int blocks, cudaStream_t s) {
-  k_event_sort_pass<<<blocks, SORT_THREADS, sizeof(SortSmem), s>>>(d, pass);
+__global__ void __launch_bounds__(REACT_THREADS) k_products_scan(const __grid_constant__ Dev d) {
+  __shared__ ScanSmem sm;
+  phase_products_scan(d, sm);
+}
+
+__global__ void __launch_bounds__(256) k_end_step(const __grid_constant__ Dev d) {
+  __shared__ EndSmem sm;
+  phase_end_step(d, sm);
+}
+
+cudaError_t enqueue_react_head(const Dev& d, const LaunchCfg& lc, cudaStream_t s) {
+  k_match_fast<<<lc.stream_blocks, 256, 0, s>>>(d);
+  k_match_rounds<<<1, REACT_THREADS, 0, s>>>(d);
+  // events are few: a handful of CTAs claim all the tiles
+  const int ev_blocks = lc.sort_blocks < 32 ? lc.sort_blocks : 32;
+  for (int p = 0; p < MAX_PASSES; ++p)
+    k_event_sort_pass<<<ev_blocks, SORT_THREADS, sizeof(SortSmem), s>>>(d, p);
+  k_products_scan<<<1, REACT_THREADS, 0, s>>>(d);
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_match(const Dev& d, cudaStream_t s) {
-  k_match<<<1, REACT_THREADS, 0, s>>>(d);
+cudaError_t enqueue_end_step(const Dev& d, cudaStream_t s) {
+  k_end_step<<<1, 256, 0, s>>>(d);
   return cudaGetLastError();
 }
 

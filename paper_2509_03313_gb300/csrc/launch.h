@@ -20,8 +20,9 @@ struct LaunchCfg {
 // kernels_exact.cu (FP64 arithmetic without contraction)
 cudaError_t enqueue_begin(const Dev& d, cudaStream_t s);
 cudaError_t enqueue_sort_pass(const Dev& d, int pass, int blocks, cudaStream_t s);
-cudaError_t enqueue_event_sort_pass(const Dev& d, int pass, int blocks, cudaStream_t s);
-cudaError_t enqueue_match(const Dev& d, cudaStream_t s);
+// matching (fast path + conflict rounds), event ordering, product prefix
+cudaError_t enqueue_react_head(const Dev& d, const LaunchCfg& lc, cudaStream_t s);
+cudaError_t enqueue_end_step(const Dev& d, cudaStream_t s);
 cudaError_t sort_pass_occupancy(int* blocks_per_sm);
 cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t enqueue_persistent_f64(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s);

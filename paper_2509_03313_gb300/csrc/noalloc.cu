@@ -31,7 +31,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(25
 
 // Byte layout of the scratch array.
 struct Layout {
-  size_t sx, sy, sz, stid, tx, ty, tz, ttid, tdx, tdy, tdz, items, cell_sorted, sortbuf, dead, cell_info, lookback, cand,
+  size_t sx, sy, sz, stid, tx, ty, tz, ttid, tdx, tdy, tdz, items, touch, cell_sorted, sortbuf, dead, cell_info, lookback, cand,
       ev_list, alive0, alive1, ev_k0, ev_k1, ev_v0, ev_v1, ev_log, step_log, pend, trains, tables,
       global, total;
 };
@@ -45,6 +45,7 @@ constexpr Layout make_layout() {
   L.tx = take(M * 8); L.ty = take(M * 8); L.tz = take(M * 8); L.ttid = take(M * 4);
   L.tdx = take(M * 8); L.tdy = take(M * 8); L.tdz = take(M * 8);
   L.items = take((M + M / ITEM_HOME + 64) * 4);
+  L.touch = take(M * 4);
   L.cell_sorted = take(M * 4);
   L.sortbuf = take(M * 16);
   L.dead = take(M);
@@ -68,7 +69,7 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = LAYOUT.total;
 
 }  // namespace
 
-// The shared working memory of chem_step_noalloc (about 3.5 MB).
+// The shared working memory of chem_step_noalloc (about 3.6 MB).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -83,6 +84,7 @@ __global__ void k_noalloc_setup(Dev d, Tables tb, Train tr) {
     *d.trains = tr;
     Global g;
     std::memset(&g, 0, sizeof(g));
+    g.item_home = ITEM_HOME;
     *d.g = g;
   }
 }
@@ -236,6 +238,9 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   tr.key0 = static_cast<uint32_t>(cfg->seed & 0xFFFFFFFFull);
   tr.key1 = static_cast<uint32_t>(cfg->seed >> 32) ^ cfg->train_id;
   tr.n_max = NA_CELLS_AXIS;
+  tr.n_alloc = NA_CELLS_AXIS;
+  tr.cb = 5;  // 32 = 2^5 cells per axis
+  tr.inv_L = 1.0 / cfg->L_nm;
   tr.id_limit = (1u << 29) - 1u;
   tr.t = t_s;
   tr.t_end = std::numeric_limits<double>::infinity();
@@ -272,6 +277,7 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   d.tdy = reinterpret_cast<double*>(b + LAYOUT.tdy);
   d.tdz = reinterpret_cast<double*>(b + LAYOUT.tdz);
   d.items = reinterpret_cast<uint32_t*>(b + LAYOUT.items);
+  d.touch = reinterpret_cast<uint32_t*>(b + LAYOUT.touch);
   d.cap_items = NA_MAX_SPECIES + NA_MAX_SPECIES / ITEM_HOME + 64;
   d.cell_sorted = reinterpret_cast<uint32_t*>(b + LAYOUT.cell_sorted);
   uint32_t* sortbuf = reinterpret_cast<uint32_t*>(b + LAYOUT.sortbuf);
@@ -314,6 +320,7 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   cudaStream_t s = static_cast<cudaStream_t>(cfg->cuda_stream);
   // leftovers of the previous call: stale hash cells and look-back words must not match
   bool ok = cudaMemsetAsync(d.cell_info, 0xFF, (NA_CELLS + 1) * 16, s) == cudaSuccess &&
+            cudaMemsetAsync(d.touch, 0, NA_MAX_SPECIES * 4, s) == cudaSuccess &&
             cudaMemsetAsync(d.lookback, 0, static_cast<size_t>(NA_TILES) * RADIX * 8, s) == cudaSuccess;
   if (ok) {
     k_noalloc_setup<<<1, 1, 0, s>>>(d, tb, tr);

@@ -9,6 +9,7 @@
 // reference's positions to rounding and its decisions exactly.
 #pragma once
 #include <cfloat>
+#include <type_traits>
 #include <math_constants.h>
 
 #include "onesweep.cuh"
@@ -31,6 +32,24 @@ __device__ __forceinline__ double wrap_box(double x, double L, double halfL) {
   if (x >= halfL) x = __dsub_rn(x, L);
   if (x < -halfL) x = __dadd_rn(x, L);
   return x;
+}
+
+// The same shift computed with 1/L instead of a division (FP32-local regrid only; the
+// FP64 mode keeps wrap_box, whose rounding is the reference's).
+__device__ __forceinline__ double wrap_box_fast(double x, double L, double halfL, double inv_L) {
+  const double k = floor((x + halfL) * inv_L);
+  x -= k * L;
+  if (x >= halfL) x -= L;
+  if (x < -halfL) x += L;
+  return x;
+}
+
+// A coordinate measured from the box corner folded into [0, L) (FP32-local regrid).
+__device__ __forceinline__ double rebase_corner(double a, double L, double inv_L) {
+  if (a >= L || a < 0.0) a -= L * floor(a * inv_L);
+  if (a >= L) a -= L;
+  if (a < 0.0) a += L;
+  return a;
 }
 
 // Eq. 2 (minimum image) for the separation of two in-box points.
@@ -108,21 +127,25 @@ __device__ __forceinline__ int wrap_cell(int i, int n) {
 // cutoffs of this step; then the slot offsets of the releases and the step counters.
 struct BeginSmem {
   uint32_t rel[MAX_TRAINS];
+  unsigned long long rcmax_bits[MAX_TRAINS];
   uint32_t any;
 };
 
+// One CTA. (1) per train: release count, clock step and free-jump decision; (2) per
+// (train, reaction) cutoff and bridge constants and per (train, type) step sigma, spread
+// over the threads because FP64 square roots and divisions are long on this part;
+// (3) per train: hash grid of the step; (4) slot offsets of the releases and counters.
 static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
-  uint32_t* s_rel = sb.rel;
-  uint32_t& s_any = sb.any;
   const int st = status_of(d);
-  if (threadIdx.x == 0) s_any = 0;
-  __syncthreads();
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) sb.any = 0;
   const Tables& tb = *d.tables;
-  for (uint32_t b = threadIdx.x; b < d.n_trains; b += blockDim.x) {
+  for (uint32_t b = tid; b < d.n_trains; b += nt) {
     Train& tr = d.trains[b];
     const bool act = (st == 0) && (tr.t < tr.t_end);
     uint32_t rel = 0;
     int free_jump = 0;
+    sb.rcmax_bits[b] = 0ull;
     if (act) {
       // pending arrivals are sorted; release those with arrival <= t
       uint32_t lo = tr.p_head, hi = tr.p_tail;
@@ -154,33 +177,6 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
       tr.dt = dt;
       tr.t_next = t_next;
       tr.t_start = tr.t;
-      // cutoffs R + c sqrt(2 D_AB dt) and the hash grid (cell >= largest cutoff)
-      double rcmax = 0.0;
-      for (int r = 0; r < tb.n_rxn; ++r) {
-        const double rc = __dadd_rn(tb.R[r], __dmul_rn(tr.c, sqrt(__dmul_rn(__dmul_rn(2.0, tb.D_AB[r]), dt))));
-        tr.rc2[r] = __dmul_rn(rc, rc);
-        tr.rc2f[r] = static_cast<float>(tr.rc2[r]);
-        tr.ddt[r] = __dmul_rn(tb.D_AB[r], dt);
-        tr.inv_ddt_f[r] = static_cast<float>(__ddiv_rn(1.0, tr.ddt[r]));
-        rcmax = fmax(rcmax, rc);
-      }
-      for (int ty = 0; ty < tb.n_types; ++ty) {
-        tr.sig[ty] = sqrt(__dmul_rn(__dmul_rn(2.0, tb.D[ty]), dt));
-        tr.sigf[ty] = static_cast<float>(tr.sig[ty]);
-      }
-      int n = tr.n_max;
-      if (free_jump) {
-        n = tr.n_ref;  // no pair search: keep the hash grid
-      } else if (rcmax > 0.0) {
-        const double nf = floor(__ddiv_rn(tr.L, __dmul_rn(rcmax, CELL_SLACK)));
-        n = static_cast<int>(fmin(nf, static_cast<double>(tr.n_max)));
-        n = max(n, 3);
-      }
-      tr.n = n;
-      tr.h = __ddiv_rn(tr.L, static_cast<double>(n));
-      tr.inv_h = __ddiv_rn(static_cast<double>(n), tr.L);
-      tr.hf = static_cast<float>(tr.h);
-      tr.inv_hf = static_cast<float>(tr.inv_h);
       tr.rel_n = rel;
       tr.rel_id0 = tr.next_id;
       tr.rel_p0 = tr.p_head;
@@ -191,24 +187,75 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
       tr.n_live_step = live;
       tr.n_events_step = 0;
       if (tr.next_id > tr.id_limit) raise_status(d.g, CHEM_ECAPACITY);
-      atomicOr(&s_any, 1u);
+      atomicOr(&sb.any, 1u);
     } else {
       tr.rel_n = 0;
     }
     tr.active = act ? 1 : 0;
     tr.free_jump = free_jump;
-    s_rel[b] = rel;
+    sb.rel[b] = rel;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  // cutoffs R + c sqrt(2 D_AB dt), bridge constants, and sigma = sqrt(2 D dt)
+  const int per = MAXR + MAXT;
+  for (uint32_t w = tid; w < d.n_trains * per; w += nt) {
+    const uint32_t b = w / per;
+    const int q = static_cast<int>(w % per);
+    Train& tr = d.trains[b];
+    if (!tr.active) continue;
+    const double dt = tr.dt;
+    if (q < MAXR) {
+      if (q >= tb.n_rxn) continue;
+      const double rc = __dadd_rn(tb.R[q], __dmul_rn(tr.c, sqrt(__dmul_rn(__dmul_rn(2.0, tb.D_AB[q]), dt))));
+      tr.rc2[q] = __dmul_rn(rc, rc);
+      tr.rc2f[q] = static_cast<float>(tr.rc2[q]);
+      tr.ddt[q] = __dmul_rn(tb.D_AB[q], dt);
+      tr.inv_ddt_f[q] = 1.0f / static_cast<float>(tr.ddt[q]);
+      atomicMax(&sb.rcmax_bits[b], static_cast<unsigned long long>(__double_as_longlong(rc)));
+    } else {
+      const int ty = q - MAXR;
+      if (ty >= tb.n_types) continue;
+      tr.sig[ty] = sqrt(__dmul_rn(__dmul_rn(2.0, tb.D[ty]), dt));
+      tr.sigf[ty] = static_cast<float>(tr.sig[ty]);
+    }
+  }
+  __syncthreads();
+  for (uint32_t b = tid; b < d.n_trains; b += nt) {
+    Train& tr = d.trains[b];
+    if (!tr.active) continue;
+    const double rcmax = __longlong_as_double(static_cast<long long>(sb.rcmax_bits[b]));
+    // finest admissible grid: cells at least the largest cutoff (with slack)
+    int n_target = tr.n_max;
+    if (rcmax > 0.0) {
+      const float nf = floorf(static_cast<float>(tr.L) / (static_cast<float>(rcmax) * CELL_SLACK_F));
+      n_target = max(3, min(tr.n_max, static_cast<int>(fminf(nf, 1048576.f))));
+    }
+    // keep the current grid while it is valid and at most 2x too coarse; when the
+    // cutoff outgrows it, move to cells 1.2x larger than needed (fewer regrids)
+    if (tr.n_ref == 0) {  // first step after init or reset
+      tr.n_ref = n_target;
+      tr.h_ref = __ddiv_rn(tr.L, static_cast<double>(n_target));
+    }
+    int n = tr.n_ref;
+    if (!tr.free_jump) {
+      if (n > n_target) n = max(3, (5 * n_target) / 6);
+      else if (2 * n < n_target) n = n_target;
+    }
+    tr.n = n;
+    tr.h = __ddiv_rn(tr.L, static_cast<double>(n));
+    tr.inv_h = __dmul_rn(static_cast<double>(n), tr.inv_L);
+    tr.hf = static_cast<float>(tr.h);
+    tr.inv_hf = static_cast<float>(tr.inv_h);
+  }
+  if (tid == 0) {
     Global* g = d.g;
     uint32_t off = g->n_total;
     const uint32_t before = off;
     unsigned long long total = off;
     for (uint32_t b = 0; b < d.n_trains; ++b) {
       d.trains[b].rel_off = off;
-      total += s_rel[b];
-      off += s_rel[b];
+      total += sb.rel[b];
+      off += sb.rel[b];
     }
     if (total > d.cap) {
       raise_status(g, CHEM_ECAPACITY);
@@ -219,18 +266,20 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     }
     for (int p = 0; p < MAX_PASSES; ++p) g->tile_ctr[p] = 0;
     g->n_cand = 0;
+    g->n_conflict = 0;
     g->n_items = 0;
+    g->item_ctr = 0;
     g->n_events = 0;
     g->n_products = 0;
     g->n_dead = 0;
     g->epoch += 1;
-    g->any_active = s_any;
+    g->any_active = sb.any;
   }
-  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) {
+  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) {
     (&d.g->hist[0][0])[i] = 0u;
     (&d.g->ev_hist[0][0])[i] = 0u;
   }
-  if (threadIdx.x < MAX_PASSES) d.g->ev_tile_ctr[threadIdx.x] = 0u;
+  if (tid < MAX_PASSES) d.g->ev_tile_ctr[tid] = 0u;
   __syncthreads();
 }
 
@@ -283,7 +332,7 @@ __device__ void phase_release(const Dev& d) {
       const double x = d.px[p], y = d.py[p], z = d.pz[p];
       if (F32L) {
         const int n = tr.n_ref;
-        const double h = tr.h_ref, inv_h = __ddiv_rn(1.0, h);
+        const double h = tr.h_ref, inv_h = static_cast<double>(n) * tr.inv_L;
         const int ix = cell_index(x, tr.halfL, inv_h, n);
         const int iy = cell_index(y, tr.halfL, inv_h, n);
         const int iz = cell_index(z, tr.halfL, inv_h, n);
@@ -291,7 +340,7 @@ __device__ void phase_release(const Dev& d) {
         const float oy = static_cast<float>(__dsub_rn(__dadd_rn(y, tr.halfL), __dmul_rn(iy, h)));
         const float oz = static_cast<float>(__dsub_rn(__dadd_rn(z, tr.halfL), __dmul_rn(iz, h)));
         d.s4[slot] = make_float4(ox, oy, oz, __uint_as_float(tid));
-        d.cell_sorted[slot] = tr.cell_base + static_cast<uint32_t>((iz * n + iy) * n + ix);
+        d.cell_sorted[slot] = tr.cell_base + cell_encode(ix, iy, iz, tr.cb);
       } else {
         d.sx[slot] = x;
         d.sy[slot] = y;
@@ -349,7 +398,7 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
           const int ix = cell_index(x, tr.halfL, tr.inv_h, n);
           const int iy = cell_index(y, tr.halfL, tr.inv_h, n);
           const int iz = cell_index(z, tr.halfL, tr.inv_h, n);
-          key = tr.cell_base + static_cast<uint32_t>((iz * n + iy) * n + ix);
+          key = tr.cell_base + cell_encode(ix, iy, iz, tr.cb);
         } else {
           const float4 v = d.s4[s];
           const uint32_t tid = __float_as_uint(v.w);
@@ -358,9 +407,8 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
           gauss3_f32(tid_id(tid), tr.step, tr.key0, tr.key1, g0, g1, g2);
           const float sig = tr.sigf[ty];
           const int nr = tr.n_ref;
-          const uint32_t loc = cell - tr.cell_base;
-          int ix = static_cast<int>(loc % nr), iy = static_cast<int>((loc / nr) % nr),
-              iz = static_cast<int>(loc / (static_cast<uint32_t>(nr) * nr));
+          int ix, iy, iz;
+          cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
           const int n = tr.n;
           const float ex = sig * g0, ey = sig * g1, ez = sig * g2;
           d.td4[s] = make_float4(ex, ey, ez, 0.f);
@@ -369,24 +417,26 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
             ox = v.x + ex; oy = v.y + ey; oz = v.z + ez;
             const float fx = floorf(ox * tr.inv_hf), fy = floorf(oy * tr.inv_hf), fz = floorf(oz * tr.inv_hf);
             ox -= fx * tr.hf; oy -= fy * tr.hf; oz -= fz * tr.hf;
-            ix = wrap_cell(ix + static_cast<int>(fx), n);
-            iy = wrap_cell(iy + static_cast<int>(fy), n);
-            iz = wrap_cell(iz + static_cast<int>(fz), n);
+            const int jx = static_cast<int>(fx), jy = static_cast<int>(fy), jz = static_cast<int>(fz);
+            ix = (jx >= -1 && jx <= 1) ? step_cell(ix, jx, n) : wrap_cell(ix + jx, n);
+            iy = (jy >= -1 && jy <= 1) ? step_cell(iy, jy, n) : wrap_cell(iy + jy, n);
+            iz = (jz >= -1 && jz <= 1) ? step_cell(iz, jz, n) : wrap_cell(iz + jz, n);
           } else {
-            // the hash grid changed this step: go through FP64 absolute positions
+            // the hash grid changed this step: FP64 position from the box corner, then
+            // the new cell and offset (no division)
             const double hr = tr.h_ref;
-            double ax = wrap_box((ix * hr - tr.halfL) + v.x + static_cast<double>(ex), tr.L, tr.halfL);
-            double ay = wrap_box((iy * hr - tr.halfL) + v.y + static_cast<double>(ey), tr.L, tr.halfL);
-            double az = wrap_box((iz * hr - tr.halfL) + v.z + static_cast<double>(ez), tr.L, tr.halfL);
-            ix = cell_index(ax, tr.halfL, tr.inv_h, n);
-            iy = cell_index(ay, tr.halfL, tr.inv_h, n);
-            iz = cell_index(az, tr.halfL, tr.inv_h, n);
-            ox = static_cast<float>((ax + tr.halfL) - ix * tr.h);
-            oy = static_cast<float>((ay + tr.halfL) - iy * tr.h);
-            oz = static_cast<float>((az + tr.halfL) - iz * tr.h);
+            const double ax = rebase_corner(ix * hr + static_cast<double>(v.x + ex), tr.L, tr.inv_L);
+            const double ay = rebase_corner(iy * hr + static_cast<double>(v.y + ey), tr.L, tr.inv_L);
+            const double az = rebase_corner(iz * hr + static_cast<double>(v.z + ez), tr.L, tr.inv_L);
+            ix = min(static_cast<int>(ax * tr.inv_h), n - 1);
+            iy = min(static_cast<int>(ay * tr.inv_h), n - 1);
+            iz = min(static_cast<int>(az * tr.inv_h), n - 1);
+            ox = static_cast<float>(ax - ix * tr.h);
+            oy = static_cast<float>(ay - iy * tr.h);
+            oz = static_cast<float>(az - iz * tr.h);
           }
           d.t4[s] = make_float4(ox, oy, oz, v.w);
-          key = tr.cell_base + static_cast<uint32_t>((iz * n + iy) * n + ix);
+          key = tr.cell_base + cell_encode(ix, iy, iz, tr.cb);
         }
       }
       d.keys0[s] = key;
@@ -407,13 +457,41 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
 }
 
 // ======================================================================== sort pass
+// A pass whose digit is the same for every key is the identity and is skipped; the
+// ping-pong buffers of the remaining passes follow from the histograms, which every CTA
+// reads identically. Returns the number of executed passes before `pass` in *before.
+__device__ __forceinline__ bool pass_active(const uint32_t (*hist)[RADIX], int pass, uint32_t n,
+                                            int* before) {
+  int cnt = 0;
+  bool act = false;
+  for (int q = 0; q <= pass; ++q) {
+    const int trivial = __syncthreads_or(static_cast<int>(hist[q][threadIdx.x & (RADIX - 1)] == n));
+    if (q < pass) cnt += trivial ? 0 : 1;
+    else act = !trivial;
+  }
+  *before = cnt;
+  return act;
+}
+
+// Status read once per CTA so that every thread takes the same branch before barriers.
+__device__ __forceinline__ bool block_status_ok(const Dev& d) {
+  return __syncthreads_and(threadIdx.x == 0 ? (status_of(d) == 0) : 1) != 0;
+}
+
 static __device__ void phase_sort_pass(const Dev& d, int pass, SortSmem& sm) {
-  if (status_of(d)) return;
-  const uint32_t* kin = (pass & 1) ? d.keys1 : d.keys0;
-  const uint32_t* vin = (pass & 1) ? d.vals1 : d.vals0;
-  uint32_t* kout = (pass & 1) ? d.keys0 : d.keys1;
-  uint32_t* vout = (pass & 1) ? d.vals0 : d.vals1;
-  onesweep_pass(kin, vin, kout, vout, d.g->n_total, 8 * pass, d.g->hist[pass], &d.g->tile_ctr[pass],
+  if (!block_status_ok(d)) return;
+  const uint32_t n = d.g->n_total;
+  int before = 0;
+  const bool act = pass_active(d.g->hist, pass, n, &before);
+  if (pass == d.passes - 1 && blockIdx.x == 0 && threadIdx.x == 0)
+    d.g->sort_parity = static_cast<uint32_t>((before + (act ? 1 : 0)) & 1);
+  if (!act) return;
+  const bool odd = before & 1;
+  const uint32_t* kin = odd ? d.keys1 : d.keys0;
+  const uint32_t* vin = odd ? d.vals1 : d.vals0;
+  uint32_t* kout = odd ? d.keys0 : d.keys1;
+  uint32_t* vout = odd ? d.vals0 : d.vals1;
+  onesweep_pass(kin, vin, kout, vout, n, 8 * pass, d.g->hist[pass], &d.g->tile_ctr[pass],
                 d.lookback, d.g->epoch * 2 * MAX_PASSES + pass, d.g, sm);
 }
 
@@ -423,10 +501,11 @@ static __device__ void phase_sort_pass(const Dev& d, int pass, SortSmem& sm) {
 template <bool F32L>
 __device__ void phase_gather(const Dev& d) {
   if (status_of(d)) return;
-  const uint32_t* kf = (d.passes & 1) ? d.keys1 : d.keys0;
-  const uint32_t* vf = (d.passes & 1) ? d.vals1 : d.vals0;
+  const uint32_t* kf = d.g->sort_parity ? d.keys1 : d.keys0;
+  const uint32_t* vf = d.g->sort_parity ? d.vals1 : d.vals0;
   const uint32_t n_live = d.g->n_total - d.g->n_dead;
   const uint32_t epoch = d.g->epoch;
+  const uint32_t item_home = d.g->item_home;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_live; s += stride) {
     const uint32_t key = kf[s];
@@ -446,7 +525,7 @@ __device__ void phase_gather(const Dev& d) {
     if (first) { ci[0] = static_cast<int>(s); ci[2] = static_cast<int>(epoch); }
     if (s + 1 == n_live || kf[s + 1] != key) ci[1] = static_cast<int>(s + 1);
     // pair-search work item: a cell's first slot and every ITEM_HOME-th slot
-    if (first || (s % ITEM_HOME) == 0) {
+    if (first || (s % item_home) == 0) {
       const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, key);
       if (d.trains[b].active && !d.trains[b].free_jump) {
         const uint32_t it = atomicAdd(&d.g->n_items, 1u);
@@ -493,15 +572,33 @@ struct SearchWarpSmem<false> {
   uint32_t tid[ITEM_HOME];
 };
 
+struct SearchRanges {
+  uint32_t start[N_FWD];   // first slot of each neighbour range
+  uint32_t off[N_FWD];     // its offset in the flattened neighbour list
+};
+
+// Squared cutoff of every type pair for the warp's current train (negative when the
+// pair does not react): FP32 in FP32-local mode, FP64 (exact) in FP64 mode.
+template <bool F32L>
+struct CutoffTable {
+  using T = typename std::conditional<F32L, float, double>::type;
+  T rc2[MAXT * MAXT];
+};
+
 template <bool F32L>
 struct SearchSmem {
   SearchWarpSmem<F32L> w[8];
+  SearchRanges rg[8];
+  CutoffTable<F32L> ct[8];
+  int ct_train[8];
 };
 
 __device__ __forceinline__ void emit_candidate(const Dev& d, uint32_t s_lo, uint32_t s_hi, uint32_t id_lo,
                                                uint32_t id_hi, int r, int b, double d1sq) {
   const uint32_t c = atomicAdd(&d.g->n_cand, 1u);
   if (c >= d.cap_cand) { raise_status(d.g, CHEM_ECAPACITY); return; }
+  atomicAdd(&d.touch[s_lo], 1u);
+  atomicAdd(&d.touch[s_hi], 1u);
   Cand cd;
   cd.s_lo = s_lo; cd.s_hi = s_hi; cd.id_lo = id_lo; cd.id_hi = id_hi;
   cd.rxn_train = static_cast<uint32_t>(r) | (static_cast<uint32_t>(b) << 8);
@@ -538,23 +635,86 @@ __device__ __forceinline__ bool accept_f32(float d0sq, float d1sq, int r, const 
   return u < bridge_p(d0, d1, tb.R[r], tr.ddt[r]);
 }
 
+// Slow path of one pair that passed the cutoff: orientation, this step's
+// displacements (stored by the diffusion), acceptance, candidate.
+template <bool F32L>
+__device__ __forceinline__ void pair_accept(const Dev& d, const Tables& tb, const Train& tr, int b,
+                                            const SearchWarpSmem<F32L>& hs, uint32_t h, uint32_t s0,
+                                            uint32_t j, uint32_t tid_j, float fx, float fy, float fz,
+                                            float f2, double d1sq, double rx1, double ry1, double rz1,
+                                            const uint32_t* vf) {
+  uint32_t tid_i;
+  if constexpr (F32L) tid_i = __float_as_uint(hs.pos[h].w);
+  else tid_i = hs.tid[h];
+  const uint32_t ti = tid_type(tid_i), tj = tid_type(tid_j);
+  const int r = tb.pair_rxn[ti][tj];
+  const uint32_t id_i = tid_id(tid_i), id_j = tid_id(tid_j);
+  const bool i_lo = id_i < id_j;
+  const uint32_t id_lo = i_lo ? id_i : id_j, id_hi = i_lo ? id_j : id_i;
+  const uint32_t si = s0 + h;
+  if constexpr (F32L) {
+    if (!i_lo) { fx = -fx; fy = -fy; fz = -fz; }
+    const float4 di = hs.dl[h];
+    const float4 dj = d.td4[vf[j]];
+    const float4 dlo = i_lo ? di : dj, dhi = i_lo ? dj : di;
+    const float r0x = fx - (dhi.x - dlo.x), r0y = fy - (dhi.y - dlo.y), r0z = fz - (dhi.z - dlo.z);
+    const float d0sq = r0x * r0x + r0y * r0y + r0z * r0z;
+    if (!accept_f32(d0sq, f2, r, tb, tr, id_lo, id_hi)) return;
+    emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, static_cast<double>(f2));
+  } else {
+    // r1 = minimum image of x_hi - x_lo, recomputed in that orientation as the reference does
+    if (!i_lo) { rx1 = -rx1; ry1 = -ry1; rz1 = -rz1; }
+    const uint32_t tj_idx = vf[j];
+    const double ejx = d.tdx[tj_idx], ejy = d.tdy[tj_idx], ejz = d.tdz[tj_idx];
+    const double elx = i_lo ? hs.ex[h] : ejx, ely = i_lo ? hs.ey[h] : ejy, elz = i_lo ? hs.ez[h] : ejz;
+    const double ehx = i_lo ? ejx : hs.ex[h], ehy = i_lo ? ejy : hs.ey[h], ehz = i_lo ? ejz : hs.ez[h];
+    const double r0x = __dsub_rn(rx1, __dsub_rn(ehx, elx));
+    const double r0y = __dsub_rn(ry1, __dsub_rn(ehy, ely));
+    const double r0z = __dsub_rn(rz1, __dsub_rn(ehz, elz));
+    const double d1 = sqrt(d1sq);
+    const double d0 = sqrt(sq3(r0x, r0y, r0z));
+    const double p = bridge_p(d0, d1, tb.R[r], tr.ddt[r]);
+    const double u = pair_uniform(id_lo, id_hi, tr.step, tr.key0, tr.key1);
+    if (!(u < p)) return;
+    emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, d1sq);
+  }
+}
+
 template <bool F32L>
 __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
   if (status_of(d)) return;
   const uint32_t n_items = min(d.g->n_items, d.cap_items);
   const uint32_t epoch = d.g->epoch;
-  const uint32_t* vf = (d.passes & 1) ? d.vals1 : d.vals0;
+  const uint32_t* vf = d.g->sort_parity ? d.vals1 : d.vals0;
   const Tables& tb = *d.tables;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const uint32_t warps_total = gridDim.x * (blockDim.x >> 5);
   SearchWarpSmem<F32L>& hs = sm.w[wib];
-  for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + wib; it < n_items; it += warps_total) {
+  SearchRanges& rg = sm.rg[wib];
+  auto& ct = sm.ct[wib];
+  if (lane == 0) sm.ct_train[wib] = -1;
+  __syncwarp();
+  const uint32_t item_home = d.g->item_home;
+  for (;;) {
+    // work stealing: one item per warp at a time
+    uint32_t it = 0;
+    if (lane == 0) it = atomicAdd(&d.g->item_ctr, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) break;
     const uint32_t s0 = d.items[it];
     const uint32_t cell = d.cell_sorted[s0];
     const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
     const Train& tr = d.trains[b];
+    if (sm.ct_train[wib] != b) {  // cutoff table of this train (warp-uniform)
+      for (int q = lane; q < MAXT * MAXT; q += 32) {
+        const int r = tb.pair_rxn[q >> 3][q & 7];
+        if constexpr (F32L) ct.rc2[q] = r >= 0 ? tr.rc2f[r] : -1.f;
+        else ct.rc2[q] = r >= 0 ? tr.rc2[r] : -1.0;
+      }
+      __syncwarp();
+      if (lane == 0) sm.ct_train[wib] = b;
+    }
     const int4 ci = d.cell_info[cell];
-    const uint32_t s_end = min(static_cast<uint32_t>(ci.y), (s0 / ITEM_HOME + 1) * ITEM_HOME);
+    const uint32_t s_end = min(static_cast<uint32_t>(ci.y), (s0 / item_home + 1) * item_home);
     const uint32_t nh = s_end - s0;
     // stage the home species; OR of the types they react with
     uint32_t want = 0;
@@ -562,17 +722,16 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
       const uint32_t s = s0 + h;
       const uint32_t ti = vf[s];
       uint32_t t;
-      if (F32L) {
+      if constexpr (F32L) {
         const float4 v = d.s4[s];
-        reinterpret_cast<SearchWarpSmem<true>&>(hs).pos[h] = v;
-        reinterpret_cast<SearchWarpSmem<true>&>(hs).dl[h] = d.td4[ti];
+        hs.pos[h] = v;
+        hs.dl[h] = d.td4[ti];
         t = __float_as_uint(v.w);
       } else {
-        auto& hd = reinterpret_cast<SearchWarpSmem<false>&>(hs);
-        hd.x[h] = d.sx[s]; hd.y[h] = d.sy[s]; hd.z[h] = d.sz[s];
-        hd.ex[h] = d.tdx[ti]; hd.ey[h] = d.tdy[ti]; hd.ez[h] = d.tdz[ti];
+        hs.x[h] = d.sx[s]; hs.y[h] = d.sy[s]; hs.z[h] = d.sz[s];
+        hs.ex[h] = d.tdx[ti]; hs.ey[h] = d.tdy[ti]; hs.ez[h] = d.tdz[ti];
         t = d.stid[s];
-        hd.tid[h] = t;
+        hs.tid[h] = t;
       }
       want |= tb.reactive_mask[tid_type(t)];
     }
@@ -581,9 +740,8 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
     if (!want) continue;
     // neighbour ranges of the half shell
     const int n = tr.n;
-    const uint32_t loc = cell - tr.cell_base;
-    const int ix = static_cast<int>(loc % n), iy = static_cast<int>((loc / n) % n),
-              iz = static_cast<int>(loc / (static_cast<uint32_t>(n) * n));
+    int ix, iy, iz;
+    cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
     uint32_t rs = 0, rl = 0;
     if (lane < N_FWD) {
       if (lane == 0) {
@@ -592,8 +750,8 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
       } else {
         int ox, oy, oz;
         fwd_offset(lane, ox, oy, oz);
-        const uint32_t nc = tr.cell_base + static_cast<uint32_t>(
-            (wrap_cell(iz + oz, n) * n + wrap_cell(iy + oy, n)) * n + wrap_cell(ix + ox, n));
+        const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, ox, n), step_cell(iy, oy, n),
+                                                       step_cell(iz, oz, n), tr.cb);
         const int4 nci = d.cell_info[nc];
         if (static_cast<uint32_t>(nci.z) == epoch) {
           rs = static_cast<uint32_t>(nci.x);
@@ -609,88 +767,52 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
     }
     const uint32_t excl = incl - rl;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, N_FWD - 1);
-    uint32_t ex_k[N_FWD];
-#pragma unroll
-    for (int q = 0; q < N_FWD; ++q) ex_k[q] = __shfl_sync(0xffffffffu, excl, q);
-    for (uint32_t f0 = 0; f0 < total; f0 += 32) {
-      const uint32_t f = f0 + lane;
-      const bool valid = f < total;
+    if (lane < N_FWD) { rg.start[lane] = rs; rg.off[lane] = excl; }
+    __syncwarp();
+    // lanes -> (neighbour, home group): with fewer than 32 neighbours several home rows
+    // are processed at once so that no lane idles
+    uint32_t T2 = 32;
+    if (total < 32) { T2 = 1; while (T2 < total) T2 <<= 1; }
+    const uint32_t G = 32 / T2, hg = lane / T2;
+    for (uint32_t f = lane & (T2 - 1); f < total; f += T2) {
       int k = 0;
 #pragma unroll
-      for (int q = 1; q < N_FWD; ++q) k += (ex_k[q] <= f) ? 1 : 0;
-      const uint32_t j_start = __shfl_sync(0xffffffffu, rs, k);
-      const uint32_t j_off = __shfl_sync(0xffffffffu, excl, k);
-      if (!valid) continue;
-      const uint32_t j = j_start + (f - j_off);
-      int odx, ody, odz;
-      fwd_offset(k, odx, ody, odz);
+      for (int q = 1; q < N_FWD; ++q) k += (rg.off[q] <= f) ? 1 : 0;
+      const uint32_t j = rg.start[k] + (f - rg.off[k]);
       uint32_t tid_j;
       float4 vj = make_float4(0.f, 0.f, 0.f, 0.f);
       double xj = 0, yj = 0, zj = 0;
-      if (F32L) { vj = d.s4[j]; tid_j = __float_as_uint(vj.w); }
+      if constexpr (F32L) { vj = d.s4[j]; tid_j = __float_as_uint(vj.w); }
       else { tid_j = d.stid[j]; }
       const uint32_t tj = tid_type(tid_j);
       if (!((want >> tj) & 1u)) continue;
-      if (!F32L) { xj = d.sx[j]; yj = d.sy[j]; zj = d.sz[j]; }
-      const uint32_t id_j = tid_id(tid_j);
-      const uint32_t jmask = tb.reactive_mask[tj];
+      if constexpr (!F32L) { xj = d.sx[j]; yj = d.sy[j]; zj = d.sz[j]; }
+      const auto* row = &ct.rc2[tj * MAXT];
+      // own cell: only home slots below j
+      const uint32_t hmax = (k == 0) ? min(nh, j - s0) : nh;
+      int odx, ody, odz;
+      fwd_offset(k, odx, ody, odz);
       const float cx = odx * tr.hf, cy = ody * tr.hf, cz = odz * tr.hf;
-      for (uint32_t h = 0; h < nh; ++h) {
-        if (k == 0 && j <= s0 + h) break;  // own cell: only later slots (slots ascend with h)
-        uint32_t tid_i;
-        if (F32L) tid_i = __float_as_uint(reinterpret_cast<SearchWarpSmem<true>&>(hs).pos[h].w);
-        else tid_i = reinterpret_cast<SearchWarpSmem<false>&>(hs).tid[h];
-        const uint32_t ti = tid_type(tid_i);
-        if (!((jmask >> ti) & 1u)) continue;
-        const int r = tb.pair_rxn[ti][tj];
-        const uint32_t id_i = tid_id(tid_i);
-        const bool i_lo = id_i < id_j;
-        if (F32L) {
-          const SearchWarpSmem<true>& hf = reinterpret_cast<const SearchWarpSmem<true>&>(hs);
-          const float4 vi = hf.pos[h];
-          float fx = cx + (vj.x - vi.x), fy = cy + (vj.y - vi.y), fz = cz + (vj.z - vi.z);
+      for (uint32_t h = hg; h < hmax; h += G) {
+        if constexpr (F32L) {
+          const float4 vi = hs.pos[h];
+          const float rc2 = row[__float_as_uint(vi.w) & 7u];
+          const float fx = cx + (vj.x - vi.x), fy = cy + (vj.y - vi.y), fz = cz + (vj.z - vi.z);
           const float f2 = fx * fx + fy * fy + fz * fz;
-          if (!(f2 < tr.rc2f[r])) continue;
-          if (!i_lo) { fx = -fx; fy = -fy; fz = -fz; }
-          const float4 di = hf.dl[h];
-          const float4 dj = d.td4[vf[j]];
-          const float4 dlo = i_lo ? di : dj, dhi = i_lo ? dj : di;
-          const float r0x = fx - (dhi.x - dlo.x), r0y = fy - (dhi.y - dlo.y), r0z = fz - (dhi.z - dlo.z);
-          const float d0sq = r0x * r0x + r0y * r0y + r0z * r0z;
-          const uint32_t id_lo = i_lo ? id_i : id_j, id_hi = i_lo ? id_j : id_i;
-          if (!accept_f32(d0sq, f2, r, tb, tr, id_lo, id_hi)) continue;
-          const uint32_t si = s0 + h;
-          emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, static_cast<double>(f2));
+          if (f2 < rc2)
+            pair_accept<true>(d, tb, tr, b, hs, h, s0, j, tid_j, fx, fy, fz, f2, 0.0, 0.0, 0.0, 0.0, vf);
         } else {
-          const SearchWarpSmem<false>& hd = reinterpret_cast<const SearchWarpSmem<false>&>(hs);
-          const double xi = hd.x[h], yi = hd.y[h], zi = hd.z[h];
-          double rx1, ry1, rz1;
-          if (i_lo) {
-            rx1 = min_image(__dsub_rn(xj, xi), tr.L, tr.halfL);
-            ry1 = min_image(__dsub_rn(yj, yi), tr.L, tr.halfL);
-            rz1 = min_image(__dsub_rn(zj, zi), tr.L, tr.halfL);
-          } else {
-            rx1 = min_image(__dsub_rn(xi, xj), tr.L, tr.halfL);
-            ry1 = min_image(__dsub_rn(yi, yj), tr.L, tr.halfL);
-            rz1 = min_image(__dsub_rn(zi, zj), tr.L, tr.halfL);
-          }
+          const double rc2 = row[hs.tid[h] & 7u];
+          if (rc2 < 0.0) continue;
+          // minimum image of x_j - x_i (Eq. 2); the reference orients it x_hi - x_lo, and
+          // negating an exactly computed separation is exact, so the orientation can be
+          // fixed afterwards without changing a bit
+          const double rx1 = min_image(__dsub_rn(xj, hs.x[h]), tr.L, tr.halfL);
+          const double ry1 = min_image(__dsub_rn(yj, hs.y[h]), tr.L, tr.halfL);
+          const double rz1 = min_image(__dsub_rn(zj, hs.z[h]), tr.L, tr.halfL);
           const double d1sq = sq3(rx1, ry1, rz1);
-          if (!(d1sq < tr.rc2[r])) continue;
-          const uint32_t tj_idx = vf[j];
-          const double ejx = d.tdx[tj_idx], ejy = d.tdy[tj_idx], ejz = d.tdz[tj_idx];
-          const double elx = i_lo ? hd.ex[h] : ejx, ely = i_lo ? hd.ey[h] : ejy, elz = i_lo ? hd.ez[h] : ejz;
-          const double ehx = i_lo ? ejx : hd.ex[h], ehy = i_lo ? ejy : hd.ey[h], ehz = i_lo ? ejz : hd.ez[h];
-          const double r0x = __dsub_rn(rx1, __dsub_rn(ehx, elx));
-          const double r0y = __dsub_rn(ry1, __dsub_rn(ehy, ely));
-          const double r0z = __dsub_rn(rz1, __dsub_rn(ehz, elz));
-          const double d1 = sqrt(d1sq);
-          const double d0 = sqrt(sq3(r0x, r0y, r0z));
-          const uint32_t id_lo = i_lo ? id_i : id_j, id_hi = i_lo ? id_j : id_i;
-          const double p = bridge_p(d0, d1, tb.R[r], tr.ddt[r]);
-          const double u = pair_uniform(id_lo, id_hi, tr.step, tr.key0, tr.key1);
-          if (!(u < p)) continue;
-          const uint32_t si = s0 + h;
-          emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, d1sq);
+          if (d1sq < rc2)
+            pair_accept<false>(d, tb, tr, b, hs, h, s0, j, tid_j, 0.f, 0.f, 0.f, 0.f, d1sq, rx1, ry1, rz1, vf);
         }
       }
     }
@@ -699,29 +821,39 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
 }
 
 // ======================================================================== react
-// One reaction per species (Sec. 2.3: reactants react on encounter), in three phases:
-//  1. phase_match (one CTA): rounds of locally-dominant selection; a pair is committed
-//     when it is the smallest (d1^2, id_lo, id_hi) remaining pair of both its species,
-//     which equals the greedy walk over pairs sorted by that key (closest first, lower
-//     ids first). Emits every event with its key (train, id_lo) and digit histograms.
-//  2. the event keys are ordered by the Onesweep passes (all CTAs);
-//  3. phase_products (one CTA): product ids in (train, id_lo) order, products at the
-//     diffusion-weighted encounter point (Table 1 right-hand sides), tallies summed in
-//     shared memory, logs, and the end of the step (FP64 clock, step counter, dt growth).
+// One reaction per species (Sec. 2.3: reactants react on encounter):
+//  1. phase_match_fast (all CTAs): an accepted pair whose two species are in no other
+//     accepted pair is committed at once; the others go to a conflict list.
+//  2. phase_match_rounds (one CTA): rounds of locally-dominant selection over the
+//     conflict list; a pair is committed when it is the smallest (d1^2, id_lo, id_hi)
+//     remaining pair of both its species. Together with 1 this equals the greedy walk
+//     over all accepted pairs sorted by that key (closest first, lower ids first).
+//  3. Onesweep passes order the events by (train, id_lo);
+//  4. phase_products_scan (one CTA): product-count prefix in that order;
+//  5. phase_products (all CTAs): product ids and positions at the diffusion-weighted
+//     encounter point (Table 1 right-hand sides), tallies summed per CTA, event log;
+//  6. phase_end_step (one CTA): FP64 clock, step counter, dt growth, step records.
 struct MatchSmem {
-  uint32_t n_alive, n_next, n_ev;
+  uint32_t n_alive, n_next;
   uint32_t hist[MAX_PASSES][RADIX];
 };
 
-struct ProductsSmem {
-  uint32_t carry, any;
+struct ScanSmem {
+  uint32_t carry;
   uint32_t warp_tot[REACT_THREADS / 32];
   uint32_t first_pref[MAX_TRAINS];
   uint32_t prods_tr[MAX_TRAINS];
   uint32_t evs_tr[MAX_TRAINS];
+};
+
+struct ProductsSmem {
   int dcount[MAX_TRAINS][MAXT];
   int devents[MAX_TRAINS][MAXR];
   int dwater[MAX_TRAINS];
+};
+
+struct EndSmem {
+  uint32_t any;
 };
 
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_tot,
@@ -750,17 +882,58 @@ __device__ __forceinline__ uint32_t event_key(const Dev& d, const Cand& cd) {
   return d.train_bits ? ((b << (32 - d.train_bits)) | cd.id_lo) : cd.id_lo;
 }
 
-static __device__ void phase_match(const Dev& d, MatchSmem& sm) {
+__device__ __forceinline__ void commit_event(const Dev& d, uint32_t c, const Cand& cd,
+                                             uint32_t (*hist)[RADIX]) {
+  d.dead[cd.s_lo] = 1;
+  d.dead[cd.s_hi] = 1;
+  const uint32_t e = atomicAdd(&d.g->n_events, 1u);
+  const uint32_t key = event_key(d, cd);
+  d.ev_k0[e] = key;
+  d.ev_v0[e] = c;
+#pragma unroll
+  for (int p = 0; p < MAX_PASSES; ++p) atomicAdd(&hist[p][(key >> (8 * p)) & 255u], 1u);
+}
+
+__device__ __forceinline__ void flush_hist(const Dev& d, uint32_t (*hist)[RADIX]) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) {
+    const uint32_t c = (&hist[0][0])[i];
+    if (c) atomicAdd(&d.g->ev_hist[0][0] + i, c);
+  }
+}
+
+static __device__ void phase_match_fast(const Dev& d, MatchSmem& sm) {
+  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sm.hist[0][0])[i] = 0u;
+  const bool ok = block_status_ok(d);  // includes a barrier
+  const uint32_t n_c = ok ? min(d.g->n_cand, d.cap_cand) : 0u;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_c; c += gridDim.x * blockDim.x) {
+    const Cand cd = d.cand[c];
+    if (d.touch[cd.s_lo] == 1u && d.touch[cd.s_hi] == 1u) {
+      commit_event(d, c, cd, sm.hist);
+      d.touch[cd.s_lo] = 0u;
+      d.touch[cd.s_hi] = 0u;
+    } else {
+      d.alive0[atomicAdd(&d.g->n_conflict, 1u)] = c;
+    }
+  }
+  flush_hist(d, sm.hist);
+}
+
+static __device__ void phase_match_rounds(const Dev& d, MatchSmem& sm) {
   const int tid = threadIdx.x;
   const int nt = blockDim.x;
-  const bool ok = status_of(d) == 0;
+  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&sm.hist[0][0])[i] = 0u;
+  const bool ok = block_status_ok(d);
   unsigned long long* bd = reinterpret_cast<unsigned long long*>(d.keys0);
   unsigned long long* bp = bd + d.cap;
-  uint32_t n_c = min(d.g->n_cand, d.cap_cand);
-  if (!ok) n_c = 0;
-  if (tid == 0) { sm.n_alive = n_c; sm.n_ev = 0; }
-  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&sm.hist[0][0])[i] = 0u;
-  for (uint32_t i = tid; i < n_c; i += nt) d.alive0[i] = i;
+  const uint32_t n_c = ok ? d.g->n_conflict : 0u;
+  if (tid == 0) sm.n_alive = n_c;
+  // the rounds do not use the accepted-pair counts: reset them for the next step now
+  for (uint32_t i = tid; i < n_c; i += nt) {
+    const Cand cd = d.cand[d.alive0[i]];
+    d.touch[cd.s_lo] = 0u;
+    d.touch[cd.s_hi] = 0u;
+  }
   __syncthreads();
   uint32_t* alive = d.alive0;
   uint32_t* nxt = d.alive1;
@@ -796,16 +969,8 @@ static __device__ void phase_match(const Dev& d, MatchSmem& sm) {
       const Cand cd = d.cand[c];
       const unsigned long long kd = __double_as_longlong(cd.d1sq);
       const unsigned long long kp = (static_cast<unsigned long long>(cd.id_lo) << 32) | cd.id_hi;
-      if (bd[cd.s_lo] == kd && bp[cd.s_lo] == kp && bd[cd.s_hi] == kd && bp[cd.s_hi] == kp) {
-        d.dead[cd.s_lo] = 1;
-        d.dead[cd.s_hi] = 1;
-        const uint32_t e = atomicAdd(&sm.n_ev, 1u);
-        const uint32_t key = event_key(d, cd);
-        d.ev_k0[e] = key;
-        d.ev_v0[e] = c;
-#pragma unroll
-        for (int p = 0; p < MAX_PASSES; ++p) atomicAdd(&sm.hist[p][(key >> (8 * p)) & 255u], 1u);
-      }
+      if (bd[cd.s_lo] == kd && bp[cd.s_lo] == kp && bd[cd.s_hi] == kd && bp[cd.s_hi] == kp)
+        commit_event(d, c, cd, sm.hist);
     }
     if (tid == 0) sm.n_next = 0;
     __syncthreads();
@@ -819,145 +984,194 @@ static __device__ void phase_match(const Dev& d, MatchSmem& sm) {
     uint32_t* tmp = alive; alive = nxt; nxt = tmp;
     __syncthreads();
   }
-  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&d.g->ev_hist[0][0])[i] = (&sm.hist[0][0])[i];
-  if (tid == 0) d.g->n_events = sm.n_ev;
+  flush_hist(d, sm.hist);
   __syncthreads();
 }
 
-// One Onesweep pass over the event keys (ev_k0/ev_v0 -> ev_k1/ev_v1 and back).
+// One Onesweep pass over the event keys (ev_k0/ev_v0 <-> ev_k1/ev_v1), skipped when its
+// digit is the same for every event key.
 static __device__ void phase_event_sort_pass(const Dev& d, int pass, SortSmem& sm) {
-  if (status_of(d)) return;
-  const uint32_t* kin = (pass & 1) ? d.ev_k1 : d.ev_k0;
-  const uint32_t* vin = (pass & 1) ? d.ev_v1 : d.ev_v0;
-  uint32_t* kout = (pass & 1) ? d.ev_k0 : d.ev_k1;
-  uint32_t* vout = (pass & 1) ? d.ev_v0 : d.ev_v1;
-  onesweep_pass(kin, vin, kout, vout, d.g->n_events, 8 * pass, d.g->ev_hist[pass],
-                &d.g->ev_tile_ctr[pass], d.lookback, d.g->epoch * 2 * MAX_PASSES + MAX_PASSES + pass,
-                d.g, sm);
+  if (!block_status_ok(d)) return;
+  const uint32_t n = d.g->n_events;
+  int before = 0;
+  const bool act = pass_active(d.g->ev_hist, pass, n, &before);
+  if (pass == MAX_PASSES - 1 && blockIdx.x == 0 && threadIdx.x == 0)
+    d.g->ev_parity = static_cast<uint32_t>((before + (act ? 1 : 0)) & 1);
+  if (!act) return;
+  const bool odd = before & 1;
+  const uint32_t* kin = odd ? d.ev_k1 : d.ev_k0;
+  const uint32_t* vin = odd ? d.ev_v1 : d.ev_v0;
+  uint32_t* kout = odd ? d.ev_k0 : d.ev_k1;
+  uint32_t* vout = odd ? d.ev_v0 : d.ev_v1;
+  onesweep_pass(kin, vin, kout, vout, n, 8 * pass, d.g->ev_hist[pass], &d.g->ev_tile_ctr[pass],
+                d.lookback, d.g->epoch * 2 * MAX_PASSES + MAX_PASSES + pass, d.g, sm);
 }
 
-template <bool F32L>
-__device__ void phase_products(const Dev& d, ProductsSmem& sm) {
-  const int tid = threadIdx.x;
-  const int nt = blockDim.x;
-  const bool ok = status_of(d) == 0;
+// Product-count prefix over the ordered events, written to the free key buffer, plus
+// each train's first prefix, event and product counts.
+static __device__ void phase_products_scan(const Dev& d, ScanSmem& sm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const bool ok = block_status_ok(d);
   const Tables& tb = *d.tables;
   const uint32_t E = ok ? d.g->n_events : 0u;
-  const uint32_t* order = d.ev_v0;  // after an even number of passes
-  for (uint32_t b = tid; b < d.n_trains; b += nt) {
-    sm.first_pref[b] = 0xFFFFFFFFu; sm.prods_tr[b] = 0; sm.evs_tr[b] = 0; sm.dwater[b] = 0;
-    for (int q = 0; q < MAXT; ++q) sm.dcount[b][q] = 0;
-    for (int q = 0; q < MAXR; ++q) sm.devents[b][q] = 0;
-  }
-  if (tid == 0) { sm.carry = 0; sm.any = 0; }
+  const uint32_t* order = d.g->ev_parity ? d.ev_v1 : d.ev_v0;
+  uint32_t* pref = d.g->ev_parity ? d.ev_k0 : d.ev_k1;
+  for (uint32_t b = tid; b < d.n_trains; b += nt) { sm.first_pref[b] = 0; sm.prods_tr[b] = 0; sm.evs_tr[b] = 0; }
+  if (tid == 0) sm.carry = 0;
   __syncthreads();
-  const uint32_t n_live = d.g->n_total - d.g->n_dead;
   for (uint32_t t0 = 0; t0 < E; t0 += nt) {
     const uint32_t k = t0 + tid;
     const bool valid = k < E;
-    Cand cd;
-    uint32_t r = 0, b = 0, np = 0;
+    uint32_t b = 0, np = 0;
+    bool first = false;
     if (valid) {
-      cd = d.cand[order[k]];
-      r = cd.rxn_train & 255u;
-      b = cd.rxn_train >> 8;
-      np = static_cast<uint32_t>(tb.n_prod[r]);
+      const uint32_t rt = d.cand[order[k]].rxn_train;
+      b = rt >> 8;
+      np = static_cast<uint32_t>(tb.n_prod[rt & 255u]);
+      first = (k == 0) || ((d.cand[order[k - 1]].rxn_train >> 8) != b);
     }
     uint32_t tot;
     const uint32_t ex = block_excl_scan(np, sm.warp_tot, tot) + sm.carry;
     if (valid) {
-      bool first = (k == 0);
-      if (!first) first = ((d.cand[order[k - 1]].rxn_train >> 8) != b);
+      pref[k] = ex;
       if (first) sm.first_pref[b] = ex;
-    }
-    __syncthreads();
-    if (valid) {
-      Train& tr = d.trains[b];
-      const uint32_t id0 = tr.next_id + (ex - sm.first_pref[b]);
-      const uint32_t slot0 = n_live + ex;
-      if (slot0 + np > d.cap) {
-        raise_status(d.g, CHEM_ECAPACITY);
-      } else {
-        const uint32_t tlo = tid_type(F32L ? __float_as_uint(d.s4[cd.s_lo].w) : d.stid[cd.s_lo]);
-        const uint32_t thi = tid_type(F32L ? __float_as_uint(d.s4[cd.s_hi].w) : d.stid[cd.s_hi]);
-        if (F32L) {
-          const float4 a = d.s4[cd.s_lo], c = d.s4[cd.s_hi];
-          const uint32_t ca = d.cell_sorted[cd.s_lo], cc = d.cell_sorted[cd.s_hi];
-          const int n = tr.n;
-          const uint32_t la = ca - tr.cell_base, lc = cc - tr.cell_base;
-          int dx = static_cast<int>(lc % n) - static_cast<int>(la % n);
-          int dy = static_cast<int>((lc / n) % n) - static_cast<int>((la / n) % n);
-          int dz = static_cast<int>(lc / (n * n)) - static_cast<int>(la / (n * n));
-          dx = dx > 1 ? dx - n : (dx < -1 ? dx + n : dx);
-          dy = dy > 1 ? dy - n : (dy < -1 ? dy + n : dy);
-          dz = dz > 1 ? dz - n : (dz < -1 ? dz + n : dz);
-          const float w = tb.Df[tlo] / (tb.Df[tlo] + tb.Df[thi]);
-          const float px = a.x + w * (dx * tr.hf + (c.x - a.x));
-          const float py = a.y + w * (dy * tr.hf + (c.y - a.y));
-          const float pz = a.z + w * (dz * tr.hf + (c.z - a.z));
-          for (uint32_t q = 0; q < np; ++q) {
-            const uint32_t pt = static_cast<uint32_t>(tb.prod[r][q]);
-            d.s4[slot0 + q] = make_float4(px, py, pz, __uint_as_float(((id0 + q) << 3) | pt));
-            d.cell_sorted[slot0 + q] = ca;
-            d.dead[slot0 + q] = 0;
-          }
-        } else {
-          const double xa = d.sx[cd.s_lo], ya = d.sy[cd.s_lo], za = d.sz[cd.s_lo];
-          const double rx = min_image(__dsub_rn(d.sx[cd.s_hi], xa), tr.L, tr.halfL);
-          const double ry = min_image(__dsub_rn(d.sy[cd.s_hi], ya), tr.L, tr.halfL);
-          const double rz = min_image(__dsub_rn(d.sz[cd.s_hi], za), tr.L, tr.halfL);
-          const double w = __ddiv_rn(tb.D[tlo], __dadd_rn(tb.D[tlo], tb.D[thi]));
-          const double px = wrap_box(__dadd_rn(xa, __dmul_rn(w, rx)), tr.L, tr.halfL);
-          const double py = wrap_box(__dadd_rn(ya, __dmul_rn(w, ry)), tr.L, tr.halfL);
-          const double pz = wrap_box(__dadd_rn(za, __dmul_rn(w, rz)), tr.L, tr.halfL);
-          for (uint32_t q = 0; q < np; ++q) {
-            const uint32_t pt = static_cast<uint32_t>(tb.prod[r][q]);
-            d.sx[slot0 + q] = px; d.sy[slot0 + q] = py; d.sz[slot0 + q] = pz;
-            d.stid[slot0 + q] = ((id0 + q) << 3) | pt;
-            d.cell_sorted[slot0 + q] = tr.cell_base;
-            d.dead[slot0 + q] = 0;
-          }
-        }
-        atomicSub(&sm.dcount[b][tlo], 1);
-        atomicSub(&sm.dcount[b][thi], 1);
-        for (uint32_t q = 0; q < np; ++q) atomicAdd(&sm.dcount[b][tb.prod[r][q]], 1);
-        atomicAdd(&sm.devents[b][r], 1);
-        if (tb.water[r]) atomicAdd(&sm.dwater[b], tb.water[r]);
-        atomicAdd(&sm.prods_tr[b], np);
-        atomicAdd(&sm.evs_tr[b], 1u);
-        if (d.cap_ev_log) {
-          const uint32_t e = d.g->ev_log_n + k;
-          if (e < d.cap_ev_log) {
-            chem_event ev;
-            ev.step = tr.step; ev.rxn = static_cast<int32_t>(r); ev.id_lo = cd.id_lo; ev.id_hi = cd.id_hi;
-            ev.prod_id0 = id0; ev.n_prod = static_cast<int32_t>(np); ev.train = b; ev.reserved = 0;
-            d.ev_log[e] = ev;
-          } else {
-            raise_status(d.g, CHEM_ECAPACITY);
-          }
-        }
-      }
+      atomicAdd(&sm.prods_tr[b], np);
+      atomicAdd(&sm.evs_tr[b], 1u);
     }
     __syncthreads();
     if (tid == 0) sm.carry += tot;
     __syncthreads();
   }
-  // end of step
+  for (uint32_t b = tid; b < d.n_trains; b += nt) {
+    Train& tr = d.trains[b];
+    tr.pref0 = sm.first_pref[b];
+    tr.prods_step = sm.prods_tr[b];
+    tr.n_events_step = sm.evs_tr[b];
+  }
+  if (tid == 0 && ok) d.g->n_products = sm.carry;
+  __syncthreads();
+}
+
+template <bool F32L>
+__device__ void phase_products(const Dev& d, ProductsSmem& sm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const Tables& tb = *d.tables;
+  for (uint32_t b = tid; b < d.n_trains; b += nt) {
+    sm.dwater[b] = 0;
+    for (int q = 0; q < MAXT; ++q) sm.dcount[b][q] = 0;
+    for (int q = 0; q < MAXR; ++q) sm.devents[b][q] = 0;
+  }
+  const bool ok = block_status_ok(d);
+  const uint32_t E = ok ? d.g->n_events : 0u;
+  const uint32_t* order = d.g->ev_parity ? d.ev_v1 : d.ev_v0;
+  const uint32_t* pref = d.g->ev_parity ? d.ev_k0 : d.ev_k1;
+  const uint32_t n_live = d.g->n_total - d.g->n_dead;
+  for (uint32_t k = blockIdx.x * nt + tid; k < E; k += gridDim.x * nt) {
+    const Cand cd = d.cand[order[k]];
+    const uint32_t r = cd.rxn_train & 255u, b = cd.rxn_train >> 8;
+    const uint32_t np = static_cast<uint32_t>(tb.n_prod[r]);
+    Train& tr = d.trains[b];
+    const uint32_t ex = pref[k];
+    const uint32_t id0 = tr.next_id + (ex - tr.pref0);
+    const uint32_t slot0 = n_live + ex;
+    if (slot0 + np > d.cap) {
+      raise_status(d.g, CHEM_ECAPACITY);
+      continue;
+    }
+    const uint32_t tlo = tid_type(F32L ? __float_as_uint(d.s4[cd.s_lo].w) : d.stid[cd.s_lo]);
+    const uint32_t thi = tid_type(F32L ? __float_as_uint(d.s4[cd.s_hi].w) : d.stid[cd.s_hi]);
+    if (F32L) {
+      const float4 a = d.s4[cd.s_lo], c = d.s4[cd.s_hi];
+      const uint32_t ca = d.cell_sorted[cd.s_lo], cc = d.cell_sorted[cd.s_hi];
+      const int n = tr.n;
+      int ax_, ay_, az_, cx_, cy_, cz_;
+      cell_decode(ca - tr.cell_base, tr.cb, ax_, ay_, az_);
+      cell_decode(cc - tr.cell_base, tr.cb, cx_, cy_, cz_);
+      int dx = cx_ - ax_, dy = cy_ - ay_, dz = cz_ - az_;
+      dx = dx > 1 ? dx - n : (dx < -1 ? dx + n : dx);
+      dy = dy > 1 ? dy - n : (dy < -1 ? dy + n : dy);
+      dz = dz > 1 ? dz - n : (dz < -1 ? dz + n : dz);
+      const float w = tb.Df[tlo] / (tb.Df[tlo] + tb.Df[thi]);
+      const float px = a.x + w * (dx * tr.hf + (c.x - a.x));
+      const float py = a.y + w * (dy * tr.hf + (c.y - a.y));
+      const float pz = a.z + w * (dz * tr.hf + (c.z - a.z));
+      for (uint32_t q = 0; q < np; ++q) {
+        const uint32_t pt = static_cast<uint32_t>(tb.prod[r][q]);
+        d.s4[slot0 + q] = make_float4(px, py, pz, __uint_as_float(((id0 + q) << 3) | pt));
+        d.cell_sorted[slot0 + q] = ca;
+        d.dead[slot0 + q] = 0;
+      }
+    } else {
+      const double xa = d.sx[cd.s_lo], ya = d.sy[cd.s_lo], za = d.sz[cd.s_lo];
+      const double rx = min_image(__dsub_rn(d.sx[cd.s_hi], xa), tr.L, tr.halfL);
+      const double ry = min_image(__dsub_rn(d.sy[cd.s_hi], ya), tr.L, tr.halfL);
+      const double rz = min_image(__dsub_rn(d.sz[cd.s_hi], za), tr.L, tr.halfL);
+      const double w = __ddiv_rn(tb.D[tlo], __dadd_rn(tb.D[tlo], tb.D[thi]));
+      const double px = wrap_box(__dadd_rn(xa, __dmul_rn(w, rx)), tr.L, tr.halfL);
+      const double py = wrap_box(__dadd_rn(ya, __dmul_rn(w, ry)), tr.L, tr.halfL);
+      const double pz = wrap_box(__dadd_rn(za, __dmul_rn(w, rz)), tr.L, tr.halfL);
+      for (uint32_t q = 0; q < np; ++q) {
+        const uint32_t pt = static_cast<uint32_t>(tb.prod[r][q]);
+        d.sx[slot0 + q] = px; d.sy[slot0 + q] = py; d.sz[slot0 + q] = pz;
+        d.stid[slot0 + q] = ((id0 + q) << 3) | pt;
+        d.cell_sorted[slot0 + q] = tr.cell_base;
+        d.dead[slot0 + q] = 0;
+      }
+    }
+    atomicSub(&sm.dcount[b][tlo], 1);
+    atomicSub(&sm.dcount[b][thi], 1);
+    for (uint32_t q = 0; q < np; ++q) atomicAdd(&sm.dcount[b][tb.prod[r][q]], 1);
+    atomicAdd(&sm.devents[b][r], 1);
+    if (tb.water[r]) atomicAdd(&sm.dwater[b], tb.water[r]);
+    if (d.cap_ev_log) {
+      const uint32_t e = d.g->ev_log_n + k;
+      if (e < d.cap_ev_log) {
+        chem_event ev;
+        ev.step = tr.step; ev.rxn = static_cast<int32_t>(r); ev.id_lo = cd.id_lo; ev.id_hi = cd.id_hi;
+        ev.prod_id0 = id0; ev.n_prod = static_cast<int32_t>(np); ev.train = b; ev.reserved = 0;
+        d.ev_log[e] = ev;
+      } else {
+        raise_status(d.g, CHEM_ECAPACITY);
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t b = 0; b < d.n_trains; ++b) {
+    Train& tr = d.trains[b];
+    for (int q = tid; q < MAXT + MAXR + 1; q += nt) {
+      if (q < MAXT) {
+        const int v = sm.dcount[b][q];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&tr.counts[q]),
+                         static_cast<unsigned long long>(static_cast<long long>(v)));
+      } else if (q < MAXT + MAXR) {
+        const int v = sm.devents[b][q - MAXT];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&tr.events[q - MAXT]),
+                         static_cast<unsigned long long>(static_cast<long long>(v)));
+      } else {
+        const int v = sm.dwater[b];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(&tr.water),
+                         static_cast<unsigned long long>(static_cast<long long>(v)));
+      }
+    }
+  }
+}
+
+static __device__ void phase_end_step(const Dev& d, EndSmem& sm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) sm.any = 0;
+  const bool ok = block_status_ok(d);
+  const Tables& tb = *d.tables;
   for (uint32_t b = tid; b < d.n_trains; b += nt) {
     Train& tr = d.trains[b];
     if (tr.active && ok) {
-      for (int q = 0; q < tb.n_types; ++q) tr.counts[q] += sm.dcount[b][q];
-      for (int q = 0; q < tb.n_rxn; ++q) tr.events[q] += sm.devents[b][q];
-      tr.water += sm.dwater[b];
-      tr.next_id += sm.prods_tr[b];
-      tr.n_events_step = sm.evs_tr[b];
+      tr.next_id += tr.prods_step;
       tr.species_steps += tr.n_live_step;
       if (d.cap_step_log) {
         const uint32_t e = atomicAdd(&d.g->step_log_n, 1u);
         if (e < d.cap_step_log) {
           chem_step_record rec;
           rec.step = tr.step; rec.train = b; rec.t_start_s = tr.t_start; rec.dt_s = tr.dt;
-          rec.n_live = tr.n_live_step; rec.n_events = sm.evs_tr[b];
+          rec.n_live = tr.n_live_step; rec.n_events = tr.n_events_step;
           for (int q = 0; q < 8; ++q) rec.counts[q] = q < tb.n_types ? tr.counts[q] : 0;
           d.step_log[e] = rec;
         } else {
@@ -978,9 +1192,9 @@ __device__ void phase_products(const Dev& d, ProductsSmem& sm) {
     for (uint32_t b = 0; b < d.n_trains; ++b) stepped |= d.trains[b].active != 0;
     if (ok && stepped) d.g->steps_active += 1;
     if (ok) {
-      d.g->n_products = sm.carry;
-      d.g->n_total = n_live + sm.carry;
-      if (d.cap_ev_log) d.g->ev_log_n += E;
+      const uint32_t n_live = d.g->n_total - d.g->n_dead;
+      d.g->n_total = n_live + d.g->n_products;
+      if (d.cap_ev_log) d.g->ev_log_n += d.g->n_events;
     }
     d.g->any_active = sm.any;
   }

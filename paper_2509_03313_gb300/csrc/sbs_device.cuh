@@ -31,7 +31,7 @@ constexpr int REACT_THREADS = 1024;
 constexpr int ITEM_HOME = 64;   // home species per pair-search work item (one cell)
 constexpr int N_FWD = 14;       // own cell + 13 forward neighbour cells (half shell)
 constexpr double END_SLACK = 1.0 + 1e-6;    // last-step trim slack (relative)
-constexpr double CELL_SLACK = 1.0 + 1e-6;   // hash cell >= cutoff * CELL_SLACK
+constexpr float CELL_SLACK_F = 1.0001f;    // hash cell >= cutoff * CELL_SLACK_F
 constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 // Chemistry shared by all trains of a context (Table 1, Table S2).
@@ -56,7 +56,10 @@ struct Train {
   double L, halfL, dt_min, dt_max, dt_growth, dt_L, c, horizon;
   uint32_t key0, key1;
   int reset_on_release;
-  int n_max;               // cells per axis limit
+  int n_max;               // cells per axis limit used at run time (<= n_alloc)
+  int n_alloc;             // cells per axis the hash table is allocated for
+  int cb;                  // bits per axis of the local cell index (n_alloc <= 2^cb)
+  double inv_L;
   uint32_t cell_base;      // first global cell of this train
   uint32_t pend_base;      // first pending slot of this train
   uint32_t pend_cap;
@@ -84,6 +87,8 @@ struct Train {
   double ddt[MAXR];        // D_AB dt per reaction (bridge denominator)
   float inv_ddt_f[MAXR];   // 1 / (D_AB dt) in FP32 (first tier of the acceptance test)
   uint32_t rel_n, rel_off, rel_id0, rel_p0;
+  uint32_t pref0;          // product prefix of this train's first event (this step)
+  uint32_t prods_step;     // products created by this train this step
   long long n_live_step;
   uint32_t n_events_step;
   uint32_t pad_;
@@ -106,6 +111,11 @@ struct Global {
   uint32_t err_where;
   uint32_t steps_active;  // steps in which at least one train advanced
   uint32_t n_items;       // pair-search work items emitted by the gather
+  uint32_t item_home;     // home species per pair-search work item (<= ITEM_HOME)
+  uint32_t n_conflict;    // accepted pairs sharing a species with another accepted pair
+  uint32_t item_ctr;      // next pair-search work item (work stealing)
+  uint32_t sort_parity;   // number of non-trivial passes of this step's cell sort, mod 2
+  uint32_t ev_parity;     // the same for the event sort
   uint32_t ev_tile_ctr[MAX_PASSES];
   uint32_t ev_hist[MAX_PASSES][RADIX];  // digit histograms of the event keys
   uint32_t pad_[1];
@@ -136,6 +146,7 @@ struct Dev {
   uint32_t* cell_sorted;
   uint32_t* keys0; uint32_t* keys1; uint32_t* vals0; uint32_t* vals1;
   uint8_t* dead;
+  uint32_t* touch;       // accepted pairs per slot this step (zero between steps)
   int4* cell_info;
   unsigned long long* lookback;
   uint32_t max_tiles;
@@ -171,6 +182,23 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+// Local cell index with power-of-two strides: ix | iy << cb | iz << 2 cb.
+__device__ __forceinline__ uint32_t cell_encode(int ix, int iy, int iz, int cb) {
+  return static_cast<uint32_t>(ix) | (static_cast<uint32_t>(iy) << cb) |
+         (static_cast<uint32_t>(iz) << (2 * cb));
+}
+__device__ __forceinline__ void cell_decode(uint32_t loc, int cb, int& ix, int& iy, int& iz) {
+  const uint32_t m = (1u << cb) - 1u;
+  ix = static_cast<int>(loc & m);
+  iy = static_cast<int>((loc >> cb) & m);
+  iz = static_cast<int>(loc >> (2 * cb));
+}
+// i + d wrapped into [0, n) for |d| <= n.
+__device__ __forceinline__ int step_cell(int i, int d, int n) {
+  i += d;
+  return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
 // Train owning a global cell: largest b with cell_base[b] <= cell (bases ascending).
