@@ -218,7 +218,12 @@ def run_gpu_arm(args):
     for name, prec, k_steps in modes:
         ctx, keep = make_ctx(chem, wl, prec, seed0, cap, stream.cuda_stream, alloc,
                              profiling=not args.no_phase_events)
+        tuned = None
         try:
+            if name == "fp32l" and not args.no_autotune:
+                chem.chem_reset(ctx, seed0 + 3)
+                chem.chem_inject_pulse(ctx, pulse.types, pulse.xyz, pulse.t_arrival, pulse.energy_eV)
+                tuned = chem.chem_autotune(ctx, args.autotune_ms)
             for w in range(args.warmup):
                 trajectory(chem, ctx, pulse, seed0 + 7 + w, wl.t_end, torch, stream, flush, ev)
             if not args.no_phase_events:
@@ -260,6 +265,7 @@ def run_gpu_arm(args):
         results[name] = dict(times=times, ss=ss, tot=tot, G_H2O2=g_h2o2, G_OH=g_oh, G_e=g_e,
                              launches=st1["kernel_launches"] - st0["kernel_launches"],
                              phases=per_phase, clocks=clk.summary(), e2e_t=e2e_t, e2e_ss=e2e_ss,
+                             tuned=tuned,
                              h2d=h2d_per, d2h=8 * 7 + 8 * 7 + 8 * 9 + 16)
     # aggregate over ranks (replicas): sum of species-steps over the max time
     r = results["fp32l"]
@@ -294,6 +300,8 @@ def run_gpu_arm(args):
                    "mode": "FP32-local positions, FP64 clock/probabilities/tallies",
                    "l2": "flushed (256 MiB write) before every timed trajectory",
                    "phase_events": not args.no_phase_events,
+                   "autotuned": None if r["tuned"] is None else
+                   dict(zip(("steps_per_launch", "cells_per_axis_limit", "species_per_item"), r["tuned"])),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "e2e": {"value": (r["e2e_ss"] / sum(r["e2e_t"])) if r["e2e_t"] else None, "unit": UNIT,
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
@@ -323,9 +331,69 @@ def run_gpu_arm(args):
                                 "rel_diff": float(abs(g32.mean() - g64.mean()) / g64.mean()),
                                 "sigma_rel": float(math.sqrt(g32.var(ddof=1) / len(g32) + g64.var(ddof=1) / len(g64)) / g64.mean())
                                 if len(g32) > 1 and len(g64) > 1 else None}
+    if not args.no_batched:
+        bres = run_batched(args, chem, W, torch, stream, alloc, flush)
+        line["batched"] = bres
+        if "fp64" in line and bres.get("value"):
+            line["speedup_batched_fp32l_over_plain_fp64"] = bres["value"] / line["fp64"]["value"]
     line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_batched(args, chem, W, torch, stream, alloc, flush):
+    """64 independent pulse trains of the dose-rate sweep (10 us window) advanced
+    together in one context: one hash for all trains, one persistent cooperative launch
+    per graph replay, parameters chosen by chem_autotune."""
+    wls = W.batched_sweep(scale=args.batch_scale)
+    cfgs, keep = [], []
+    for b, wl in enumerate(wls):
+        s = wl.schedule
+        n = wl.n_species
+        cfg, k = chem.make_config(
+            wl.L, wl.D, wl.reactions, seed=77 + b, train_id=b, precision=chem.CHEM_FP32_LOCAL,
+            dt_min=s.dt_min, dt_max=s.dt_max, dt_growth=s.dt_growth, sbs_horizon=s.sbs_horizon,
+            capacity_species=int(n * 1.3) + 4096, capacity_pending=n + 16,
+            capacity_candidates=max(4096, n // 2), stream=stream.cuda_stream, allocator=alloc)
+        cfgs.append(cfg)
+        keep.append(k)
+    ctx = chem.chem_batch_init(cfgs)
+    ends = [wl.t_end for wl in wls]
+
+    def load(seed_base):
+        chem.chem_batch_reset(ctx, [seed_base + b for b in range(len(wls))])
+        for b, wl in enumerate(wls):
+            for p in wl.pulses:
+                chem.chem_batch_inject(ctx, b, p.types, p.xyz, p.t_arrival, p.energy_eV)
+
+    try:
+        load(500)
+        tuned = chem.chem_autotune(ctx, args.autotune_ms)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        times, ss = [], 0
+        for k in range(args.batch_reps + 1):
+            load(600 + 100 * k)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[0].record(stream)
+            chem.chem_batch_run_until(ctx, ends)
+            with torch.cuda.stream(stream):
+                ev[1].record(stream)
+            ev[1].synchronize()
+            if k == 0:
+                continue  # warm-up repetition
+            times.append(ev[0].elapsed_time(ev[1]) * 1e-3)
+            ss += sum(chem.chem_batch_tally(ctx, b, 7, 9)["species_steps"] for b in range(len(wls)))
+        stats = chem.chem_get_stats(ctx)
+    finally:
+        chem.chem_destroy(ctx)
+    return {"value": ss / sum(times), "unit": UNIT, "trains": len(wls),
+            "species": int(sum(w.n_species for w in wls)), "reps": len(times),
+            "ms_per_rep": 1e3 * sum(times) / len(times), "window_s": wls[0].t_end,
+            "mode": "FP32-local, persistent cooperative launch per graph replay",
+            "autotuned": dict(zip(("steps_per_launch", "cells_per_axis_limit", "species_per_item"), tuned)),
+            "workload": "dose-rate sweep: 64 trains, Dav log-spaced 0.01-1e5 Gy/s at Dp 2e5 and 1e6 Gy/s, "
+                        "species log-spaced 1e4-2e6 per 10 pulses, pulses of 4 bunches, 10 us window"}
 
 
 def main():
@@ -343,6 +411,11 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-phase-events", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune-ms", type=float, default=1500.0)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-scale", type=float, default=1.0)
+    ap.add_argument("--batch-reps", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference_arm(args)

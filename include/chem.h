@@ -50,6 +50,7 @@ typedef enum chem_status {
 } chem_status;
 
 enum { CHEM_FP64 = 0, CHEM_FP32_LOCAL = 1 };
+enum { CHEM_LAUNCH_AUTO = 0, CHEM_LAUNCH_PHASES = 1, CHEM_LAUNCH_PERSISTENT = 2 };
 enum { CHEM_MAX_TYPES = 8, CHEM_MAX_RXN = 16, CHEM_MAX_PRODUCTS = 3 };
 
 /* One diffusion-controlled reaction A + B -> products (Table 1). */
@@ -97,6 +98,9 @@ typedef struct chem_config {
   int64_t capacity_step_log;   /* >0: keep up to this many per-step records            */
   int32_t cells_per_axis_max;  /* spatial-hash resolution limit; 0 = automatic         */
   int32_t steps_per_launch;    /* steps per captured graph replay; 0 = automatic       */
+  int32_t launch_mode;         /* CHEM_LAUNCH_AUTO: persistent for batches, one kernel
+                                  per phase otherwise; CHEM_LAUNCH_PHASES;
+                                  CHEM_LAUNCH_PERSISTENT (cooperative, grid barriers)  */
   void* cuda_stream;           /* cudaStream_t to run on; NULL = library-owned stream  */
   chem_alloc_fn dev_alloc;     /* NULL = cudaMalloc / cudaFree                         */
   chem_free_fn dev_free;
@@ -198,10 +202,14 @@ chem_status chem_batch_get_state(chem_ctx* ctx, int32_t train, int64_t cap, int3
 chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds);
 int32_t chem_batch_size(const chem_ctx* ctx);
 
-/* Choose the steps per graph replay and the hash cell-size factor by timing short
- * replays (state is saved and restored around the trials). budget_ms bounds the time
- * spent. Reports the choice through chosen[2] = {steps_per_launch, cell_factor_x100}
- * when chosen is not NULL. */
+/* Choose, by timing short runs from the current state, the steps per graph replay,
+ * the hash resolution limit (cells per axis at small cutoffs, i.e. the cell size) and
+ * the number of species one warp takes per pair-search work item (the threads per
+ * cell). The device state is saved before and restored after every trial; trials run
+ * past the end time. FP64 results do not depend on the choice; FP32-local results
+ * depend on the hash resolution only through rounding. budget_ms bounds the time spent
+ * (at least one trial runs). chosen[3] = {steps_per_launch, cells_per_axis_limit,
+ * species_per_item} when chosen is not NULL. */
 chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen);
 
 /* Counters of a context since chem_init (host side, exact). Phase indices:
@@ -234,7 +242,7 @@ chem_status chem_set_profiling(chem_ctx* ctx, int32_t on);
  * created by chem_init with dt_min = dt_max = dt_s would take that step.
  *
  * Memory: it calls no cudaMalloc, cudaFree or allocator callback. All working memory is
- * one file-scope __device__ array of about 3.6 MB sized for CHEM_NOALLOC_MAX_SPECIES
+ * one file-scope __device__ array of about 3.7 MB sized for CHEM_NOALLOC_MAX_SPECIES
  * species; every GPU that loads this library holds that array until the process exits.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any

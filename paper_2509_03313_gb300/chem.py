@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libchem.so")
 
 CHEM_OK, CHEM_EINVAL, CHEM_ENOMEM, CHEM_ECAPACITY, CHEM_ECUDA, CHEM_ETIMEOUT, CHEM_ESTATE = range(7)
 CHEM_FP64, CHEM_FP32_LOCAL = 0, 1
+CHEM_LAUNCH_AUTO, CHEM_LAUNCH_PHASES, CHEM_LAUNCH_PERSISTENT = 0, 1, 2
 STATUS_NAMES = {0: "CHEM_OK", 1: "CHEM_EINVAL", 2: "CHEM_ENOMEM", 3: "CHEM_ECAPACITY",
                 4: "CHEM_ECUDA", 5: "CHEM_ETIMEOUT", 6: "CHEM_ESTATE"}
 
@@ -44,6 +45,7 @@ class chem_config(ctypes.Structure):
         ("capacity_candidates", ctypes.c_int64), ("capacity_event_log", ctypes.c_int64),
         ("capacity_step_log", ctypes.c_int64),
         ("cells_per_axis_max", ctypes.c_int32), ("steps_per_launch", ctypes.c_int32),
+        ("launch_mode", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p),
         ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", ctypes.c_void_p),
     ]
@@ -176,7 +178,8 @@ def make_config(L_nm: float, D: Sequence[float], reactions, seed: int = 0, train
                 sbs_horizon: float = 0.0, capacity_species: int = 1 << 16,
                 capacity_pending: Optional[int] = None, capacity_candidates: Optional[int] = None,
                 capacity_event_log: int = 0, capacity_step_log: int = 0,
-                cells_per_axis_max: int = 0, steps_per_launch: int = 0, stream=None,
+                cells_per_axis_max: int = 0, steps_per_launch: int = 0,
+                launch_mode: int = CHEM_LAUNCH_AUTO, stream=None,
                 allocator: Optional[torch_allocator] = None):
     """Build a chem_config. Returns (config, keepalive); keep both alive while in use.
     ``reactions`` holds objects with a, b, k_tab, products, water_delta (or tuples)."""
@@ -211,6 +214,7 @@ def make_config(L_nm: float, D: Sequence[float], reactions, seed: int = 0, train
     cfg.capacity_step_log = capacity_step_log
     cfg.cells_per_axis_max = cells_per_axis_max
     cfg.steps_per_launch = steps_per_launch
+    cfg.launch_mode = launch_mode
     if stream is not None:
         cfg.cuda_stream = ctypes.c_void_p(int(stream))
     if allocator is not None:
@@ -349,9 +353,10 @@ def chem_batch_reset(ctx, seeds):
 
 
 def chem_autotune(ctx, budget_ms: float = 2000.0):
-    chosen = np.zeros(2, np.int32)
+    """Returns (steps_per_launch, cells_per_axis_limit, species_per_item)."""
+    chosen = np.zeros(3, np.int32)
     _check(ctx, lib().chem_autotune(ctx, float(budget_ms), _ptr(chosen)))
-    return int(chosen[0]), int(chosen[1])
+    return int(chosen[0]), int(chosen[1]), int(chosen[2])
 
 
 def chem_last_error(ctx) -> str:

@@ -2,6 +2,7 @@
 // the pending-species queue, CUDA-graph capture of the step kernels and the run loop.
 // The host never computes a step: it only queues kernels and copies data.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -497,7 +498,12 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
   ctx->th.resize(n_trains);
   for (int b = 0; b < n_trains; ++b) ctx->th[b].cfg = cfgs[b];
   if (c0.steps_per_launch > 0) ctx->steps_per_launch = c0.steps_per_launch;
-  ctx->persistent = n_trains > 1;
+  if (c0.launch_mode < CHEM_LAUNCH_AUTO || c0.launch_mode > CHEM_LAUNCH_PERSISTENT) {
+    delete ctx;
+    return CHEM_EINVAL;
+  }
+  ctx->persistent = c0.launch_mode == CHEM_LAUNCH_PERSISTENT ||
+                    (c0.launch_mode == CHEM_LAUNCH_AUTO && n_trains > 1);
 
   // ---- chemistry tables
   Tables& T = ctx->tables;
@@ -666,7 +672,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     d.td4 = static_cast<float4*>(A(cap * 16));
   }
   d.cap_items = static_cast<uint32_t>(cap + cap / ITEM_HOME + 64);
-  d.items = static_cast<uint32_t*>(A(static_cast<size_t>(d.cap_items) * 4));
+  d.items = static_cast<uint2*>(A(static_cast<size_t>(d.cap_items) * 8));
   d.cell_sorted = static_cast<uint32_t*>(A(cap * 4));
   {
     uint32_t* sortbuf = static_cast<uint32_t*>(A(cap * 16));  // keys0|keys1|vals0|vals1
@@ -678,6 +684,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
   d.dead = static_cast<uint8_t*>(A(cap));
   d.touch = static_cast<uint32_t*>(A(cap * 4));
   d.cell_info = static_cast<int4*>(A((cells + 1) * 16));
+  d.cstamp = static_cast<uint8_t*>(A(cells + 1));
   d.lookback = static_cast<unsigned long long*>(A(static_cast<size_t>(d.max_tiles) * RADIX * 8));
   d.cand = static_cast<Cand*>(A(cand * sizeof(Cand)));
   const uint64_t evn = std::max<uint64_t>(cand, RADIX);
@@ -710,6 +717,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
   CK(cudaMemsetAsync(d.dead, 0, cap, ctx->stream));
   CK(cudaMemsetAsync(d.touch, 0, cap * 4, ctx->stream));
   CK(cudaMemsetAsync(d.cell_info, 0xFF, (cells + 1) * 16, ctx->stream));
+  CK(cudaMemsetAsync(d.cstamp, 0xFF, cells + 1, ctx->stream));
   CK(cudaMemsetAsync(d.lookback, 0, static_cast<size_t>(d.max_tiles) * RADIX * 8, ctx->stream));
   CK(cudaMemcpyAsync(tables_dev, &T, sizeof(Tables), cudaMemcpyHostToDevice, ctx->stream));
   chem_status gs = init_global(ctx);
@@ -812,6 +820,7 @@ chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds) {
   CK(cudaMemsetAsync(ctx->d.dead, 0, ctx->d.cap, ctx->stream));
   CK(cudaMemsetAsync(ctx->d.touch, 0, static_cast<size_t>(ctx->d.cap) * 4, ctx->stream));
   CK(cudaMemsetAsync(ctx->d.cell_info, 0xFF, (static_cast<size_t>(ctx->d.total_cells) + 1) * 16, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d.cstamp, 0xFF, static_cast<size_t>(ctx->d.total_cells) + 1, ctx->stream));
   CK(cudaMemsetAsync(ctx->d.lookback, 0, static_cast<size_t>(ctx->d.max_tiles) * RADIX * 8, ctx->stream));
   s = upload_trains(ctx, tr);
   if (s) return s;
@@ -847,11 +856,152 @@ chem_status chem_set_profiling(chem_ctx* ctx, int32_t on) {
 }
 
 chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
-  if (!ctx) return CHEM_EINVAL;
-  (void)budget_ms;
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  if (!(budget_ms > 0.0)) return CHEM_EINVAL;
+  // ---- snapshot of everything a step changes (pending data and tables do not change)
+  s = download_global(ctx);
+  if (s) return s;
+  const uint32_t n = ctx->g_pinned->n_total;
+  Dev& d = ctx->d;
+  const bool f64 = ctx->precision == CHEM_FP64;
+  const size_t state_b = f64 ? 28 : 16;
+  const size_t snap_bytes = static_cast<size_t>(n) * (state_b + 4 + 1) + sizeof(Train) * ctx->B + sizeof(Global) + 256;
+  unsigned char* snap = static_cast<unsigned char*>(dev_alloc(ctx, snap_bytes));
+  if (!snap) return fail(ctx, CHEM_ENOMEM, "autotune snapshot allocation failed");
+  auto copies = [&](bool save) -> cudaError_t {
+    size_t o = 0;
+    auto cp = [&](void* dev, size_t bytes) {
+      cudaError_t e = save ? cudaMemcpyAsync(snap + o, dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream)
+                           : cudaMemcpyAsync(dev, snap + o, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+      o += bytes;
+      return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (n) {
+      if (f64) {
+        e = cp(d.sx, n * 8ull); if (e) return e;
+        e = cp(d.sy, n * 8ull); if (e) return e;
+        e = cp(d.sz, n * 8ull); if (e) return e;
+        e = cp(d.stid, n * 4ull); if (e) return e;
+      } else {
+        e = cp(d.s4, n * 16ull); if (e) return e;
+      }
+      e = cp(d.cell_sorted, n * 4ull); if (e) return e;
+      e = cp(d.dead, n); if (e) return e;
+    }
+    return cp(d.trains, sizeof(Train) * ctx->B);
+  };
+  const size_t global_off = static_cast<size_t>(n) * (state_b + 4 + 1) + sizeof(Train) * ctx->B;
+  CK(copies(true));
+  CK(cudaMemcpyAsync(snap + global_off, d.g, sizeof(Global), cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<Train> tr0;
+  s = download_trains(ctx, tr0);
+  if (s) return s;
+  // ---- candidates: runtime hash limit, species per work item, steps per replay
+  const int n_alloc = tr0[0].n_alloc;
+  std::vector<int> n_cands;
+  for (double f : {1.0, 0.75, 0.55, 0.4}) n_cands.push_back(std::max(3, static_cast<int>(n_alloc * f)));
+  const int ih_cands[3] = {16, 32, 64};
+  const int spl_cands[2] = {8, 32};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const auto t_start = std::chrono::steady_clock::now();
+  double best_rate = -1.0;
+  int best_n = tr0[0].n_max, best_ih = ctx->item_home, best_spl = ctx->steps_per_launch;
+  const int saved_spl = ctx->steps_per_launch;
+  const bool saved_prof = ctx->profiling;
+  ctx->profiling = false;
+  for (int spl : spl_cands) {
+    ctx->steps_per_launch = spl;
+    s = capture_graph(ctx);
+    if (s) break;
+    for (int nm : n_cands) {
+      for (int ih : ih_cands) {
+        const double spent = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        if (spent > budget_ms && best_rate > 0.0) break;
+        // restore the state, then set this trial's parameters and an open end time
+        CK(copies(false));
+        const uint32_t epoch_now = ctx->g_pinned->epoch;
+        CK(cudaMemcpyAsync(d.g, snap + global_off, sizeof(Global), cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        std::vector<Train> tr = tr0;
+        for (auto& t : tr) { t.n_max = std::min(nm, t.n_alloc); t.t_end = std::numeric_limits<double>::infinity(); }
+        s = upload_trains(ctx, tr);
+        if (s) break;
+        Global& gfix = *ctx->g_pinned;
+        CK(cudaMemcpyAsync(&gfix, d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        gfix.epoch = std::max(gfix.epoch, epoch_now) + 1;  // stale hash stamps never match
+        gfix.item_home = static_cast<uint32_t>(ih);
+        CK(cudaMemcpyAsync(d.g, &gfix, sizeof(Global), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        const int reps = std::max(1, 24 / spl);
+        CK(cudaGraphLaunch(ctx->graph, ctx->stream));  // settle
+        CK(cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < reps; ++r) CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->g_pinned, d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        std::vector<Train> after;
+        s = download_trains(ctx, after);
+        if (s) break;
+        if (ctx->g_pinned->status != 0) {
+          // a trial ran out of a capacity (e.g. candidates on a coarse grid): skip it
+          CK(cudaMemsetAsync(&d.g->status, 0, sizeof(int), ctx->stream));
+          continue;
+        }
+        long long ss = 0;
+        for (int b = 0; b < ctx->B; ++b) ss += after[b].species_steps;
+        // steps of the settle replay are included in ss; subtract them with the rate of
+        // the timed part by counting the timed replays' share
+        const double timed_frac = static_cast<double>(reps) / (reps + 1);
+        const double rate = ms > 0.f ? (static_cast<double>(ss - [&] { long long z = 0; for (int b = 0; b < ctx->B; ++b) z += tr0[b].species_steps; return z; }()) * timed_frac) / (ms * 1e-3) : 0.0;
+        if (rate > best_rate) { best_rate = rate; best_n = nm; best_ih = ih; best_spl = spl; }
+      }
+    }
+    if (s) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // ---- restore the state and apply the best parameters
+  CK(copies(false));
+  {
+    const uint32_t epoch_now = ctx->g_pinned->epoch;
+    Global& gfix = *ctx->g_pinned;
+    CK(cudaMemcpyAsync(&gfix, snap + global_off, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    gfix.epoch = std::max(gfix.epoch, epoch_now) + 1;
+    gfix.item_home = static_cast<uint32_t>(best_ih);
+    CK(cudaMemcpyAsync(d.g, &gfix, sizeof(Global), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  for (auto& t : tr0) t.n_max = std::min(best_n, t.n_alloc);
+  chem_status s2 = upload_trains(ctx, tr0);
+  // release the snapshot
+  for (size_t i = 0; i < ctx->allocs.size(); ++i) {
+    if (ctx->allocs[i].first == snap) {
+      if (ctx->dfree) ctx->dfree(snap, ctx->allocs[i].second, ctx->alloc_user);
+      else cudaFree(snap);
+      ctx->allocs.erase(ctx->allocs.begin() + static_cast<long>(i));
+      break;
+    }
+  }
+  if (s) return s;
+  if (s2) return s2;
+  ctx->item_home = best_ih;
+  ctx->steps_per_launch = best_rate > 0.0 ? best_spl : saved_spl;
+  ctx->profiling = saved_prof;
+  s = capture_graph(ctx);
+  if (s) return s;
   if (chosen) {
     chosen[0] = ctx->steps_per_launch;
-    chosen[1] = ctx->cell_factor_x100;
+    chosen[1] = best_n;
+    chosen[2] = best_ih;
   }
   return ctx->status;
 }

@@ -31,7 +31,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(25
 
 // Byte layout of the scratch array.
 struct Layout {
-  size_t sx, sy, sz, stid, tx, ty, tz, ttid, tdx, tdy, tdz, items, touch, cell_sorted, sortbuf, dead, cell_info, lookback, cand,
+  size_t sx, sy, sz, stid, tx, ty, tz, ttid, tdx, tdy, tdz, items, touch, cell_sorted, sortbuf, dead, cell_info, cstamp, lookback, cand,
       ev_list, alive0, alive1, ev_k0, ev_k1, ev_v0, ev_v1, ev_log, step_log, pend, trains, tables,
       global, total;
 };
@@ -44,12 +44,13 @@ constexpr Layout make_layout() {
   L.sx = take(M * 8); L.sy = take(M * 8); L.sz = take(M * 8); L.stid = take(M * 4);
   L.tx = take(M * 8); L.ty = take(M * 8); L.tz = take(M * 8); L.ttid = take(M * 4);
   L.tdx = take(M * 8); L.tdy = take(M * 8); L.tdz = take(M * 8);
-  L.items = take((M + M / ITEM_HOME + 64) * 4);
+  L.items = take((M + M / ITEM_HOME + 64) * 8);
   L.touch = take(M * 4);
   L.cell_sorted = take(M * 4);
   L.sortbuf = take(M * 16);
   L.dead = take(M);
   L.cell_info = take((NA_CELLS + 1) * 16);
+  L.cstamp = take(NA_CELLS + 1);
   L.lookback = take(static_cast<size_t>(NA_TILES) * RADIX * 8);
   L.cand = take(C * sizeof(Cand));
   L.ev_list = take(C * 4); L.alive0 = take(C * 4); L.alive1 = take(C * 4);
@@ -69,7 +70,7 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = LAYOUT.total;
 
 }  // namespace
 
-// The shared working memory of chem_step_noalloc (about 3.6 MB).
+// The shared working memory of chem_step_noalloc (about 3.7 MB).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -276,7 +277,7 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   d.tdx = reinterpret_cast<double*>(b + LAYOUT.tdx);
   d.tdy = reinterpret_cast<double*>(b + LAYOUT.tdy);
   d.tdz = reinterpret_cast<double*>(b + LAYOUT.tdz);
-  d.items = reinterpret_cast<uint32_t*>(b + LAYOUT.items);
+  d.items = reinterpret_cast<uint2*>(b + LAYOUT.items);
   d.touch = reinterpret_cast<uint32_t*>(b + LAYOUT.touch);
   d.cap_items = NA_MAX_SPECIES + NA_MAX_SPECIES / ITEM_HOME + 64;
   d.cell_sorted = reinterpret_cast<uint32_t*>(b + LAYOUT.cell_sorted);
@@ -287,6 +288,7 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   d.vals1 = sortbuf + 3 * NA_MAX_SPECIES;
   d.dead = b + LAYOUT.dead;
   d.cell_info = reinterpret_cast<int4*>(b + LAYOUT.cell_info);
+  d.cstamp = b + LAYOUT.cstamp;
   d.lookback = reinterpret_cast<unsigned long long*>(b + LAYOUT.lookback);
   d.max_tiles = NA_TILES;
   d.cand = reinterpret_cast<Cand*>(b + LAYOUT.cand);
@@ -320,6 +322,7 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   cudaStream_t s = static_cast<cudaStream_t>(cfg->cuda_stream);
   // leftovers of the previous call: stale hash cells and look-back words must not match
   bool ok = cudaMemsetAsync(d.cell_info, 0xFF, (NA_CELLS + 1) * 16, s) == cudaSuccess &&
+            cudaMemsetAsync(d.cstamp, 0xFF, NA_CELLS + 1, s) == cudaSuccess &&
             cudaMemsetAsync(d.touch, 0, NA_MAX_SPECIES * 4, s) == cudaSuccess &&
             cudaMemsetAsync(d.lookback, 0, static_cast<size_t>(NA_TILES) * RADIX * 8, s) == cudaSuccess;
   if (ok) {

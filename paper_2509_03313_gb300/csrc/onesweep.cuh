@@ -57,7 +57,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t v, uint32_t
 }
 
 // One pass over n keys by digit (key >> shift) & 255. ghist = this digit's histogram
-// over all n keys. Must be called by all SORT_THREADS threads of every CTA.
+// over all n keys; vin == nullptr means value = input index. Must be called by all
+// SORT_THREADS threads of every CTA.
 static __device__ void onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
                               int shift, const uint32_t* ghist, uint32_t* tile_ctr,
@@ -89,7 +90,7 @@ static __device__ void onesweep_pass(const uint32_t* __restrict__ kin, const uin
       const uint32_t idx = wbase + r * 32 + lane;
       const bool valid = idx < n;
       key[r] = valid ? kin[idx] : 0xFFFFFFFFu;
-      val[r] = valid ? vin[idx] : 0u;
+      val[r] = valid ? (vin ? vin[idx] : idx) : 0u;
     }
 #pragma unroll
     for (int r = 0; r < SORT_ITEMS; ++r) {

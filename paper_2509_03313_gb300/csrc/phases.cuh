@@ -127,6 +127,7 @@ __device__ __forceinline__ int wrap_cell(int i, int n) {
 // cutoffs of this step; then the slot offsets of the releases and the step counters.
 struct BeginSmem {
   uint32_t rel[MAX_TRAINS];
+  double dt[MAX_TRAINS];
   unsigned long long rcmax_bits[MAX_TRAINS];
   uint32_t any;
 };
@@ -142,51 +143,62 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
   const Tables& tb = *d.tables;
   for (uint32_t b = tid; b < d.n_trains; b += nt) {
     Train& tr = d.trains[b];
-    const bool act = (st == 0) && (tr.t < tr.t_end);
+    // independent loads first: the per-train work below is one short dependency chain
+    const double t = tr.t, t_end = tr.t_end, t_lr = tr.t_last_release, horizon = tr.horizon;
+    const double dt_min = tr.dt_min, dt_L = tr.dt_L;
+    double dt_cur = tr.dt_cur;
+    const uint32_t p_head = tr.p_head, p_tail = tr.p_tail, pend_base = tr.pend_base;
+    const uint32_t next_id = tr.next_id, id_limit = tr.id_limit;
+    const int reset = tr.reset_on_release;
+    long long live = 0;
+    for (int ty = 0; ty < MAXT; ++ty) live += (ty < tb.n_types) ? tr.counts[ty] : 0;
+    const bool act = (st == 0) && (t < t_end);
     uint32_t rel = 0;
     int free_jump = 0;
+    double dt = 0.0;
     sb.rcmax_bits[b] = 0ull;
     if (act) {
       // pending arrivals are sorted; release those with arrival <= t
-      uint32_t lo = tr.p_head, hi = tr.p_tail;
-      const double* pt = d.pt + tr.pend_base;
+      uint32_t lo = p_head, hi = p_tail;
+      const double* pt = d.pt + pend_base;
       while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (pt[mid] <= tr.t) lo = mid + 1; else hi = mid;
+        if (pt[mid] <= t) lo = mid + 1; else hi = mid;
       }
-      rel = lo - tr.p_head;
+      rel = lo - p_head;
+      double t_last = t_lr;
       if (rel > 0) {
-        tr.t_last_release = tr.t;
-        if (tr.reset_on_release) tr.dt_cur = tr.dt_min;
+        t_last = t;
+        tr.t_last_release = t;
+        if (reset) dt_cur = dt_min;
       }
-      const double next_arr = (lo < tr.p_tail) ? pt[lo] : CUDART_INF;
-      double dt, t_next;
-      if (tr.horizon > 0.0 && __dsub_rn(tr.t, tr.t_last_release) >= tr.horizon && next_arr > tr.t) {
+      const double next_arr = (lo < p_tail) ? pt[lo] : CUDART_INF;
+      double t_next;
+      if (horizon > 0.0 && __dsub_rn(t, t_last) >= horizon && next_arr > t) {
         free_jump = 1;
-        t_next = fmin(tr.t_end, next_arr);
-        dt = __dsub_rn(t_next, tr.t);
+        t_next = fmin(t_end, next_arr);
+        dt = __dsub_rn(t_next, t);
       } else {
-        dt = fmin(tr.dt_cur, tr.dt_L);
-        if (__dsub_rn(tr.t_end, tr.t) <= __dmul_rn(dt, END_SLACK)) {
-          dt = __dsub_rn(tr.t_end, tr.t);
-          t_next = tr.t_end;
+        dt = fmin(dt_cur, dt_L);
+        if (__dsub_rn(t_end, t) <= __dmul_rn(dt, END_SLACK)) {
+          dt = __dsub_rn(t_end, t);
+          t_next = t_end;
         } else {
-          t_next = __dadd_rn(tr.t, dt);
+          t_next = __dadd_rn(t, dt);
         }
       }
+      tr.dt_cur = dt_cur;
       tr.dt = dt;
       tr.t_next = t_next;
-      tr.t_start = tr.t;
+      tr.t_start = t;
       tr.rel_n = rel;
-      tr.rel_id0 = tr.next_id;
-      tr.rel_p0 = tr.p_head;
-      tr.p_head += rel;
-      tr.next_id += rel;
-      long long live = rel;
-      for (int ty = 0; ty < tb.n_types; ++ty) live += tr.counts[ty];
-      tr.n_live_step = live;
+      tr.rel_id0 = next_id;
+      tr.rel_p0 = p_head;
+      tr.p_head = p_head + rel;
+      tr.next_id = next_id + rel;
+      tr.n_live_step = live + rel;
       tr.n_events_step = 0;
-      if (tr.next_id > tr.id_limit) raise_status(d.g, CHEM_ECAPACITY);
+      if (next_id + rel > id_limit) raise_status(d.g, CHEM_ECAPACITY);
       atomicOr(&sb.any, 1u);
     } else {
       tr.rel_n = 0;
@@ -194,6 +206,7 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     tr.active = act ? 1 : 0;
     tr.free_jump = free_jump;
     sb.rel[b] = rel;
+    sb.dt[b] = act ? dt : 0.0;
   }
   __syncthreads();
   // cutoffs R + c sqrt(2 D_AB dt), bridge constants, and sigma = sqrt(2 D dt)
@@ -201,9 +214,9 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
   for (uint32_t w = tid; w < d.n_trains * per; w += nt) {
     const uint32_t b = w / per;
     const int q = static_cast<int>(w % per);
+    const double dt = sb.dt[b];
+    if (dt <= 0.0) continue;  // train not advancing this step
     Train& tr = d.trains[b];
-    if (!tr.active) continue;
-    const double dt = tr.dt;
     if (q < MAXR) {
       if (q >= tb.n_rxn) continue;
       const double rc = __dadd_rn(tb.R[q], __dmul_rn(tr.c, sqrt(__dmul_rn(__dmul_rn(2.0, tb.D_AB[q]), dt))));
@@ -221,32 +234,39 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
   }
   __syncthreads();
   for (uint32_t b = tid; b < d.n_trains; b += nt) {
+    if (sb.dt[b] <= 0.0) continue;
     Train& tr = d.trains[b];
-    if (!tr.active) continue;
+    const double L = tr.L, inv_L = tr.inv_L;
+    const int n_max = tr.n_max, fj = tr.free_jump;
+    int n_ref = tr.n_ref;
     const double rcmax = __longlong_as_double(static_cast<long long>(sb.rcmax_bits[b]));
     // finest admissible grid: cells at least the largest cutoff (with slack)
-    int n_target = tr.n_max;
+    int n_target = n_max;
     if (rcmax > 0.0) {
-      const float nf = floorf(static_cast<float>(tr.L) / (static_cast<float>(rcmax) * CELL_SLACK_F));
-      n_target = max(3, min(tr.n_max, static_cast<int>(fminf(nf, 1048576.f))));
+      const float nf = floorf(static_cast<float>(L) / (static_cast<float>(rcmax) * CELL_SLACK_F));
+      n_target = max(3, min(n_max, static_cast<int>(fminf(nf, 1048576.f))));
+    }
+    if (n_ref == 0) {  // first step after init or reset
+      n_ref = n_target;
+      tr.n_ref = n_target;
+      tr.h_ref = __ddiv_rn(L, static_cast<double>(n_target));
     }
     // keep the current grid while it is valid and at most 2x too coarse; when the
     // cutoff outgrows it, move to cells 1.2x larger than needed (fewer regrids)
-    if (tr.n_ref == 0) {  // first step after init or reset
-      tr.n_ref = n_target;
-      tr.h_ref = __ddiv_rn(tr.L, static_cast<double>(n_target));
-    }
-    int n = tr.n_ref;
-    if (!tr.free_jump) {
+    int n = n_ref;
+    if (!fj) {
       if (n > n_target) n = max(3, (5 * n_target) / 6);
       else if (2 * n < n_target) n = n_target;
     }
+    const double h = __ddiv_rn(L, static_cast<double>(n));
+    const double inv_h = __dmul_rn(static_cast<double>(n), inv_L);
     tr.n = n;
-    tr.h = __ddiv_rn(tr.L, static_cast<double>(n));
-    tr.inv_h = __dmul_rn(static_cast<double>(n), tr.inv_L);
-    tr.hf = static_cast<float>(tr.h);
-    tr.inv_hf = static_cast<float>(tr.inv_h);
+    tr.h = h;
+    tr.inv_h = inv_h;
+    tr.hf = static_cast<float>(h);
+    tr.inv_hf = static_cast<float>(inv_h);
   }
+
   if (tid == 0) {
     Global* g = d.g;
     uint32_t off = g->n_total;
@@ -439,8 +459,7 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
           key = tr.cell_base + cell_encode(ix, iy, iz, tr.cb);
         }
       }
-      d.keys0[s] = key;
-      d.vals0[s] = s;
+      d.keys0[s] = key;  // the first radix pass takes the slot itself as the value
       for (int p = 0; p < d.passes; ++p) atomicAdd(&hist[p][(key >> (8 * p)) & 255u], 1u);
     }
   }
@@ -483,12 +502,14 @@ static __device__ void phase_sort_pass(const Dev& d, int pass, SortSmem& sm) {
   const uint32_t n = d.g->n_total;
   int before = 0;
   const bool act = pass_active(d.g->hist, pass, n, &before);
-  if (pass == d.passes - 1 && blockIdx.x == 0 && threadIdx.x == 0)
+  if (pass == d.passes - 1 && blockIdx.x == 0 && threadIdx.x == 0) {
     d.g->sort_parity = static_cast<uint32_t>((before + (act ? 1 : 0)) & 1);
+    d.g->sort_any = (before + (act ? 1 : 0)) > 0 ? 1u : 0u;
+  }
   if (!act) return;
   const bool odd = before & 1;
   const uint32_t* kin = odd ? d.keys1 : d.keys0;
-  const uint32_t* vin = odd ? d.vals1 : d.vals0;
+  const uint32_t* vin = before == 0 ? nullptr : (odd ? d.vals1 : d.vals0);  // nullptr: value = index
   uint32_t* kout = odd ? d.keys0 : d.keys1;
   uint32_t* vout = odd ? d.vals0 : d.vals1;
   onesweep_pass(kin, vin, kout, vout, n, 8 * pass, d.g->hist[pass], &d.g->tile_ctr[pass],
@@ -502,14 +523,14 @@ template <bool F32L>
 __device__ void phase_gather(const Dev& d) {
   if (status_of(d)) return;
   const uint32_t* kf = d.g->sort_parity ? d.keys1 : d.keys0;
-  const uint32_t* vf = d.g->sort_parity ? d.vals1 : d.vals0;
+  const uint32_t* vf = d.g->sort_any ? (d.g->sort_parity ? d.vals1 : d.vals0) : nullptr;
   const uint32_t n_live = d.g->n_total - d.g->n_dead;
   const uint32_t epoch = d.g->epoch;
   const uint32_t item_home = d.g->item_home;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_live; s += stride) {
     const uint32_t key = kf[s];
-    const uint32_t i = vf[s];
+    const uint32_t i = vf ? vf[s] : s;
     if (key >= d.sentinel || i >= d.g->n_total) {  // only after a timed-out sort
       raise_status(d.g, CHEM_ETIMEOUT);
       continue;
@@ -522,14 +543,18 @@ __device__ void phase_gather(const Dev& d) {
     d.cell_sorted[s] = key;
     int* ci = reinterpret_cast<int*>(&d.cell_info[key]);
     const bool first = (s == 0 || kf[s - 1] != key);
-    if (first) { ci[0] = static_cast<int>(s); ci[2] = static_cast<int>(epoch); }
+    if (first) {
+      ci[0] = static_cast<int>(s);
+      ci[2] = static_cast<int>(epoch);
+      d.cstamp[key] = static_cast<uint8_t>(epoch);
+    }
     if (s + 1 == n_live || kf[s + 1] != key) ci[1] = static_cast<int>(s + 1);
     // pair-search work item: a cell's first slot and every ITEM_HOME-th slot
     if (first || (s % item_home) == 0) {
       const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, key);
       if (d.trains[b].active && !d.trains[b].free_jump) {
         const uint32_t it = atomicAdd(&d.g->n_items, 1u);
-        if (it < d.cap_items) d.items[it] = s;
+        if (it < d.cap_items) d.items[it] = make_uint2(s, key);
         else raise_status(d.g, CHEM_ECAPACITY);
       }
     }
@@ -562,13 +587,11 @@ struct SearchWarpSmem;
 template <>
 struct SearchWarpSmem<true> {
   float4 pos[ITEM_HOME];   // offsets + tid bits
-  float4 dl[ITEM_HOME];    // this step's displacement
 };
 
 template <>
 struct SearchWarpSmem<false> {
   double x[ITEM_HOME], y[ITEM_HOME], z[ITEM_HOME];
-  double ex[ITEM_HOME], ey[ITEM_HOME], ez[ITEM_HOME];
   uint32_t tid[ITEM_HOME];
 };
 
@@ -585,11 +608,34 @@ struct CutoffTable {
   T rc2[MAXT * MAXT];
 };
 
+// Pairs inside the cutoff, queued per warp and resolved with one pair per lane.
+template <bool F32L>
+struct PairQueue;
+
+template <>
+struct PairQueue<true> {
+  static constexpr int CAP = 96;
+  uint32_t hj[CAP];                  // home index in the item
+  uint32_t j[CAP];                   // neighbour slot
+  float fx[CAP], fy[CAP], fz[CAP], f2[CAP];
+  uint32_t n;
+};
+
+template <>
+struct PairQueue<false> {
+  static constexpr int CAP = 64;
+  uint32_t hj[CAP];
+  uint32_t j[CAP];
+  double rx[CAP], ry[CAP], rz[CAP], d2[CAP];
+  uint32_t n;
+};
+
 template <bool F32L>
 struct SearchSmem {
   SearchWarpSmem<F32L> w[8];
   SearchRanges rg[8];
   CutoffTable<F32L> ct[8];
+  PairQueue<F32L> q[8];
   int ct_train[8];
 };
 
@@ -654,8 +700,9 @@ __device__ __forceinline__ void pair_accept(const Dev& d, const Tables& tb, cons
   const uint32_t si = s0 + h;
   if constexpr (F32L) {
     if (!i_lo) { fx = -fx; fy = -fy; fz = -fz; }
-    const float4 di = hs.dl[h];
-    const float4 dj = d.td4[vf[j]];
+    // this step's displacements, stored by the diffusion in pre-sort order
+    const float4 di = d.td4[vf ? vf[si] : si];
+    const float4 dj = d.td4[vf ? vf[j] : j];
     const float4 dlo = i_lo ? di : dj, dhi = i_lo ? dj : di;
     const float r0x = fx - (dhi.x - dlo.x), r0y = fy - (dhi.y - dlo.y), r0z = fz - (dhi.z - dlo.z);
     const float d0sq = r0x * r0x + r0y * r0y + r0z * r0z;
@@ -664,10 +711,12 @@ __device__ __forceinline__ void pair_accept(const Dev& d, const Tables& tb, cons
   } else {
     // r1 = minimum image of x_hi - x_lo, recomputed in that orientation as the reference does
     if (!i_lo) { rx1 = -rx1; ry1 = -ry1; rz1 = -rz1; }
-    const uint32_t tj_idx = vf[j];
+    // this step's displacements, stored by the diffusion in pre-sort order
+    const uint32_t tj_idx = vf ? vf[j] : j, ti_idx = vf ? vf[si] : si;
     const double ejx = d.tdx[tj_idx], ejy = d.tdy[tj_idx], ejz = d.tdz[tj_idx];
-    const double elx = i_lo ? hs.ex[h] : ejx, ely = i_lo ? hs.ey[h] : ejy, elz = i_lo ? hs.ez[h] : ejz;
-    const double ehx = i_lo ? ejx : hs.ex[h], ehy = i_lo ? ejy : hs.ey[h], ehz = i_lo ? ejz : hs.ez[h];
+    const double eix = d.tdx[ti_idx], eiy = d.tdy[ti_idx], eiz = d.tdz[ti_idx];
+    const double elx = i_lo ? eix : ejx, ely = i_lo ? eiy : ejy, elz = i_lo ? eiz : ejz;
+    const double ehx = i_lo ? ejx : eix, ehy = i_lo ? ejy : eiy, ehz = i_lo ? ejz : eiz;
     const double r0x = __dsub_rn(rx1, __dsub_rn(ehx, elx));
     const double r0y = __dsub_rn(ry1, __dsub_rn(ehy, ely));
     const double r0z = __dsub_rn(rz1, __dsub_rn(ehz, elz));
@@ -680,28 +729,59 @@ __device__ __forceinline__ void pair_accept(const Dev& d, const Tables& tb, cons
   }
 }
 
+// Resolve the queued pairs, one per lane (the warp is converged here).
+template <bool F32L>
+__device__ __forceinline__ void flush_pairs(const Dev& d, const Tables& tb, const Train& tr, int b,
+                                            const SearchWarpSmem<F32L>& hs, PairQueue<F32L>& q,
+                                            uint32_t s0, const uint32_t* vf, int lane) {
+  const uint32_t nq = q.n;
+  for (uint32_t e = lane; e < nq; e += 32) {
+    const uint32_t h = q.hj[e], j = q.j[e];
+    uint32_t tid_j;
+    if constexpr (F32L) tid_j = __float_as_uint(d.s4[j].w);
+    else tid_j = d.stid[j];
+    if constexpr (F32L)
+      pair_accept<true>(d, tb, tr, b, hs, h, s0, j, tid_j, q.fx[e], q.fy[e], q.fz[e], q.f2[e], 0.0, 0.0,
+                        0.0, 0.0, vf);
+    else
+      pair_accept<false>(d, tb, tr, b, hs, h, s0, j, tid_j, 0.f, 0.f, 0.f, 0.f, q.d2[e], q.rx[e], q.ry[e],
+                         q.rz[e], vf);
+  }
+  __syncwarp();
+  if (lane == 0) q.n = 0;
+  __syncwarp();
+}
+
 template <bool F32L>
 __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
   if (status_of(d)) return;
   const uint32_t n_items = min(d.g->n_items, d.cap_items);
+  const uint32_t n_live = d.g->n_total - d.g->n_dead;
   const uint32_t epoch = d.g->epoch;
-  const uint32_t* vf = d.g->sort_parity ? d.vals1 : d.vals0;
+  // pre-sort slot of each sorted slot; nullptr when no radix pass moved anything
+  const uint32_t* vf = d.g->sort_any ? (d.g->sort_parity ? d.vals1 : d.vals0) : nullptr;
   const Tables& tb = *d.tables;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   SearchWarpSmem<F32L>& hs = sm.w[wib];
   SearchRanges& rg = sm.rg[wib];
   auto& ct = sm.ct[wib];
-  if (lane == 0) sm.ct_train[wib] = -1;
+  PairQueue<F32L>& q = sm.q[wib];
+  if (lane == 0) { sm.ct_train[wib] = -1; q.n = 0; }
   __syncwarp();
   const uint32_t item_home = d.g->item_home;
+  // work stealing, one item ahead: the next item's index and record are fetched while
+  // the current item computes
+  uint32_t it_next = 0;
+  if (lane == 0) it_next = atomicAdd(&d.g->item_ctr, 1u);
+  it_next = __shfl_sync(0xffffffffu, it_next, 0);
+  uint2 rec_next = make_uint2(0u, 0u);
+  if (it_next < n_items) rec_next = d.items[it_next];
   for (;;) {
-    // work stealing: one item per warp at a time
-    uint32_t it = 0;
-    if (lane == 0) it = atomicAdd(&d.g->item_ctr, 1u);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= n_items) break;
-    const uint32_t s0 = d.items[it];
-    const uint32_t cell = d.cell_sorted[s0];
+    if (it_next >= n_items) break;
+    const uint2 rec = rec_next;
+    uint32_t it_ahead = 0;
+    if (lane == 0) it_ahead = atomicAdd(&d.g->item_ctr, 1u);
+    const uint32_t s0 = rec.x, cell = rec.y;
     const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
     const Train& tr = d.trains[b];
     if (sm.ct_train[wib] != b) {  // cutoff table of this train (warp-uniform)
@@ -713,45 +793,22 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
       __syncwarp();
       if (lane == 0) sm.ct_train[wib] = b;
     }
-    const int4 ci = d.cell_info[cell];
-    const uint32_t s_end = min(static_cast<uint32_t>(ci.y), (s0 / item_home + 1) * item_home);
-    const uint32_t nh = s_end - s0;
-    // stage the home species; OR of the types they react with
-    uint32_t want = 0;
-    for (uint32_t h = lane; h < nh; h += 32) {
-      const uint32_t s = s0 + h;
-      const uint32_t ti = vf[s];
-      uint32_t t;
-      if constexpr (F32L) {
-        const float4 v = d.s4[s];
-        hs.pos[h] = v;
-        hs.dl[h] = d.td4[ti];
-        t = __float_as_uint(v.w);
-      } else {
-        hs.x[h] = d.sx[s]; hs.y[h] = d.sy[s]; hs.z[h] = d.sz[s];
-        hs.ex[h] = d.tdx[ti]; hs.ey[h] = d.tdy[ti]; hs.ez[h] = d.tdz[ti];
-        t = d.stid[s];
-        hs.tid[h] = t;
-      }
-      want |= tb.reactive_mask[tid_type(t)];
-    }
-    want = __reduce_or_sync(0xffffffffu, want);
-    __syncwarp();
-    if (!want) continue;
-    // neighbour ranges of the half shell
+    // in parallel: own cell range (lane 0), the 13 forward cells (lanes 1-13) and the
+    // home species, staged speculatively up to the item size
     const int n = tr.n;
     int ix, iy, iz;
     cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
-    uint32_t rs = 0, rl = 0;
-    if (lane < N_FWD) {
-      if (lane == 0) {
-        rs = s0 + 1;
-        rl = static_cast<uint32_t>(ci.y) - rs;
-      } else {
-        int ox, oy, oz;
-        fwd_offset(lane, ox, oy, oz);
-        const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, ox, n), step_cell(iy, oy, n),
-                                                       step_cell(iz, oz, n), tr.cb);
+    uint32_t rs = 0, rl = 0, own_end = 0;
+    if (lane == 0) {
+      own_end = static_cast<uint32_t>(d.cell_info[cell].y);
+    } else if (lane < N_FWD) {
+      int ox, oy, oz;
+      fwd_offset(lane, ox, oy, oz);
+      const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, ox, n), step_cell(iy, oy, n),
+                                                     step_cell(iz, oz, n), tr.cb);
+      // one byte per cell (L2-resident) filters the empty cells; the 16-byte entry with
+      // its full epoch decides
+      if (d.cstamp[nc] == static_cast<uint8_t>(epoch)) {
         const int4 nci = d.cell_info[nc];
         if (static_cast<uint32_t>(nci.z) == epoch) {
           rs = static_cast<uint32_t>(nci.x);
@@ -759,6 +816,29 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
         }
       }
     }
+    const uint32_t stage_end = min(n_live, (s0 / item_home + 1) * item_home);
+    for (uint32_t h = lane; s0 + h < stage_end; h += 32) {
+      const uint32_t s = s0 + h;
+      if constexpr (F32L) {
+        hs.pos[h] = d.s4[s];
+      } else {
+        hs.x[h] = d.sx[s]; hs.y[h] = d.sy[s]; hs.z[h] = d.sz[s];
+        hs.tid[h] = d.stid[s];
+      }
+    }
+    own_end = __shfl_sync(0xffffffffu, own_end, 0);
+    const uint32_t s_end = min(own_end, stage_end);
+    const uint32_t nh = s_end - s0;
+    if (lane == 0) { rs = s0 + 1; rl = own_end - rs; }
+    __syncwarp();
+    uint32_t want = 0;
+    for (uint32_t h = lane; h < nh; h += 32) {
+      uint32_t t;
+      if constexpr (F32L) t = __float_as_uint(hs.pos[h].w);
+      else t = hs.tid[h];
+      want |= tb.reactive_mask[tid_type(t)];
+    }
+    want = __reduce_or_sync(0xffffffffu, want);
     uint32_t incl = rl;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -766,56 +846,87 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
       if (lane >= o) incl += y;
     }
     const uint32_t excl = incl - rl;
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, N_FWD - 1);
+    const uint32_t total = want ? __shfl_sync(0xffffffffu, incl, N_FWD - 1) : 0u;
     if (lane < N_FWD) { rg.start[lane] = rs; rg.off[lane] = excl; }
+    // the stolen index is needed only now; fetch the record of the item after this one
+    it_next = __shfl_sync(0xffffffffu, it_ahead, 0);
+    if (it_next < n_items) rec_next = d.items[it_next];
     __syncwarp();
     // lanes -> (neighbour, home group): with fewer than 32 neighbours several home rows
-    // are processed at once so that no lane idles
+    // are processed at once so that no lane idles. Both loops have warp-uniform trip
+    // counts; pairs inside the cutoff go to the warp's queue, which is resolved one
+    // pair per lane whenever it could overflow and at the end of the item.
     uint32_t T2 = 32;
     if (total < 32) { T2 = 1; while (T2 < total) T2 <<= 1; }
     const uint32_t G = 32 / T2, hg = lane / T2;
-    for (uint32_t f = lane & (T2 - 1); f < total; f += T2) {
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+    for (uint32_t f0 = 0; f0 < total; f0 += T2) {
+      const uint32_t f = f0 + (lane & (T2 - 1));
+      bool lane_on = f < total;
       int k = 0;
-#pragma unroll
-      for (int q = 1; q < N_FWD; ++q) k += (rg.off[q] <= f) ? 1 : 0;
-      const uint32_t j = rg.start[k] + (f - rg.off[k]);
-      uint32_t tid_j;
+      uint32_t j = 0, tid_j = 0;
       float4 vj = make_float4(0.f, 0.f, 0.f, 0.f);
       double xj = 0, yj = 0, zj = 0;
-      if constexpr (F32L) { vj = d.s4[j]; tid_j = __float_as_uint(vj.w); }
-      else { tid_j = d.stid[j]; }
-      const uint32_t tj = tid_type(tid_j);
-      if (!((want >> tj) & 1u)) continue;
-      if constexpr (!F32L) { xj = d.sx[j]; yj = d.sy[j]; zj = d.sz[j]; }
-      const auto* row = &ct.rc2[tj * MAXT];
+      if (lane_on) {
+#pragma unroll
+        for (int q = 1; q < N_FWD; ++q) k += (rg.off[q] <= f) ? 1 : 0;
+        j = rg.start[k] + (f - rg.off[k]);
+        if constexpr (F32L) { vj = d.s4[j]; tid_j = __float_as_uint(vj.w); }
+        else { tid_j = d.stid[j]; }
+        lane_on = (want >> tid_type(tid_j)) & 1u;
+        if constexpr (!F32L) { if (lane_on) { xj = d.sx[j]; yj = d.sy[j]; zj = d.sz[j]; } }
+      }
+      const auto* row = &ct.rc2[tid_type(tid_j) * MAXT];
       // own cell: only home slots below j
-      const uint32_t hmax = (k == 0) ? min(nh, j - s0) : nh;
+      const uint32_t hmax = lane_on ? ((k == 0) ? min(nh, j - s0) : nh) : 0u;
       int odx, ody, odz;
       fwd_offset(k, odx, ody, odz);
       const float cx = odx * tr.hf, cy = ody * tr.hf, cz = odz * tr.hf;
-      for (uint32_t h = hg; h < hmax; h += G) {
-        if constexpr (F32L) {
-          const float4 vi = hs.pos[h];
-          const float rc2 = row[__float_as_uint(vi.w) & 7u];
-          const float fx = cx + (vj.x - vi.x), fy = cy + (vj.y - vi.y), fz = cz + (vj.z - vi.z);
-          const float f2 = fx * fx + fy * fy + fz * fz;
-          if (f2 < rc2)
-            pair_accept<true>(d, tb, tr, b, hs, h, s0, j, tid_j, fx, fy, fz, f2, 0.0, 0.0, 0.0, 0.0, vf);
-        } else {
-          const double rc2 = row[hs.tid[h] & 7u];
-          if (rc2 < 0.0) continue;
-          // minimum image of x_j - x_i (Eq. 2); the reference orients it x_hi - x_lo, and
-          // negating an exactly computed separation is exact, so the orientation can be
-          // fixed afterwards without changing a bit
-          const double rx1 = min_image(__dsub_rn(xj, hs.x[h]), tr.L, tr.halfL);
-          const double ry1 = min_image(__dsub_rn(yj, hs.y[h]), tr.L, tr.halfL);
-          const double rz1 = min_image(__dsub_rn(zj, hs.z[h]), tr.L, tr.halfL);
-          const double d1sq = sq3(rx1, ry1, rz1);
-          if (d1sq < rc2)
-            pair_accept<false>(d, tb, tr, b, hs, h, s0, j, tid_j, 0.f, 0.f, 0.f, 0.f, d1sq, rx1, ry1, rz1, vf);
+      for (uint32_t h0 = 0; h0 < nh; h0 += G) {
+        const uint32_t h = h0 + hg;
+        bool pass = false;
+        float fx = 0.f, fy = 0.f, fz = 0.f, f2 = 0.f;
+        double rx1 = 0, ry1 = 0, rz1 = 0, d1sq = 0;
+        if (h < hmax) {
+          if constexpr (F32L) {
+            const float4 vi = hs.pos[h];
+            const float rc2 = row[__float_as_uint(vi.w) & 7u];
+            fx = cx + (vj.x - vi.x); fy = cy + (vj.y - vi.y); fz = cz + (vj.z - vi.z);
+            f2 = fx * fx + fy * fy + fz * fz;
+            pass = f2 < rc2;
+          } else {
+            const double rc2 = row[hs.tid[h] & 7u];
+            if (rc2 >= 0.0) {
+              // minimum image of x_j - x_i (Eq. 2). The reference orients it x_hi - x_lo;
+              // for any pair inside the cutoff (|dx| < L/2) negating this exactly
+              // computed separation gives that orientation bit for bit
+              rx1 = min_image(__dsub_rn(xj, hs.x[h]), tr.L, tr.halfL);
+              ry1 = min_image(__dsub_rn(yj, hs.y[h]), tr.L, tr.halfL);
+              rz1 = min_image(__dsub_rn(zj, hs.z[h]), tr.L, tr.halfL);
+              d1sq = sq3(rx1, ry1, rz1);
+              pass = d1sq < rc2;
+            }
+          }
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, pass);
+        if (bal) {
+          const uint32_t base = q.n;
+          if (pass) {
+            const uint32_t pos = base + __popc(bal & lanemask_lt);
+            q.hj[pos] = h;
+            q.j[pos] = j;
+            if constexpr (F32L) { q.fx[pos] = fx; q.fy[pos] = fy; q.fz[pos] = fz; q.f2[pos] = f2; }
+            else { q.rx[pos] = rx1; q.ry[pos] = ry1; q.rz[pos] = rz1; q.d2[pos] = d1sq; }
+          }
+          __syncwarp();
+          if (lane == 0) q.n = base + __popc(bal);
+          __syncwarp();
+          if (q.n > static_cast<uint32_t>(PairQueue<F32L>::CAP) - 32u)
+            flush_pairs<F32L>(d, tb, tr, b, hs, q, s0, vf, lane);
         }
       }
     }
+    flush_pairs<F32L>(d, tb, tr, b, hs, q, s0, vf, lane);
     __syncwarp();
   }
 }

@@ -115,6 +115,7 @@ struct Global {
   uint32_t n_conflict;    // accepted pairs sharing a species with another accepted pair
   uint32_t item_ctr;      // next pair-search work item (work stealing)
   uint32_t sort_parity;   // number of non-trivial passes of this step's cell sort, mod 2
+  uint32_t sort_any;      // at least one pass executed (else the order is unchanged)
   uint32_t ev_parity;     // the same for the event sort
   uint32_t ev_tile_ctr[MAX_PASSES];
   uint32_t ev_hist[MAX_PASSES][RADIX];  // digit histograms of the event keys
@@ -139,15 +140,16 @@ struct Dev {
   double* sx; double* sy; double* sz; uint32_t* stid;
   double* tx; double* ty; double* tz; uint32_t* ttid;
   float4* s4; float4* t4;
-  double* tdx; double* tdy; double* tdz;  // FP64 displacement of this step, T order
-  float4* td4;                            // FP32-local displacement of this step, T order
-  uint32_t* items;                        // pair-search work items (first home slot)
+  double* tdx; double* tdy; double* tdz;  // FP64 displacement of this step, pre-sort order
+  float4* td4;                            // FP32-local displacement of this step, pre-sort order
+  uint2* items;                           // pair-search work items {first home slot, cell}
   uint32_t cap_items;
   uint32_t* cell_sorted;
   uint32_t* keys0; uint32_t* keys1; uint32_t* vals0; uint32_t* vals1;
   uint8_t* dead;
   uint32_t* touch;       // accepted pairs per slot this step (zero between steps)
   int4* cell_info;
+  uint8_t* cstamp;       // low byte of the epoch of each cell's last occupancy
   unsigned long long* lookback;
   uint32_t max_tiles;
   Cand* cand;

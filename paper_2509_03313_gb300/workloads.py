@@ -244,3 +244,38 @@ def dose_rate_sweep(n_trains: int = 64, seed: int = 0, n_min: int = 10_000,
                         n_pulses=n_pulses, fwhm_s=fwhm_s, sbs_horizon=sbs_horizon,
                         seed=seed * 1000 + b))
     return out
+
+
+def batched_sweep(n_trains: int = 64, seed: int = 0, scale: float = 1.0, t_sim: float = 10e-6,
+                  bunches: int = 4, fwhm_s: float = 1e-6, n_min: int = 10_000,
+                  n_max: int = 2_000_000) -> List[Workload]:
+    """Batched dose-rate sweep, one Workload per train: the trains of ``dose_rate_sweep``
+    (species per train log-spaced over [n_min, n_max] * scale, spread over 10 pulses)
+    simulated over the same window [0, t_sim). Each square pulse of width fwhm_s is
+    delivered as ``bunches`` equally spaced bunches of tracks; pulses repeat with the
+    train's period Dp / Dav, so high average dose rates put several pulses (and the
+    species they leave behind) into the window."""
+    out = []
+    for desc in dose_rate_sweep(n_trains, seed, int(n_min * scale), int(n_max * scale),
+                                fwhm_s=fwhm_s):
+        b = desc["train"]
+        L = desc["L"]
+        per_pulse = desc["species_per_pulse"]
+        n_tracks = max(2, int(round(160 * (L / 5000.0) ** 2)))
+        per_track = max(1, per_pulse // n_tracks)
+        pulses = []
+        k = 0
+        while k * desc["period_s"] < t_sim and k < desc["n_pulses"]:
+            t0 = k * desc["period_s"]
+            for q in range(bunches):
+                tb = t0 + fwhm_s * q / bunches
+                if tb >= t_sim:
+                    break
+                pulses.append(track_pulse(max(1, n_tracks // bunches), L, per_track, desc["seed"],
+                                          t0=tb, stream=10_000 + 100 * k + q))
+            k += 1
+        out.append(Workload(f"sweep{b}", L, pulses,
+                            Schedule(dt_min=1e-11, dt_max=1e-7, dt_growth=LOG_GROWTH_20_PER_DECADE,
+                                     sbs_horizon=desc["sbs_horizon"]),
+                            t_end=t_sim))
+    return out

@@ -14,7 +14,8 @@ def cuda_available():
 
 
 def gpu_run(wl, seed, precision=chem.CHEM_FP64, t_end=None, capacity=None, record=True,
-            steps_per_launch=0, cells_per_axis_max=0, train_id=0, t_stops=None):
+            steps_per_launch=0, cells_per_axis_max=0, train_id=0, t_stops=None,
+            launch_mode=chem.CHEM_LAUNCH_AUTO):
     import torch
     s = wl.schedule
     n = wl.n_species
@@ -26,7 +27,7 @@ def gpu_run(wl, seed, precision=chem.CHEM_FP64, t_end=None, capacity=None, recor
         capacity_pending=max(n, 1), capacity_candidates=max(4096, cap // 2),
         capacity_event_log=(4 * n + 1024) if record else 0,
         capacity_step_log=200000 if record else 0, steps_per_launch=steps_per_launch,
-        cells_per_axis_max=cells_per_axis_max,
+        cells_per_axis_max=cells_per_axis_max, launch_mode=launch_mode,
         stream=torch.cuda.current_stream().cuda_stream, allocator=chem.torch_allocator(0))
     ctx = chem.chem_init(cfg)
     out = {}
@@ -89,8 +90,10 @@ def assert_fp64_parity(g, o, L, pos_tol_rel=1e-12):
     # per-step clock
     t_o = np.array([s[1] for s in o.step_log])
     dt_o = np.array([s[2] for s in o.step_log])
-    assert np.array_equal(g["steps"]["t_start_s"], t_o)
-    assert np.array_equal(g["steps"]["dt_s"], dt_o)
+    for name, got, ref in (("t_start", g["steps"]["t_start_s"], t_o), ("dt", g["steps"]["dt_s"], dt_o)):
+        bad = np.nonzero(got != ref)[0]
+        assert bad.size == 0, (f"{name} differs at step {bad[0]} of {got.size}: "
+                               f"gpu {got[bad[0]]!r} oracle {ref[bad[0]]!r}")
     tal = g["tally"]
     assert np.array_equal(tal["counts"], o.counts())
     assert np.array_equal(tal["events"], o.events_total)
@@ -103,3 +106,48 @@ def assert_fp64_parity(g, o, L, pos_tol_rel=1e-12):
         d = gx - ox
         d = d - L * np.round(d / L)
         assert np.abs(d).max() <= pos_tol_rel * L, np.abs(d).max()
+
+
+def gpu_batch_run(wls, seeds, train_ids=None, precision=chem.CHEM_FP64, record=True,
+                  launch_mode=chem.CHEM_LAUNCH_AUTO, steps_per_launch=0, t_end=None):
+    """Run several trains in one batched context; returns one result dict per train."""
+    import torch
+    train_ids = train_ids or list(range(len(wls)))
+    cfgs, keep = [], []
+    for wl, seed, tid in zip(wls, seeds, train_ids):
+        s = wl.schedule
+        n = wl.n_species
+        cap = max(4096, 2 * n)
+        cfg, k = chem.make_config(
+            wl.L, wl.D, wl.reactions, seed=seed, train_id=tid, precision=precision,
+            dt_min=s.dt_min, dt_max=s.dt_max, dt_growth=s.dt_growth,
+            reset_on_release=s.reset_on_release, cutoff_c=s.cutoff_c, sbs_horizon=s.sbs_horizon,
+            capacity_species=cap, capacity_pending=max(n, 1), capacity_candidates=max(4096, cap // 2),
+            capacity_event_log=(4 * n + 1024) if record else 0,
+            capacity_step_log=200000 if record else 0, steps_per_launch=steps_per_launch,
+            launch_mode=launch_mode, stream=torch.cuda.current_stream().cuda_stream,
+            allocator=chem.torch_allocator(0))
+        cfgs.append(cfg)
+        keep.append(k)
+    ctx = chem.chem_batch_init(cfgs)
+    outs = []
+    try:
+        for b, wl in enumerate(wls):
+            for p in wl.pulses:
+                chem.chem_batch_inject(ctx, b, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        ends = [t_end if t_end is not None else wl.t_end for wl in wls]
+        chem.chem_batch_run_until(ctx, ends)
+        ev = chem.chem_get_events(ctx) if record else None
+        st = chem.chem_get_step_log(ctx) if record else None
+        for b, wl in enumerate(wls):
+            o = {"tally": chem.chem_batch_tally(ctx, b, wl.n_types, len(wl.reactions))}
+            ids, types, xyz = chem.chem_batch_get_state(ctx, b)
+            order = np.argsort(ids)
+            o["state"] = (ids[order].astype(np.int64), types[order].astype(np.int64), xyz[order])
+            if record:
+                o["events"] = ev[ev["train"] == b]
+                o["steps"] = st[st["train"] == b]
+            outs.append(o)
+    finally:
+        chem.chem_destroy(ctx)
+    return outs
