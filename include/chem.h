@@ -202,14 +202,15 @@ chem_status chem_batch_get_state(chem_ctx* ctx, int32_t train, int64_t cap, int3
 chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds);
 int32_t chem_batch_size(const chem_ctx* ctx);
 
-/* Choose, by timing short runs from the current state, the steps per graph replay,
+/* Choose, by timing short runs from the current state, the launch form (one kernel per
+ * phase in a graph, or the persistent cooperative kernel), the steps per graph replay,
  * the hash resolution limit (cells per axis at small cutoffs, i.e. the cell size) and
  * the number of species one warp takes per pair-search work item (the threads per
  * cell). The device state is saved before and restored after every trial; trials run
  * past the end time. FP64 results do not depend on the choice; FP32-local results
  * depend on the hash resolution only through rounding. budget_ms bounds the time spent
- * (at least one trial runs). chosen[3] = {steps_per_launch, cells_per_axis_limit,
- * species_per_item} when chosen is not NULL. */
+ * (at least one trial runs). chosen[4] = {steps_per_launch, cells_per_axis_limit,
+ * species_per_item, launch_mode} when chosen is not NULL. */
 chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen);
 
 /* Counters of a context since chem_init (host side, exact). Phase indices:

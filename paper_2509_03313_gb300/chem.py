@@ -353,10 +353,10 @@ def chem_batch_reset(ctx, seeds):
 
 
 def chem_autotune(ctx, budget_ms: float = 2000.0):
-    """Returns (steps_per_launch, cells_per_axis_limit, species_per_item)."""
-    chosen = np.zeros(3, np.int32)
+    """Returns (steps_per_launch, cells_per_axis_limit, species_per_item, launch_mode)."""
+    chosen = np.zeros(4, np.int32)
     _check(ctx, lib().chem_autotune(ctx, float(budget_ms), _ptr(chosen)))
-    return int(chosen[0]), int(chosen[1]), int(chosen[2])
+    return int(chosen[0]), int(chosen[1]), int(chosen[2]), int(chosen[3])
 
 
 def chem_last_error(ctx) -> str:

@@ -903,8 +903,11 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   const int n_alloc = tr0[0].n_alloc;
   std::vector<int> n_cands;
   for (double f : {1.0, 0.75, 0.55, 0.4}) n_cands.push_back(std::max(3, static_cast<int>(n_alloc * f)));
-  const int ih_cands[3] = {16, 32, 64};
+  const int ih_cands[2] = {32, 64};
   const int spl_cands[2] = {8, 32};
+  const bool mode_cands[2] = {false, true};  // per-phase graph, persistent launch
+  const bool saved_persistent = ctx->persistent;
+  bool best_persistent = saved_persistent;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -914,7 +917,10 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   const int saved_spl = ctx->steps_per_launch;
   const bool saved_prof = ctx->profiling;
   ctx->profiling = false;
-  for (int spl : spl_cands) {
+  for (int combo = 0; combo < 4; ++combo) {
+    const bool pers = mode_cands[combo / 2];
+    const int spl = spl_cands[combo % 2];
+    ctx->persistent = pers;
     ctx->steps_per_launch = spl;
     s = capture_graph(ctx);
     if (s) break;
@@ -961,7 +967,7 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
         // the timed part by counting the timed replays' share
         const double timed_frac = static_cast<double>(reps) / (reps + 1);
         const double rate = ms > 0.f ? (static_cast<double>(ss - [&] { long long z = 0; for (int b = 0; b < ctx->B; ++b) z += tr0[b].species_steps; return z; }()) * timed_frac) / (ms * 1e-3) : 0.0;
-        if (rate > best_rate) { best_rate = rate; best_n = nm; best_ih = ih; best_spl = spl; }
+        if (rate > best_rate) { best_rate = rate; best_n = nm; best_ih = ih; best_spl = spl; best_persistent = pers; }
       }
     }
     if (s) break;
@@ -995,6 +1001,7 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   if (s2) return s2;
   ctx->item_home = best_ih;
   ctx->steps_per_launch = best_rate > 0.0 ? best_spl : saved_spl;
+  ctx->persistent = best_rate > 0.0 ? best_persistent : saved_persistent;
   ctx->profiling = saved_prof;
   s = capture_graph(ctx);
   if (s) return s;
@@ -1002,6 +1009,7 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
     chosen[0] = ctx->steps_per_launch;
     chosen[1] = best_n;
     chosen[2] = best_ih;
+    chosen[3] = ctx->persistent ? CHEM_LAUNCH_PERSISTENT : CHEM_LAUNCH_PHASES;
   }
   return ctx->status;
 }

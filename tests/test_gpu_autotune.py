@@ -29,8 +29,9 @@ def test_tuning_mid_run_leaves_fp64_results_unchanged(launch_mode):
         p = wl.pulses[0]
         chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
         chem.chem_run_until(ctx, 70e-9)
-        spl, n_lim, ih = chem.chem_autotune(ctx, 400.0)
+        spl, n_lim, ih, mode = chem.chem_autotune(ctx, 400.0)
         assert spl in (8, 32) and ih in (16, 32, 64) and n_lim >= 3
+        assert mode in (chem.CHEM_LAUNCH_PHASES, chem.CHEM_LAUNCH_PERSISTENT)
         chem.chem_run_until(ctx, wl.t_end)
         ids, types, xyz = chem.chem_get_state(ctx)
         o = np.argsort(ids)
