@@ -234,7 +234,10 @@ def run_gpu_arm(args):
                              profiling=not args.no_phase_events)
         tuned = None
         try:
-            if name == "fp32l" and not args.no_autotune:
+            if name == "fp32l" and args.tuned:
+                tuned = tuple(int(v) for v in args.tuned.split(","))
+                chem.chem_set_tuning(ctx, *tuned)
+            elif name == "fp32l" and not args.no_autotune:
                 chem.chem_reset(ctx, seed0 + 3)
                 chem.chem_inject_pulse(ctx, pulse.types, pulse.xyz, pulse.t_arrival, pulse.energy_eV)
                 tuned = chem.chem_autotune(ctx, args.autotune_ms)
@@ -384,7 +387,11 @@ def run_batched(args, chem, W, torch, stream, alloc, flush):
 
     try:
         load(500)
-        tuned = chem.chem_autotune(ctx, args.autotune_ms)
+        if args.batch_tuned:
+            tuned = tuple(int(v) for v in args.batch_tuned.split(","))
+            chem.chem_set_tuning(ctx, *tuned)
+        else:
+            tuned = chem.chem_autotune(ctx, args.autotune_ms)
         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         times, ss = [], 0
         for k in range(args.batch_reps + 1):
@@ -429,6 +436,10 @@ def main():
     ap.add_argument("--no-phase-events", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--autotune-ms", type=float, default=1500.0)
+    ap.add_argument("--tuned", default="",
+                    help="FP32-local tuning instead of the autotuner: steps_per_launch,"
+                         "cells_per_axis_limit,species_per_item,launch_mode (1 phases, 2 persistent)")
+    ap.add_argument("--batch-tuned", default="", help="the same for the batched run")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--batch-reps", type=int, default=2)

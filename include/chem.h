@@ -213,6 +213,14 @@ int32_t chem_batch_size(const chem_ctx* ctx);
  * species_per_item, launch_mode} when chosen is not NULL. */
 chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen);
 
+/* Apply tuning parameters directly, in the layout chem_autotune reports: tuning[4] =
+ * {steps_per_launch (1..1024), cells_per_axis_limit (>= 3; clamped to the allocated hash),
+ * species_per_item (1..64), launch_mode (CHEM_LAUNCH_PHASES or CHEM_LAUNCH_PERSISTENT)}.
+ * Allowed between runs; the device state is kept. Results depend on the parameters as
+ * described for chem_autotune. Out-of-range values: CHEM_EINVAL, nothing changed. No
+ * counterpart in the paper (a performance setting). */
+chem_status chem_set_tuning(chem_ctx* ctx, const int32_t* tuning);
+
 /* Counters of a context since chem_init (host side, exact). Phase indices:
  * 0 step begin, 1 release, 2 diffusion + hash keys, 3 radix sort (all passes),
  * 4 gather + cell ranges, 5 pair search, 6 matching + products + tallies,

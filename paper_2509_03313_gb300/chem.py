@@ -83,7 +83,7 @@ STEP_DTYPE = np.dtype([("step", np.uint32), ("train", np.uint32), ("t_start_s", 
 EXPORTS = ["chem_init", "chem_inject_pulse", "chem_run_until", "chem_tally", "chem_get_state",
            "chem_get_events", "chem_get_step_log", "chem_reset", "chem_last_error", "chem_destroy",
            "chem_batch_init", "chem_batch_inject", "chem_batch_run_until", "chem_batch_tally",
-           "chem_batch_get_state", "chem_batch_reset", "chem_batch_size", "chem_autotune",
+           "chem_batch_get_state", "chem_batch_reset", "chem_batch_size", "chem_autotune", "chem_set_tuning",
            "chem_version", "chem_get_stats", "chem_set_profiling", "chem_step_noalloc"]
 
 
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "chem_batch_reset": (i32, [vp, vp]),
         "chem_batch_size": (i32, [vp]),
         "chem_autotune": (i32, [vp, dbl, vp]),
+        "chem_set_tuning": (i32, [vp, vp]),
         "chem_version": (ctypes.c_char_p, []),
         "chem_get_stats": (i32, [vp, P(chem_stats)]),
         "chem_set_profiling": (i32, [vp, i32]),
@@ -357,6 +358,13 @@ def chem_autotune(ctx, budget_ms: float = 2000.0):
     chosen = np.zeros(4, np.int32)
     _check(ctx, lib().chem_autotune(ctx, float(budget_ms), _ptr(chosen)))
     return int(chosen[0]), int(chosen[1]), int(chosen[2]), int(chosen[3])
+
+
+def chem_set_tuning(ctx, steps_per_launch: int, cells_per_axis_limit: int, species_per_item: int,
+                    launch_mode: int):
+    """Apply the parameters chem_autotune would choose (same order as its result)."""
+    t = np.array([steps_per_launch, cells_per_axis_limit, species_per_item, launch_mode], np.int32)
+    _check(ctx, lib().chem_set_tuning(ctx, _ptr(t)))
 
 
 def chem_last_error(ctx) -> str:

@@ -1014,4 +1014,29 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   return ctx->status;
 }
 
+chem_status chem_set_tuning(chem_ctx* ctx, const int32_t* tuning) {
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  if (!tuning) return CHEM_EINVAL;
+  const int spl = tuning[0], n_lim = tuning[1], ih = tuning[2], mode = tuning[3];
+  if (spl < 1 || spl > 1024 || n_lim < 3 || ih < 1 || ih > ITEM_HOME ||
+      (mode != CHEM_LAUNCH_PHASES && mode != CHEM_LAUNCH_PERSISTENT))
+    return CHEM_EINVAL;
+  std::vector<Train> tr;
+  s = download_trains(ctx, tr);
+  if (s) return s;
+  for (auto& t : tr) t.n_max = std::min(n_lim, t.n_alloc);
+  s = upload_trains(ctx, tr);
+  if (s) return s;
+  const uint32_t ih32 = static_cast<uint32_t>(ih);
+  CK(cudaMemcpyAsync(&ctx->d.g->item_home, &ih32, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->item_home = ih;
+  ctx->steps_per_launch = spl;
+  ctx->persistent = mode == CHEM_LAUNCH_PERSISTENT;
+  s = capture_graph(ctx);
+  if (s) return s;
+  return ctx->status;
+}
+
 }  // extern "C"

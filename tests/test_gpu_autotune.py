@@ -63,3 +63,35 @@ def test_tuning_fp32_local_keeps_counts_consistent():
     assert np.unique(ids).size == ids.size
     c0 = np.bincount(pulse.types, minlength=7)
     assert int((tal["counts"] * W.CHARGE).sum()) == int((c0 * W.CHARGE).sum())
+
+
+@pytest.mark.parametrize("tuning", [(4, 12, 16, chem.CHEM_LAUNCH_PERSISTENT), (32, 200, 64, chem.CHEM_LAUNCH_PHASES)])
+def test_set_tuning_mid_run_leaves_fp64_results_unchanged(tuning):
+    wl = W.uniform_2000(seed=53, L=200.0, n_steps=200)
+    ctx, keep = _ctx(wl, 53, chem.CHEM_FP64)
+    try:
+        p = wl.pulses[0]
+        chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        chem.chem_run_until(ctx, 90e-9)
+        chem.chem_set_tuning(ctx, *tuning)
+        chem.chem_run_until(ctx, wl.t_end)
+        ids, types, xyz = chem.chem_get_state(ctx)
+        o = np.argsort(ids)
+        g = {"tally": chem.chem_tally(ctx, 7, 9), "events": chem.chem_get_events(ctx),
+             "steps": chem.chem_get_step_log(ctx),
+             "state": (ids[o].astype(np.int64), types[o].astype(np.int64), xyz[o])}
+    finally:
+        chem.chem_destroy(ctx)
+    assert_fp64_parity(g, oracle_run(wl, 53, t_stops=[90e-9]), wl.L)
+
+
+def test_set_tuning_rejects_out_of_range_values():
+    wl = W.uniform_2000(seed=54, L=200.0, n_steps=10)
+    ctx, keep = _ctx(wl, 54, chem.CHEM_FP64)
+    try:
+        for bad in [(0, 12, 16, 1), (8, 2, 16, 1), (8, 12, 65, 1), (8, 12, 16, 0), (8, 12, 16, 3)]:
+            with pytest.raises(chem.ChemError) as ei:
+                chem.chem_set_tuning(ctx, *bad)
+            assert ei.value.status == chem.CHEM_EINVAL
+    finally:
+        chem.chem_destroy(ctx)
