@@ -219,7 +219,7 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
   t.key1 = static_cast<uint32_t>(c.seed >> 32) ^ c.train_id;
 }
 
-int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 10 + ctx->d.passes + MAX_PASSES; }
+int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 9 + ctx->d.passes; }
 
 chem_status capture_graph(chem_ctx* ctx) {
   if (ctx->graph) {

@@ -9,8 +9,7 @@ namespace chem {
 
 union PhaseSmem {
   BeginSmem begin;
-  MatchSmem match;
-  ScanSmem scan;
+  SerialSmem serial;
   ProductsSmem products;
   EndSmem end;
   SearchSmem<true> search32;
@@ -97,15 +96,9 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev 
     if constexpr (F32L) phase_search<true>(d, sm.search32);
     else phase_search<false>(d, sm.search64);
     grid_sync(d);
-    phase_match_fast(d, sm.match);
+    phase_match_fast(d);
     grid_sync(d);
-    if (blockIdx.x == 0) phase_match_rounds(d, sm.match);
-    grid_sync(d);
-    for (int p = 0; p < MAX_PASSES; ++p) {
-      phase_event_sort_pass(d, p, sm.sort);
-      grid_sync(d);
-    }
-    if (blockIdx.x == 0) phase_products_scan(d, sm.scan);
+    if (blockIdx.x == 0) phase_react_serial(d, sm.serial, nullptr);
     grid_sync(d);
     phase_products<F32L>(d, sm.products);
     grid_sync(d);

@@ -16,23 +16,15 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_pass(const __grid_constan
 }
 
 __global__ void __launch_bounds__(256) k_match_fast(const __grid_constant__ Dev d) {
-  __shared__ MatchSmem sm;
-  phase_match_fast(d, sm);
+  phase_match_fast(d);
 }
 
-__global__ void __launch_bounds__(REACT_THREADS) k_match_rounds(const __grid_constant__ Dev d) {
-  __shared__ MatchSmem sm;
-  phase_match_rounds(d, sm);
-}
+constexpr size_t REACT_SERIAL_DYN_SMEM = 4 * EV_SMEM_CAP * sizeof(uint32_t);
 
-__global__ void __launch_bounds__(SORT_THREADS) k_event_sort_pass(const __grid_constant__ Dev d, int pass) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  phase_event_sort_pass(d, pass, *reinterpret_cast<SortSmem*>(smem_raw));
-}
-
-__global__ void __launch_bounds__(REACT_THREADS) k_products_scan(const __grid_constant__ Dev d) {
-  __shared__ ScanSmem sm;
-  phase_products_scan(d, sm);
+__global__ void __launch_bounds__(REACT_THREADS) k_react_serial(const __grid_constant__ Dev d) {
+  __shared__ SerialSmem sm;
+  extern __shared__ __align__(16) uint32_t sbuf[];
+  phase_react_serial(d, sm, sbuf);
 }
 
 __global__ void __launch_bounds__(256) k_end_step(const __grid_constant__ Dev d) {
@@ -42,12 +34,7 @@ __global__ void __launch_bounds__(256) k_end_step(const __grid_constant__ Dev d)
 
 cudaError_t enqueue_react_head(const Dev& d, const LaunchCfg& lc, cudaStream_t s) {
   k_match_fast<<<lc.stream_blocks, 256, 0, s>>>(d);
-  k_match_rounds<<<1, REACT_THREADS, 0, s>>>(d);
-  // events are few: a handful of CTAs claim all the tiles
-  const int ev_blocks = lc.sort_blocks < 32 ? lc.sort_blocks : 32;
-  for (int p = 0; p < MAX_PASSES; ++p)
-    k_event_sort_pass<<<ev_blocks, SORT_THREADS, sizeof(SortSmem), s>>>(d, p);
-  k_products_scan<<<1, REACT_THREADS, 0, s>>>(d);
+  k_react_serial<<<1, REACT_THREADS, REACT_SERIAL_DYN_SMEM, s>>>(d);
   return cudaGetLastError();
 }
 
@@ -74,8 +61,8 @@ cudaError_t sort_pass_occupancy(int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sizeof(SortSmem)));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_event_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(sizeof(SortSmem)));
+  e = cudaFuncSetAttribute(k_react_serial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(REACT_SERIAL_DYN_SMEM));
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_sort_pass, SORT_THREADS,
                                                        sizeof(SortSmem));

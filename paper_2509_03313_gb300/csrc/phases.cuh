@@ -295,11 +295,7 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     g->epoch += 1;
     g->any_active = sb.any;
   }
-  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) {
-    (&d.g->hist[0][0])[i] = 0u;
-    (&d.g->ev_hist[0][0])[i] = 0u;
-  }
-  if (tid < MAX_PASSES) d.g->ev_tile_ctr[tid] = 0u;
+  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&d.g->hist[0][0])[i] = 0u;
   __syncthreads();
 }
 
@@ -939,14 +935,23 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
 //     conflict list; a pair is committed when it is the smallest (d1^2, id_lo, id_hi)
 //     remaining pair of both its species. Together with 1 this equals the greedy walk
 //     over all accepted pairs sorted by that key (closest first, lower ids first).
-//  3. Onesweep passes order the events by (train, id_lo);
-//  4. phase_products_scan (one CTA): product-count prefix in that order;
-//  5. phase_products (all CTAs): product ids and positions at the diffusion-weighted
+//  3. phase_react_serial runs 2 and then, in the same CTA, orders the events by
+//     (train, id_lo) with a block radix sort (in shared memory when they fit) and forms
+//     the product-count prefix in that order;
+//  4. phase_products (all CTAs): product ids and positions at the diffusion-weighted
 //     encounter point (Table 1 right-hand sides), tallies summed per CTA, event log;
-//  6. phase_end_step (one CTA): FP64 clock, step counter, dt growth, step records.
+//  5. phase_end_step (one CTA): FP64 clock, step counter, dt growth, step records.
 struct MatchSmem {
   uint32_t n_alive, n_next;
-  uint32_t hist[MAX_PASSES][RADIX];
+};
+
+// Events ordered in shared memory by the one-CTA react kernel (4 arrays of this size).
+constexpr int EV_SMEM_CAP = 8192;
+
+struct BlockSortSmem {
+  uint32_t whist[REACT_THREADS / 32][RADIX];  // per warp: digit counts, then offsets
+  uint32_t dtot[RADIX];                       // digit totals, then digit starts
+  uint32_t trivial[4];                        // pass p has one digit for every key
 };
 
 struct ScanSmem {
@@ -993,47 +998,32 @@ __device__ __forceinline__ uint32_t event_key(const Dev& d, const Cand& cd) {
   return d.train_bits ? ((b << (32 - d.train_bits)) | cd.id_lo) : cd.id_lo;
 }
 
-__device__ __forceinline__ void commit_event(const Dev& d, uint32_t c, const Cand& cd,
-                                             uint32_t (*hist)[RADIX]) {
+__device__ __forceinline__ void commit_event(const Dev& d, uint32_t c, const Cand& cd) {
   d.dead[cd.s_lo] = 1;
   d.dead[cd.s_hi] = 1;
   const uint32_t e = atomicAdd(&d.g->n_events, 1u);
-  const uint32_t key = event_key(d, cd);
-  d.ev_k0[e] = key;
+  d.ev_k0[e] = event_key(d, cd);
   d.ev_v0[e] = c;
-#pragma unroll
-  for (int p = 0; p < MAX_PASSES; ++p) atomicAdd(&hist[p][(key >> (8 * p)) & 255u], 1u);
 }
 
-__device__ __forceinline__ void flush_hist(const Dev& d, uint32_t (*hist)[RADIX]) {
-  __syncthreads();
-  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) {
-    const uint32_t c = (&hist[0][0])[i];
-    if (c) atomicAdd(&d.g->ev_hist[0][0] + i, c);
-  }
-}
-
-static __device__ void phase_match_fast(const Dev& d, MatchSmem& sm) {
-  for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&sm.hist[0][0])[i] = 0u;
+static __device__ void phase_match_fast(const Dev& d) {
   const bool ok = block_status_ok(d);  // includes a barrier
   const uint32_t n_c = ok ? min(d.g->n_cand, d.cap_cand) : 0u;
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_c; c += gridDim.x * blockDim.x) {
     const Cand cd = d.cand[c];
     if (d.touch[cd.s_lo] == 1u && d.touch[cd.s_hi] == 1u) {
-      commit_event(d, c, cd, sm.hist);
+      commit_event(d, c, cd);
       d.touch[cd.s_lo] = 0u;
       d.touch[cd.s_hi] = 0u;
     } else {
       d.alive0[atomicAdd(&d.g->n_conflict, 1u)] = c;
     }
   }
-  flush_hist(d, sm.hist);
 }
 
 static __device__ void phase_match_rounds(const Dev& d, MatchSmem& sm) {
   const int tid = threadIdx.x;
   const int nt = blockDim.x;
-  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&sm.hist[0][0])[i] = 0u;
   const bool ok = block_status_ok(d);
   unsigned long long* bd = reinterpret_cast<unsigned long long*>(d.keys0);
   unsigned long long* bp = bd + d.cap;
@@ -1081,7 +1071,7 @@ static __device__ void phase_match_rounds(const Dev& d, MatchSmem& sm) {
       const unsigned long long kd = __double_as_longlong(cd.d1sq);
       const unsigned long long kp = (static_cast<unsigned long long>(cd.id_lo) << 32) | cd.id_hi;
       if (bd[cd.s_lo] == kd && bp[cd.s_lo] == kp && bd[cd.s_hi] == kd && bp[cd.s_hi] == kp)
-        commit_event(d, c, cd, sm.hist);
+        commit_event(d, c, cd);
     }
     if (tid == 0) sm.n_next = 0;
     __syncthreads();
@@ -1095,38 +1085,90 @@ static __device__ void phase_match_rounds(const Dev& d, MatchSmem& sm) {
     uint32_t* tmp = alive; alive = nxt; nxt = tmp;
     __syncthreads();
   }
-  flush_hist(d, sm.hist);
   __syncthreads();
 }
 
-// One Onesweep pass over the event keys (ev_k0/ev_v0 <-> ev_k1/ev_v1), skipped when its
-// digit is the same for every event key.
-static __device__ void phase_event_sort_pass(const Dev& d, int pass, SortSmem& sm) {
-  if (!block_status_ok(d)) return;
-  const uint32_t n = d.g->n_events;
-  int before = 0;
-  const bool act = pass_active(d.g->ev_hist, pass, n, &before);
-  if (pass == MAX_PASSES - 1 && blockIdx.x == 0 && threadIdx.x == 0)
-    d.g->ev_parity = static_cast<uint32_t>((before + (act ? 1 : 0)) & 1);
-  if (!act) return;
-  const bool odd = before & 1;
-  const uint32_t* kin = odd ? d.ev_k1 : d.ev_k0;
-  const uint32_t* vin = odd ? d.ev_v1 : d.ev_v0;
-  uint32_t* kout = odd ? d.ev_k0 : d.ev_k1;
-  uint32_t* vout = odd ? d.ev_v0 : d.ev_v1;
-  onesweep_pass(kin, vin, kout, vout, n, 8 * pass, d.g->ev_hist[pass], &d.g->ev_tile_ctr[pass],
-                d.lookback, d.g->epoch * 2 * MAX_PASSES + MAX_PASSES + pass, d.g, sm);
+// Stable LSD radix sort of n (key, value) pairs by the whole CTA, 8-bit digits over the
+// 32 key bits. Each warp owns one contiguous chunk of the input and scatters it in order
+// (ranks among equal digits from __match_any_sync), so equal digits keep their order.
+// A pass whose digit is the same for every key is skipped. The arrays may live in shared
+// or global memory. Returns 0 when the result is in (k0, v0), 1 when in (k1, v1).
+static __device__ int block_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t n,
+                                BlockSortSmem& sm) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5, nw = nt >> 5;
+  const uint32_t chunk = (n + static_cast<uint32_t>(nw) - 1u) / static_cast<uint32_t>(nw);
+  const uint32_t lo = min(n, static_cast<uint32_t>(w) * chunk), hi = min(n, lo + chunk);
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t *kin = k0, *vin = v0, *kout = k1, *vout = v1;
+  int parity = 0;
+  if (tid < 4) sm.trivial[tid] = 0u;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 8 * pass;
+    for (int i = tid; i < nw * RADIX; i += nt) (&sm.whist[0][0])[i] = 0u;
+    __syncthreads();
+    for (uint32_t i = lo + lane; i < hi; i += 32) atomicAdd(&sm.whist[w][(kin[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    for (int dg = tid; dg < RADIX; dg += nt) {
+      uint32_t run = 0;
+      for (int q = 0; q < nw; ++q) {
+        const uint32_t c = sm.whist[q][dg];
+        sm.whist[q][dg] = run;
+        run += c;
+      }
+      sm.dtot[dg] = run;
+      if (run == n) sm.trivial[pass] = 1u;
+    }
+    __syncthreads();
+    if (sm.trivial[pass]) continue;  // the same value for every thread
+    if (w == 0) {
+      uint32_t carry = 0;
+      for (int base = 0; base < RADIX; base += 32) {
+        const uint32_t v = sm.dtot[base + lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        sm.dtot[base + lane] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+      }
+    }
+    __syncthreads();
+    for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
+      const uint32_t i = b0 + lane;
+      const bool act = i < hi;
+      uint32_t key = 0, val = 0, dg = RADIX;  // inactive lanes form their own group
+      if (act) {
+        key = kin[i];
+        val = vin[i];
+        dg = (key >> shift) & 255u;
+      }
+      const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+      if (act) {
+        const uint32_t dst = sm.dtot[dg] + sm.whist[w][dg] + __popc(peers & lt);
+        kout[dst] = key;
+        vout[dst] = val;
+      }
+      __syncwarp();
+      if (act && (peers & lt) == 0u) sm.whist[w][dg] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t* t = kin; kin = kout; kout = t;
+    t = vin; vin = vout; vout = t;
+    parity ^= 1;
+  }
+  return parity;
 }
 
-// Product-count prefix over the ordered events, written to the free key buffer, plus
-// each train's first prefix, event and product counts.
-static __device__ void phase_products_scan(const Dev& d, ScanSmem& sm) {
+// Product-count prefix over the ordered events (`order`, optionally copied to
+// `order_out`), written to `pref`, plus each train's first prefix, event and product
+// counts.
+static __device__ void products_prefix(const Dev& d, ScanSmem& sm, const uint32_t* order, uint32_t* order_out,
+                                uint32_t* pref, uint32_t E, bool ok) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const bool ok = block_status_ok(d);
   const Tables& tb = *d.tables;
-  const uint32_t E = ok ? d.g->n_events : 0u;
-  const uint32_t* order = d.g->ev_parity ? d.ev_v1 : d.ev_v0;
-  uint32_t* pref = d.g->ev_parity ? d.ev_k0 : d.ev_k1;
   for (uint32_t b = tid; b < d.n_trains; b += nt) { sm.first_pref[b] = 0; sm.prods_tr[b] = 0; sm.evs_tr[b] = 0; }
   if (tid == 0) sm.carry = 0;
   __syncthreads();
@@ -1145,6 +1187,7 @@ static __device__ void phase_products_scan(const Dev& d, ScanSmem& sm) {
     const uint32_t ex = block_excl_scan(np, sm.warp_tot, tot) + sm.carry;
     if (valid) {
       pref[k] = ex;
+      if (order_out) order_out[k] = order[k];
       if (first) sm.first_pref[b] = ex;
       atomicAdd(&sm.prods_tr[b], np);
       atomicAdd(&sm.evs_tr[b], 1u);
@@ -1161,6 +1204,44 @@ static __device__ void phase_products_scan(const Dev& d, ScanSmem& sm) {
   }
   if (tid == 0 && ok) d.g->n_products = sm.carry;
   __syncthreads();
+}
+
+struct SerialSmem {
+  MatchSmem match;
+  BlockSortSmem sort;
+  ScanSmem scan;
+};
+
+// The one-CTA part of the react phase: conflict rounds, event order, product prefix.
+// With `sbuf` (4 * EV_SMEM_CAP words of shared memory) and at most EV_SMEM_CAP events
+// the sort runs in shared memory; otherwise in the global event buffers.
+static __device__ void phase_react_serial(const Dev& d, SerialSmem& sm, uint32_t* sbuf) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  phase_match_rounds(d, sm.match);
+  const bool ok = block_status_ok(d);
+  const uint32_t E = ok ? min(d.g->n_events, d.cap_cand) : 0u;
+  const uint32_t* order;
+  uint32_t* order_out = nullptr;
+  uint32_t* pref;
+  if (sbuf != nullptr && E <= static_cast<uint32_t>(EV_SMEM_CAP)) {
+    uint32_t* k0 = sbuf;
+    uint32_t* v0 = sbuf + EV_SMEM_CAP;
+    uint32_t* k1 = sbuf + 2 * EV_SMEM_CAP;
+    uint32_t* v1 = sbuf + 3 * EV_SMEM_CAP;
+    for (uint32_t i = tid; i < E; i += nt) { k0[i] = d.ev_k0[i]; v0[i] = d.ev_v0[i]; }
+    __syncthreads();
+    const int p = block_sort_pairs(k0, v0, k1, v1, E, sm.sort);
+    order = p ? v1 : v0;
+    order_out = d.ev_v0;
+    pref = d.ev_k1;
+    if (tid == 0) d.g->ev_parity = 0u;
+  } else {
+    const int p = block_sort_pairs(d.ev_k0, d.ev_v0, d.ev_k1, d.ev_v1, E, sm.sort);
+    order = p ? d.ev_v1 : d.ev_v0;
+    pref = p ? d.ev_k0 : d.ev_k1;
+    if (tid == 0) d.g->ev_parity = static_cast<uint32_t>(p);
+  }
+  products_prefix(d, sm.scan, order, order_out, pref, E, ok);
 }
 
 template <bool F32L>

@@ -116,9 +116,7 @@ struct Global {
   uint32_t item_ctr;      // next pair-search work item (work stealing)
   uint32_t sort_parity;   // number of non-trivial passes of this step's cell sort, mod 2
   uint32_t sort_any;      // at least one pass executed (else the order is unchanged)
-  uint32_t ev_parity;     // the same for the event sort
-  uint32_t ev_tile_ctr[MAX_PASSES];
-  uint32_t ev_hist[MAX_PASSES][RADIX];  // digit histograms of the event keys
+  uint32_t ev_parity;     // event order in ev_v1 (1) or ev_v0 (0), prefix in the other key buffer
   uint32_t pad_[1];
 };
 
