@@ -205,8 +205,8 @@ int32_t chem_batch_size(const chem_ctx* ctx);
 /* Choose, by timing short runs from the current state, the launch form (one kernel per
  * phase in a graph, or the persistent cooperative kernel), the steps per graph replay,
  * the hash resolution limit (cells per axis at small cutoffs, i.e. the cell size) and
- * the number of species one warp takes per pair-search work item (the threads per
- * cell). The device state is saved before and restored after every trial; trials run
+ * the pair-search mapping (threads per cell): 0 = one thread per home species, else the
+ * number of home species one warp takes per work item of a cell. The device state is saved before and restored after every trial; trials run
  * past the end time. FP64 results do not depend on the choice; FP32-local results
  * depend on the hash resolution only through rounding. budget_ms bounds the time spent
  * (at least one trial runs). chosen[4] = {steps_per_launch, cells_per_axis_limit,
@@ -215,7 +215,8 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen);
 
 /* Apply tuning parameters directly, in the layout chem_autotune reports: tuning[4] =
  * {steps_per_launch (1..1024), cells_per_axis_limit (>= 3; clamped to the allocated hash),
- * species_per_item (1..64), launch_mode (CHEM_LAUNCH_PHASES or CHEM_LAUNCH_PERSISTENT)}.
+ * species_per_item (0..64, 0 = one thread per home species), launch_mode
+ * (CHEM_LAUNCH_PHASES or CHEM_LAUNCH_PERSISTENT)}.
  * Allowed between runs; the device state is kept. Results depend on the parameters as
  * described for chem_autotune. Out-of-range values: CHEM_EINVAL, nothing changed. No
  * counterpart in the paper (a performance setting). */

@@ -222,6 +222,7 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
 int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 9 + ctx->d.passes; }
 
 chem_status capture_graph(chem_ctx* ctx) {
+  ctx->lc.search_tps = ctx->item_home == 0 ? 1 : 0;
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
@@ -684,7 +685,8 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
   d.dead = static_cast<uint8_t*>(A(cap));
   d.touch = static_cast<uint32_t*>(A(cap * 4));
   d.cell_info = static_cast<int4*>(A((cells + 1) * 16));
-  d.cstamp = static_cast<uint8_t*>(A(cells + 1));
+  d.occ_vec4 = static_cast<uint32_t>((cells + 127) / 128);
+  d.occ = static_cast<uint32_t*>(A(static_cast<size_t>(d.occ_vec4) * 16));
   d.lookback = static_cast<unsigned long long*>(A(static_cast<size_t>(d.max_tiles) * RADIX * 8));
   d.cand = static_cast<Cand*>(A(cand * sizeof(Cand)));
   const uint64_t evn = std::max<uint64_t>(cand, RADIX);
@@ -717,7 +719,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
   CK(cudaMemsetAsync(d.dead, 0, cap, ctx->stream));
   CK(cudaMemsetAsync(d.touch, 0, cap * 4, ctx->stream));
   CK(cudaMemsetAsync(d.cell_info, 0xFF, (cells + 1) * 16, ctx->stream));
-  CK(cudaMemsetAsync(d.cstamp, 0xFF, cells + 1, ctx->stream));
+  CK(cudaMemsetAsync(d.occ, 0, static_cast<size_t>(d.occ_vec4) * 16, ctx->stream));
   CK(cudaMemsetAsync(d.lookback, 0, static_cast<size_t>(d.max_tiles) * RADIX * 8, ctx->stream));
   CK(cudaMemcpyAsync(tables_dev, &T, sizeof(Tables), cudaMemcpyHostToDevice, ctx->stream));
   chem_status gs = init_global(ctx);
@@ -820,7 +822,7 @@ chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds) {
   CK(cudaMemsetAsync(ctx->d.dead, 0, ctx->d.cap, ctx->stream));
   CK(cudaMemsetAsync(ctx->d.touch, 0, static_cast<size_t>(ctx->d.cap) * 4, ctx->stream));
   CK(cudaMemsetAsync(ctx->d.cell_info, 0xFF, (static_cast<size_t>(ctx->d.total_cells) + 1) * 16, ctx->stream));
-  CK(cudaMemsetAsync(ctx->d.cstamp, 0xFF, static_cast<size_t>(ctx->d.total_cells) + 1, ctx->stream));
+  CK(cudaMemsetAsync(ctx->d.occ, 0, static_cast<size_t>(ctx->d.occ_vec4) * 16, ctx->stream));
   CK(cudaMemsetAsync(ctx->d.lookback, 0, static_cast<size_t>(ctx->d.max_tiles) * RADIX * 8, ctx->stream));
   s = upload_trains(ctx, tr);
   if (s) return s;
@@ -903,7 +905,7 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   const int n_alloc = tr0[0].n_alloc;
   std::vector<int> n_cands;
   for (double f : {1.0, 0.75, 0.55, 0.4}) n_cands.push_back(std::max(3, static_cast<int>(n_alloc * f)));
-  const int ih_cands[2] = {32, 64};
+  const int ih_cands[3] = {0, 32, 64};  // 0: one thread per home species
   const int spl_cands[2] = {8, 32};
   const bool mode_cands[2] = {false, true};  // per-phase graph, persistent launch
   const bool saved_persistent = ctx->persistent;
@@ -917,15 +919,17 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   const int saved_spl = ctx->steps_per_launch;
   const bool saved_prof = ctx->profiling;
   ctx->profiling = false;
-  for (int combo = 0; combo < 4; ++combo) {
-    const bool pers = mode_cands[combo / 2];
-    const int spl = spl_cands[combo % 2];
+  for (int combo = 0; combo < 4 * 3; ++combo) {
+    const bool pers = mode_cands[combo / 6];
+    const int spl = spl_cands[(combo / 3) % 2];
+    const int ih = ih_cands[combo % 3];
     ctx->persistent = pers;
     ctx->steps_per_launch = spl;
+    ctx->item_home = ih;  // selects the search kernel of the captured graph
     s = capture_graph(ctx);
     if (s) break;
-    for (int nm : n_cands) {
-      for (int ih : ih_cands) {
+    {
+      for (int nm : n_cands) {
         const double spent = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
         if (spent > budget_ms && best_rate > 0.0) break;
         // restore the state, then set this trial's parameters and an open end time
@@ -1019,7 +1023,7 @@ chem_status chem_set_tuning(chem_ctx* ctx, const int32_t* tuning) {
   if (s) return s;
   if (!tuning) return CHEM_EINVAL;
   const int spl = tuning[0], n_lim = tuning[1], ih = tuning[2], mode = tuning[3];
-  if (spl < 1 || spl > 1024 || n_lim < 3 || ih < 1 || ih > ITEM_HOME ||
+  if (spl < 1 || spl > 1024 || n_lim < 3 || ih < 0 || ih > ITEM_HOME ||
       (mode != CHEM_LAUNCH_PHASES && mode != CHEM_LAUNCH_PERSISTENT))
     return CHEM_EINVAL;
   std::vector<Train> tr;

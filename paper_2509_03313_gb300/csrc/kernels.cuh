@@ -14,6 +14,8 @@ union PhaseSmem {
   EndSmem end;
   SearchSmem<true> search32;
   SearchSmem<false> search64;
+  TpsSmem<true, 8> tps32;
+  TpsSmem<false, 8> tps64;
   uint32_t hist[MAX_PASSES][RADIX];
   SortSmem sort;
 };
@@ -70,6 +72,14 @@ __global__ void __launch_bounds__(256, 4) k_search(const __grid_constant__ Dev d
   phase_search<F32L>(d, sm);
 }
 
+constexpr int TPS_WARPS = 4;  // warps per CTA of the one-thread-per-species search
+
+template <bool F32L>
+__global__ void __launch_bounds__(32 * TPS_WARPS, 6) k_search_tps(const __grid_constant__ Dev d) {
+  __shared__ TpsSmem<F32L, TPS_WARPS> sm;
+  phase_search_tps<F32L, TPS_WARPS>(d, sm);
+}
+
 template <bool F32L>
 __global__ void __launch_bounds__(256) k_products(const __grid_constant__ Dev d) {
   __shared__ ProductsSmem sm;
@@ -93,8 +103,13 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev 
     }
     phase_gather<F32L>(d);
     grid_sync(d);
-    if constexpr (F32L) phase_search<true>(d, sm.search32);
-    else phase_search<false>(d, sm.search64);
+    if (d.g->item_home == 0) {
+      if constexpr (F32L) phase_search_tps<true, 8>(d, sm.tps32);
+      else phase_search_tps<false, 8>(d, sm.tps64);
+    } else {
+      if constexpr (F32L) phase_search<true>(d, sm.search32);
+      else phase_search<false>(d, sm.search64);
+    }
     grid_sync(d);
     phase_match_fast(d);
     grid_sync(d);
@@ -132,7 +147,8 @@ cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cu
   k_gather<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
   mark(2 * PH_GATHER + 1);
   mark(2 * PH_SEARCH);
-  k_search<F32L><<<lc.search_blocks, 256, 0, s>>>(d);
+  if (lc.search_tps) k_search_tps<F32L><<<2 * lc.search_blocks, 32 * TPS_WARPS, 0, s>>>(d);
+  else k_search<F32L><<<lc.search_blocks, 256, 0, s>>>(d);
   mark(2 * PH_SEARCH + 1);
   mark(2 * PH_REACT);
   e = enqueue_react_head(d, lc, s);

@@ -15,6 +15,7 @@ struct LaunchCfg {
   int search_blocks;      // grid of the pair search
   int sort_blocks;        // resident CTAs of a sort pass
   int persistent_blocks;  // resident CTAs of the persistent step kernel
+  int search_tps;         // pair search with one thread per home species (else warp per item)
 };
 
 // kernels_exact.cu (FP64 arithmetic without contraction)

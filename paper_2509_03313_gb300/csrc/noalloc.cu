@@ -31,7 +31,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(25
 
 // Byte layout of the scratch array.
 struct Layout {
-  size_t sx, sy, sz, stid, tx, ty, tz, ttid, tdx, tdy, tdz, items, touch, cell_sorted, sortbuf, dead, cell_info, cstamp, lookback, cand,
+  size_t sx, sy, sz, stid, tx, ty, tz, ttid, tdx, tdy, tdz, items, touch, cell_sorted, sortbuf, dead, cell_info, occ, lookback, cand,
       ev_list, alive0, alive1, ev_k0, ev_k1, ev_v0, ev_v1, ev_log, step_log, pend, trains, tables,
       global, total;
 };
@@ -50,7 +50,7 @@ constexpr Layout make_layout() {
   L.sortbuf = take(M * 16);
   L.dead = take(M);
   L.cell_info = take((NA_CELLS + 1) * 16);
-  L.cstamp = take(NA_CELLS + 1);
+  L.occ = take((NA_CELLS + 127) / 128 * 16);
   L.lookback = take(static_cast<size_t>(NA_TILES) * RADIX * 8);
   L.cand = take(C * sizeof(Cand));
   L.ev_list = take(C * 4); L.alive0 = take(C * 4); L.alive1 = take(C * 4);
@@ -288,7 +288,8 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   d.vals1 = sortbuf + 3 * NA_MAX_SPECIES;
   d.dead = b + LAYOUT.dead;
   d.cell_info = reinterpret_cast<int4*>(b + LAYOUT.cell_info);
-  d.cstamp = b + LAYOUT.cstamp;
+  d.occ = reinterpret_cast<uint32_t*>(b + LAYOUT.occ);
+  d.occ_vec4 = (NA_CELLS + 127) / 128;
   d.lookback = reinterpret_cast<unsigned long long*>(b + LAYOUT.lookback);
   d.max_tiles = NA_TILES;
   d.cand = reinterpret_cast<Cand*>(b + LAYOUT.cand);
@@ -319,10 +320,11 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   lc.search_blocks = lc.stream_blocks;
   lc.sort_blocks = std::min(sms * sort_occ, static_cast<int>(NA_TILES));
   lc.persistent_blocks = 1;
+  lc.search_tps = 0;
   cudaStream_t s = static_cast<cudaStream_t>(cfg->cuda_stream);
   // leftovers of the previous call: stale hash cells and look-back words must not match
   bool ok = cudaMemsetAsync(d.cell_info, 0xFF, (NA_CELLS + 1) * 16, s) == cudaSuccess &&
-            cudaMemsetAsync(d.cstamp, 0xFF, NA_CELLS + 1, s) == cudaSuccess &&
+            cudaMemsetAsync(d.occ, 0, (NA_CELLS + 127) / 128 * 16, s) == cudaSuccess &&
             cudaMemsetAsync(d.touch, 0, NA_MAX_SPECIES * 4, s) == cudaSuccess &&
             cudaMemsetAsync(d.lookback, 0, static_cast<size_t>(NA_TILES) * RADIX * 8, s) == cudaSuccess;
   if (ok) {

@@ -381,9 +381,12 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
   const bool ok = status_of(d) == 0;
   const uint32_t n_total = d.g->n_total;
   const uint32_t stride = gridDim.x * blockDim.x;
-  const Tables& tb = *d.tables;
   uint32_t n_dead_local = 0;
   if (ok) {
+    // the occupancy bitmap is rebuilt by this step's gather (the last step's search has
+    // finished reading it)
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < d.occ_vec4; w += stride)
+      reinterpret_cast<uint4*>(d.occ)[w] = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_total; s += stride) {
       uint32_t key;
       if (d.dead[s]) {
@@ -542,11 +545,12 @@ __device__ void phase_gather(const Dev& d) {
     if (first) {
       ci[0] = static_cast<int>(s);
       ci[2] = static_cast<int>(epoch);
-      d.cstamp[key] = static_cast<uint8_t>(epoch);
+      atomicOr(&d.occ[key >> 5], 1u << (key & 31u));
     }
     if (s + 1 == n_live || kf[s + 1] != key) ci[1] = static_cast<int>(s + 1);
-    // pair-search work item: a cell's first slot and every ITEM_HOME-th slot
-    if (first || (s % item_home) == 0) {
+    // pair-search work item: a cell's first slot and every item_home-th slot (none when
+    // the search runs one thread per species)
+    if (item_home != 0 && (first || (s % item_home) == 0)) {
       const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, key);
       if (d.trains[b].active && !d.trains[b].free_jump) {
         const uint32_t it = atomicAdd(&d.g->n_items, 1u);
@@ -802,9 +806,9 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
       fwd_offset(lane, ox, oy, oz);
       const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, ox, n), step_cell(iy, oy, n),
                                                      step_cell(iz, oz, n), tr.cb);
-      // one byte per cell (L2-resident) filters the empty cells; the 16-byte entry with
-      // its full epoch decides
-      if (d.cstamp[nc] == static_cast<uint8_t>(epoch)) {
+      // one bit per cell (L2-resident) filters the empty cells; the 16-byte entry with
+      // its epoch confirms
+      if ((d.occ[nc >> 5] >> (nc & 31u)) & 1u) {
         const int4 nci = d.cell_info[nc];
         if (static_cast<uint32_t>(nci.z) == epoch) {
           rs = static_cast<uint32_t>(nci.x);
@@ -925,6 +929,263 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
     flush_pairs<F32L>(d, tb, tr, b, hs, q, s0, vf, lane);
     __syncwarp();
   }
+}
+
+// ---- one thread per home species
+// The same pairs as phase_search, assigned differently: each lane takes one home species
+// (warps take 32 consecutive sorted slots by work stealing) and walks its own cell's later
+// slots and its 13 forward cells. Lanes of one cell walk the same ranges in step, so their
+// neighbour loads are broadcasts; the loops are warp-uniform (trip count = the longest
+// range among the lanes) and pairs inside the cutoff go to the warp's pair queue.
+
+template <bool F32L>
+struct TpsQueue;
+
+template <>
+struct TpsQueue<true> {
+  static constexpr int CAP = 96;
+  uint32_t si[CAP], j[CAP], tid_i[CAP], b[CAP];
+  float fx[CAP], fy[CAP], fz[CAP], f2[CAP];
+  uint32_t n;
+};
+
+template <>
+struct TpsQueue<false> {
+  static constexpr int CAP = 64;
+  uint32_t si[CAP], j[CAP], tid_i[CAP], b[CAP];
+  double rx[CAP], ry[CAP], rz[CAP], d2[CAP];
+  uint32_t n;
+};
+
+template <bool F32L, int W>
+struct TpsSmem {
+  using T = typename std::conditional<F32L, float, double>::type;
+  T rc2[W][32][MAXT + 1];     // per warp and lane: squared cutoff against each type (-1: none)
+  uint32_t rs[W][N_FWD][32];  // per lane: its non-empty neighbour ranges [rs, re) ...
+  uint32_t re[W][N_FWD][32];
+  uint8_t rk[W][N_FWD][32];   // ... and their half-shell offsets
+  TpsQueue<F32L> q[W];
+};
+
+// Acceptance of one queued pair (the slow path of phase_search's pair_accept, with the
+// home species given by slot and packed id/type).
+template <bool F32L>
+__device__ __forceinline__ void tps_accept(const Dev& d, const Tables& tb, const Train& tr, int b, uint32_t si,
+                                           uint32_t tid_i, uint32_t j, uint32_t tid_j, float fx, float fy,
+                                           float fz, float f2, double d1sq, double rx1, double ry1, double rz1,
+                                           const uint32_t* vf) {
+  const uint32_t ti = tid_type(tid_i), tj = tid_type(tid_j);
+  const int r = tb.pair_rxn[ti][tj];
+  const uint32_t id_i = tid_id(tid_i), id_j = tid_id(tid_j);
+  const bool i_lo = id_i < id_j;
+  const uint32_t id_lo = i_lo ? id_i : id_j, id_hi = i_lo ? id_j : id_i;
+  if constexpr (F32L) {
+    if (!i_lo) { fx = -fx; fy = -fy; fz = -fz; }
+    const float4 di = d.td4[vf ? vf[si] : si];
+    const float4 dj = d.td4[vf ? vf[j] : j];
+    const float4 dlo = i_lo ? di : dj, dhi = i_lo ? dj : di;
+    const float r0x = fx - (dhi.x - dlo.x), r0y = fy - (dhi.y - dlo.y), r0z = fz - (dhi.z - dlo.z);
+    const float d0sq = r0x * r0x + r0y * r0y + r0z * r0z;
+    if (!accept_f32(d0sq, f2, r, tb, tr, id_lo, id_hi)) return;
+    emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, static_cast<double>(f2));
+  } else {
+    if (!i_lo) { rx1 = -rx1; ry1 = -ry1; rz1 = -rz1; }
+    const uint32_t tj_idx = vf ? vf[j] : j, ti_idx = vf ? vf[si] : si;
+    const double ejx = d.tdx[tj_idx], ejy = d.tdy[tj_idx], ejz = d.tdz[tj_idx];
+    const double eix = d.tdx[ti_idx], eiy = d.tdy[ti_idx], eiz = d.tdz[ti_idx];
+    const double elx = i_lo ? eix : ejx, ely = i_lo ? eiy : ejy, elz = i_lo ? eiz : ejz;
+    const double ehx = i_lo ? ejx : eix, ehy = i_lo ? ejy : eiy, ehz = i_lo ? ejz : eiz;
+    const double r0x = __dsub_rn(rx1, __dsub_rn(ehx, elx));
+    const double r0y = __dsub_rn(ry1, __dsub_rn(ehy, ely));
+    const double r0z = __dsub_rn(rz1, __dsub_rn(ehz, elz));
+    const double d1 = sqrt(d1sq);
+    const double d0 = sqrt(sq3(r0x, r0y, r0z));
+    const double p = bridge_p(d0, d1, tb.R[r], tr.ddt[r]);
+    const double u = pair_uniform(id_lo, id_hi, tr.step, tr.key0, tr.key1);
+    if (!(u < p)) return;
+    emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, d1sq);
+  }
+}
+
+template <bool F32L>
+__device__ __forceinline__ void tps_flush(const Dev& d, const Tables& tb, TpsQueue<F32L>& q, const uint32_t* vf,
+                                          int lane) {
+  const uint32_t nq = q.n;
+  for (uint32_t e = lane; e < nq; e += 32) {
+    const uint32_t j = q.j[e];
+    const int b = static_cast<int>(q.b[e]);
+    const Train& tr = d.trains[b];
+    if constexpr (F32L)
+      tps_accept<true>(d, tb, tr, b, q.si[e], q.tid_i[e], j, __float_as_uint(d.s4[j].w), q.fx[e], q.fy[e],
+                       q.fz[e], q.f2[e], 0.0, 0.0, 0.0, 0.0, vf);
+    else
+      tps_accept<false>(d, tb, tr, b, q.si[e], q.tid_i[e], j, d.stid[j], 0.f, 0.f, 0.f, 0.f, q.d2[e], q.rx[e],
+                        q.ry[e], q.rz[e], vf);
+  }
+  __syncwarp();
+  if (lane == 0) q.n = 0;
+  __syncwarp();
+}
+
+template <bool F32L, int W>
+__device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
+  using T = typename TpsSmem<F32L, W>::T;
+  if (status_of(d)) return;
+  const uint32_t n_live = d.g->n_total - d.g->n_dead;
+  const uint32_t epoch = d.g->epoch;
+  const uint32_t* vf = d.g->sort_any ? (d.g->sort_parity ? d.vals1 : d.vals0) : nullptr;
+  const Tables& tb = *d.tables;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  T(&rc2)[MAXT + 1] = sm.rc2[wib][lane];
+  TpsQueue<F32L>& q = sm.q[wib];
+  if (lane == 0) q.n = 0;
+  __syncwarp();
+  const uint32_t lanemask_lt = (1u << lane) - 1u;
+  const uint32_t n_chunks = (n_live + 31u) / 32u;
+  uint32_t c_next = 0;
+  if (lane == 0) c_next = atomicAdd(&d.g->item_ctr, 1u);
+  c_next = __shfl_sync(0xffffffffu, c_next, 0);
+  while (c_next < n_chunks) {
+    const uint32_t c = c_next;
+    if (lane == 0) c_next = atomicAdd(&d.g->item_ctr, 1u);  // the next chunk, used at the end
+    const uint32_t s = c * 32u + static_cast<uint32_t>(lane);
+    bool home = s < n_live;
+    uint32_t tid_i = 0, cell = 0;
+    float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
+    double xi = 0, yi = 0, zi = 0;
+    if (home) {
+      cell = d.cell_sorted[s];
+      if constexpr (F32L) { vi = d.s4[s]; tid_i = __float_as_uint(vi.w); }
+      else { xi = d.sx[s]; yi = d.sy[s]; zi = d.sz[s]; tid_i = d.stid[s]; }
+    }
+    const int b = (d.n_trains == 1 || !home) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
+    const Train& tr = d.trains[b];
+    const uint32_t ti = tid_type(tid_i);
+    home = home && tr.active && !tr.free_jump && tb.reactive_mask[ti] != 0u;
+#pragma unroll
+    for (int t = 0; t < MAXT; ++t) {
+      const int r = tb.pair_rxn[ti][t];
+      T v = static_cast<T>(-1);
+      if (home && r >= 0) {
+        if constexpr (F32L) v = tr.rc2f[r];
+        else v = tr.rc2[r];
+      }
+      rc2[t] = v;
+    }
+    if (__any_sync(0xffffffffu, home)) {
+      // this lane's non-empty ranges: the own cell's later slots, then the occupied
+      // forward cells (13 bit tests in the L2-resident bitmap, then their 16-byte entries)
+      uint32_t* rs_l = &sm.rs[wib][0][lane];
+      uint32_t* re_l = &sm.re[wib][0][lane];
+      uint8_t* rk_l = &sm.rk[wib][0][lane];
+      int nr = 0;
+      if (home) {
+        const int n = tr.n;
+        int ix, iy, iz;
+        cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
+        const uint32_t own_end = static_cast<uint32_t>(d.cell_info[cell].y);
+        if (s + 1u < own_end) { rs_l[0] = s + 1u; re_l[0] = own_end; rk_l[0] = 0; nr = 1; }
+#pragma unroll
+        for (int k = 1; k < N_FWD; ++k) {
+          int ox, oy, oz;
+          fwd_offset(k, ox, oy, oz);
+          const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, ox, n), step_cell(iy, oy, n),
+                                                         step_cell(iz, oz, n), tr.cb);
+          if ((d.occ[nc >> 5] >> (nc & 31u)) & 1u) {
+            const int4 ci = d.cell_info[nc];
+            if (static_cast<uint32_t>(ci.z) == epoch && ci.y > ci.x) {
+              rs_l[32 * nr] = static_cast<uint32_t>(ci.x);
+              re_l[32 * nr] = static_cast<uint32_t>(ci.y);
+              rk_l[32 * nr] = static_cast<uint8_t>(k);
+              ++nr;
+            }
+          }
+        }
+      }
+      // walk the ranges as one flattened list, four neighbours per iteration whose loads
+      // are in flight together; lanes of one cell stay in step (broadcast loads)
+      int ri = 0;
+      uint32_t j = 0, je = 0;
+      float cx = 0.f, cy = 0.f, cz = 0.f;
+      auto open = [&](int r) {
+        j = rs_l[32 * r];
+        je = re_l[32 * r];
+        if constexpr (F32L) {
+          int ox, oy, oz;
+          fwd_offset(rk_l[32 * r], ox, oy, oz);
+          cx = ox * tr.hf; cy = oy * tr.hf; cz = oz * tr.hf;
+        }
+      };
+      if (nr > 0) open(0);
+      while (__any_sync(0xffffffffu, ri < nr)) {
+        uint32_t ju[4];
+        bool vu[4];
+        float cxu[4], cyu[4], czu[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          vu[u] = ri < nr;
+          ju[u] = j;
+          cxu[u] = cx; cyu[u] = cy; czu[u] = cz;
+          if (vu[u] && ++j == je) {
+            if (++ri < nr) open(ri);
+          }
+        }
+        float4 vj[4];
+        uint32_t tj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          vj[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          tj[u] = 0u;
+          if (vu[u]) {
+            if constexpr (F32L) vj[u] = d.s4[ju[u]];
+            else tj[u] = d.stid[ju[u]];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t jj = ju[u];
+          bool pass = false;
+          float fx = 0.f, fy = 0.f, fz = 0.f, f2 = 0.f;
+          double rx1 = 0, ry1 = 0, rz1 = 0, d1sq = 0;
+          if (vu[u]) {
+            if constexpr (F32L) {
+              const float c2 = rc2[__float_as_uint(vj[u].w) & 7u];
+              fx = cxu[u] + (vj[u].x - vi.x); fy = cyu[u] + (vj[u].y - vi.y); fz = czu[u] + (vj[u].z - vi.z);
+              f2 = fx * fx + fy * fy + fz * fz;
+              pass = f2 < c2;
+            } else {
+              const double c2 = rc2[tj[u] & 7u];
+              if (c2 >= 0.0) {
+                // minimum image of x_j - x_i (Eq. 2); negated later into the reference's
+                // x_hi - x_lo orientation, which is exact for pairs inside the cutoff
+                rx1 = min_image(__dsub_rn(d.sx[jj], xi), tr.L, tr.halfL);
+                ry1 = min_image(__dsub_rn(d.sy[jj], yi), tr.L, tr.halfL);
+                rz1 = min_image(__dsub_rn(d.sz[jj], zi), tr.L, tr.halfL);
+                d1sq = sq3(rx1, ry1, rz1);
+                pass = d1sq < c2;
+              }
+            }
+          }
+          const uint32_t bal = __ballot_sync(0xffffffffu, pass);
+          if (bal) {
+            const uint32_t base = q.n;
+            if (pass) {
+              const uint32_t pos = base + __popc(bal & lanemask_lt);
+              q.si[pos] = s; q.j[pos] = jj; q.tid_i[pos] = tid_i; q.b[pos] = static_cast<uint32_t>(b);
+              if constexpr (F32L) { q.fx[pos] = fx; q.fy[pos] = fy; q.fz[pos] = fz; q.f2[pos] = f2; }
+              else { q.rx[pos] = rx1; q.ry[pos] = ry1; q.rz[pos] = rz1; q.d2[pos] = d1sq; }
+            }
+            __syncwarp();
+            if (lane == 0) q.n = base + __popc(bal);
+            __syncwarp();
+            if (q.n > static_cast<uint32_t>(TpsQueue<F32L>::CAP) - 32u) tps_flush<F32L>(d, tb, q, vf, lane);
+          }
+        }
+      }
+    }
+    c_next = __shfl_sync(0xffffffffu, c_next, 0);
+  }
+  tps_flush<F32L>(d, tb, q, vf, lane);
 }
 
 // ======================================================================== react

@@ -10,7 +10,10 @@
 //  * cell_sorted[cap]: global cell of every slot of S (train = cell -> train lookup)
 //  * radix scratch keys[2][cap], vals[2][cap] (reused as the matching arrays)
 //  * cell_info[total_cells]: int4 {first slot, end slot, epoch stamp, 0}. An entry is
-//    valid only when its stamp equals the current step epoch, so nothing is cleared.
+//    valid only when its stamp equals the current step epoch, so the table (large at
+//    fine grids) is never cleared.
+//  * occ[total_cells / 32]: occupancy bitmap (one bit per cell, a few MB, L2-resident),
+//    cleared and rebuilt every step; the pair search tests it before reading an entry.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -147,7 +150,8 @@ struct Dev {
   uint8_t* dead;
   uint32_t* touch;       // accepted pairs per slot this step (zero between steps)
   int4* cell_info;
-  uint8_t* cstamp;       // low byte of the epoch of each cell's last occupancy
+  uint32_t* occ;         // occupancy bitmap, one bit per cell, rebuilt every step
+  uint32_t occ_vec4;     // its size in 16-byte words
   unsigned long long* lookback;
   uint32_t max_tiles;
   Cand* cand;

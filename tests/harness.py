@@ -15,7 +15,7 @@ def cuda_available():
 
 def gpu_run(wl, seed, precision=chem.CHEM_FP64, t_end=None, capacity=None, record=True,
             steps_per_launch=0, cells_per_axis_max=0, train_id=0, t_stops=None,
-            launch_mode=chem.CHEM_LAUNCH_AUTO):
+            launch_mode=chem.CHEM_LAUNCH_AUTO, tuning=None):
     import torch
     s = wl.schedule
     n = wl.n_species
@@ -32,6 +32,8 @@ def gpu_run(wl, seed, precision=chem.CHEM_FP64, t_end=None, capacity=None, recor
     ctx = chem.chem_init(cfg)
     out = {}
     try:
+        if tuning is not None:
+            chem.chem_set_tuning(ctx, *tuning)
         for p in wl.pulses:
             chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
         stops = list(t_stops or []) + [t_end if t_end is not None else wl.t_end]
