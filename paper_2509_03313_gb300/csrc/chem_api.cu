@@ -54,7 +54,8 @@ struct chem_ctx {
   int steps_per_launch = 16;
   bool persistent = false;
   int cell_factor_x100 = 1600;  // hash cells per species (x100) of the runtime grid limit
-  int item_home = ITEM_HOME;     // home species per pair-search work item
+  int item_home = 0;             // pair search: 0 = one thread per home species, else
+                                 // home species per warp work item
   Global* g_pinned = nullptr;  // host copy of the global counters
   double* t_end_pinned = nullptr;
   double* t_end_dev = nullptr;
@@ -569,7 +570,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     int n_alloc = c.cells_per_axis_max, n_max = c.cells_per_axis_max;
     if (n_alloc <= 0) {
       const double cap_sp = static_cast<double>(c.capacity_species);
-      n_alloc = static_cast<int>(std::floor(std::cbrt(cap_sp * 64.0)));
+      n_alloc = static_cast<int>(std::floor(std::cbrt(cap_sp * 128.0)));
       n_alloc = std::max(3, std::min(n_alloc, 512));
       n_max = static_cast<int>(std::floor(std::cbrt(cap_sp * ctx->cell_factor_x100 / 100.0)));
       n_max = std::max(3, std::min(n_max, n_alloc));
@@ -978,8 +979,10 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  // ---- restore the state and apply the best parameters
+  // ---- restore the state and apply the best parameters (the trials' occupancy bits
+  // are cleared; stale ones would only cost lookups)
   CK(copies(false));
+  CK(cudaMemsetAsync(d.occ, 0, static_cast<size_t>(d.occ_vec4) * 16, ctx->stream));
   {
     const uint32_t epoch_now = ctx->g_pinned->epoch;
     Global& gfix = *ctx->g_pinned;

@@ -383,18 +383,19 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
   const uint32_t stride = gridDim.x * blockDim.x;
   uint32_t n_dead_local = 0;
   if (ok) {
-    // the occupancy bitmap is rebuilt by this step's gather (the last step's search has
-    // finished reading it)
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < d.occ_vec4; w += stride)
-      reinterpret_cast<uint4*>(d.occ)[w] = make_uint4(0u, 0u, 0u, 0u);
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_total; s += stride) {
       uint32_t key;
+      // the occupancy bitmap is rebuilt by this step's gather: clear the words holding
+      // the last step's cells (the first slot of each run of equal cells clears its word;
+      // the last step's search has finished reading them)
+      const uint32_t cell_old = d.cell_sorted[s];
+      if (s == 0 || d.cell_sorted[s - 1] != cell_old) d.occ[cell_old >> 5] = 0u;
       if (d.dead[s]) {
         d.dead[s] = 0;
         key = d.sentinel;
         ++n_dead_local;
       } else {
-        const uint32_t cell = d.cell_sorted[s];
+        const uint32_t cell = cell_old;
         const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
         const Train& tr = d.trains[b];
         if (!tr.active) {
@@ -654,31 +655,63 @@ __device__ __forceinline__ void emit_candidate(const Dev& d, uint32_t s_lo, uint
 }
 
 // Accept iff u < p with p evaluated in FP64 from the FP32 squared distances:
-// p = 1 when d0 <= R or d1 <= R, else exp(-(d0 - R)(d1 - R) / (D_AB dt)). An FP32
-// estimate decides whenever it lies farther from u than twice its error bound (FP32
-// rounding of d0, d1, R and of the products, cancellation in d - R, and __expf);
-// otherwise the FP64 value decides, so the outcome is always that of the FP64 test.
+// p = 1 when d0 <= R or d1 <= R, else exp(-(d0 - R)(d1 - R) / (D_AB dt)). The uniform
+// u = (w0:w1 >> 11) 2^-53 of the pair's Philox block lies in [k 2^-24, (k + 1) 2^-24)
+// with k = w0 >> 8, bounds that are exact in FP32. An FP32 estimate of p decides
+// whenever those bounds clear it by twice its error bound (FP32 rounding of d0, d1, R
+// and of the products, cancellation in d - R, and the documented __expf error);
+// otherwise u and p are formed in FP64, so the outcome is always that of the FP64 test.
+// The fast path uses no FP64 arithmetic (a slow pipe on this part).
 __device__ __forceinline__ bool accept_f32(float d0sq, float d1sq, int r, const Tables& tb, const Train& tr,
                                           uint32_t id_lo, uint32_t id_hi) {
   const float d1f = sqrtf(d1sq), d0f = sqrtf(d0sq);
   const float Rf = tb.Rf[r];
-  const double u = pair_uniform(id_lo, id_hi, tr.step, tr.key0, tr.key1);
   if (d1f < Rf * 0.999f || d0f < Rf * 0.999f) return true;  // p = 1 > u
+  const uint4 w = philox4x32_10(make_uint4(id_lo, tr.step, id_hi, 2u), tr.key0, tr.key1);
   if (d1f > Rf * 1.001f && d0f > Rf * 1.001f) {
     const float a = d0f - Rf, b = d1f - Rf, inv = tr.inv_ddt_f[r];
     const float x = a * b * inv;
     if (x > 60.f) {
-      if (u != 0.0) return false;  // p < 1e-26 < 2^-53 <= u
+      if ((w.x | (w.y >> 11)) != 0u) return false;  // p < 1e-26 < 2^-53 <= u
     } else {
       const float p = __expf(-x);
       const float err = 1.2e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x);
-      const double band = 2.0 * static_cast<double>(err) * p + 1e-300;
-      if (u > static_cast<double>(p) + band) return false;
-      if (u < static_cast<double>(p) - band) return true;
+      const float band = 2.f * err * p;
+      const float ulo = static_cast<float>(w.x >> 8) * 5.9604645e-8f;  // k 2^-24 <= u
+      if (ulo >= p + band) return false;
+      if (ulo + 5.9604645e-8f <= p - band) return true;               // u < (k + 1) 2^-24
     }
   }
+  const double u = __dmul_rn(static_cast<double>(u53(w.x, w.y)), TWO_POW_M53);
   const double d0 = sqrt(static_cast<double>(d0sq)), d1 = sqrt(static_cast<double>(d1sq));
   return u < bridge_p(d0, d1, tb.R[r], tr.ddt[r]);
+}
+
+// The same test for FP64 squared distances: the FP32 estimate starts from their FP32
+// roundings (one more rounding, covered by a doubled distance term in the error
+// bound), and the exact fallback is the FP64 reference's own arithmetic.
+__device__ __forceinline__ bool accept_f64(double d0sq, double d1sq, int r, const Tables& tb, const Train& tr,
+                                          uint32_t id_lo, uint32_t id_hi) {
+  const float d1f = sqrtf(static_cast<float>(d1sq)), d0f = sqrtf(static_cast<float>(d0sq));
+  const float Rf = tb.Rf[r];
+  if (d1f < Rf * 0.999f || d0f < Rf * 0.999f) return true;  // p = 1 > u
+  const uint4 w = philox4x32_10(make_uint4(id_lo, tr.step, id_hi, 2u), tr.key0, tr.key1);
+  if (d1f > Rf * 1.001f && d0f > Rf * 1.001f) {
+    const float a = d0f - Rf, b = d1f - Rf, inv = tr.inv_ddt_f[r];
+    const float x = a * b * inv;
+    if (x > 60.f) {
+      if ((w.x | (w.y >> 11)) != 0u) return false;
+    } else {
+      const float p = __expf(-x);
+      const float err = 2.4e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x);
+      const float band = 2.f * err * p;
+      const float ulo = static_cast<float>(w.x >> 8) * 5.9604645e-8f;
+      if (ulo >= p + band) return false;
+      if (ulo + 5.9604645e-8f <= p - band) return true;
+    }
+  }
+  const double u = __dmul_rn(static_cast<double>(u53(w.x, w.y)), TWO_POW_M53);
+  return u < bridge_p(sqrt(d0sq), sqrt(d1sq), tb.R[r], tr.ddt[r]);
 }
 
 // Slow path of one pair that passed the cutoff: orientation, this step's
@@ -720,11 +753,7 @@ __device__ __forceinline__ void pair_accept(const Dev& d, const Tables& tb, cons
     const double r0x = __dsub_rn(rx1, __dsub_rn(ehx, elx));
     const double r0y = __dsub_rn(ry1, __dsub_rn(ehy, ely));
     const double r0z = __dsub_rn(rz1, __dsub_rn(ehz, elz));
-    const double d1 = sqrt(d1sq);
-    const double d0 = sqrt(sq3(r0x, r0y, r0z));
-    const double p = bridge_p(d0, d1, tb.R[r], tr.ddt[r]);
-    const double u = pair_uniform(id_lo, id_hi, tr.step, tr.key0, tr.key1);
-    if (!(u < p)) return;
+    if (!accept_f64(sq3(r0x, r0y, r0z), d1sq, r, tb, tr, id_lo, id_hi)) return;
     emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, d1sq);
   }
 }
@@ -998,11 +1027,7 @@ __device__ __forceinline__ void tps_accept(const Dev& d, const Tables& tb, const
     const double r0x = __dsub_rn(rx1, __dsub_rn(ehx, elx));
     const double r0y = __dsub_rn(ry1, __dsub_rn(ehy, ely));
     const double r0z = __dsub_rn(rz1, __dsub_rn(ehz, elz));
-    const double d1 = sqrt(d1sq);
-    const double d0 = sqrt(sq3(r0x, r0y, r0z));
-    const double p = bridge_p(d0, d1, tb.R[r], tr.ddt[r]);
-    const double u = pair_uniform(id_lo, id_hi, tr.step, tr.key0, tr.key1);
-    if (!(u < p)) return;
+    if (!accept_f64(sq3(r0x, r0y, r0z), d1sq, r, tb, tr, id_lo, id_hi)) return;
     emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, d1sq);
   }
 }

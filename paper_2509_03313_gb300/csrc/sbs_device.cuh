@@ -12,8 +12,10 @@
 //  * cell_info[total_cells]: int4 {first slot, end slot, epoch stamp, 0}. An entry is
 //    valid only when its stamp equals the current step epoch, so the table (large at
 //    fine grids) is never cleared.
-//  * occ[total_cells / 32]: occupancy bitmap (one bit per cell, a few MB, L2-resident),
-//    cleared and rebuilt every step; the pair search tests it before reading an entry.
+//  * occ[total_cells / 32]: occupancy bitmap (one bit per cell, L2-resident in use),
+//    rebuilt every step (the diffusion clears the words of the last step's cells); the
+//    pair search tests it before reading an entry. A stale bit only costs a lookup:
+//    the entry's epoch stamp still decides.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
