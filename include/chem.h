@@ -223,7 +223,8 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen);
 chem_status chem_set_tuning(chem_ctx* ctx, const int32_t* tuning);
 
 /* Counters of a context since chem_init (host side, exact). Phase indices:
- * 0 step begin, 1 release, 2 diffusion + hash keys, 3 radix sort (all passes),
+ * 0 step begin, 1 release (runs inside the diffusion kernel, so 0), 2 release +
+ * diffusion + hash keys, 3 radix sort (all passes),
  * 4 gather + cell ranges, 5 pair search, 6 matching + products + tallies,
  * 7 persistent step kernel (batched contexts). phase_ms and phase_launches are only
  * accumulated while profiling is on (chem_set_profiling), from CUDA events recorded

@@ -220,7 +220,7 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
   t.key1 = static_cast<uint32_t>(c.seed >> 32) ^ c.train_id;
 }
 
-int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 9 + ctx->d.passes; }
+int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 8 + ctx->d.passes; }
 
 chem_status capture_graph(chem_ctx* ctx) {
   ctx->lc.search_tps = ctx->item_home == 0 ? 1 : 0;
@@ -297,7 +297,7 @@ chem_status run_loop(chem_ctx* ctx) {
           cudaEvent_t* ev = &ctx->events[static_cast<size_t>(st) * 2 * N_PHASES];
           if (cudaEventElapsedTime(&ms, ev[2 * ph], ev[2 * ph + 1]) == cudaSuccess) {
             ctx->stats.phase_ms[ph] += ms;
-            ctx->stats.phase_launches[ph] += ph == PH_SORT ? ctx->d.passes : 1;
+            ctx->stats.phase_launches[ph] += ph == PH_SORT ? ctx->d.passes : (ph == PH_RELEASE ? 0 : 1);
           }
         }
       }

@@ -51,11 +51,6 @@ __device__ __forceinline__ void grid_sync(const Dev& d) {
 }
 
 template <bool F32L>
-__global__ void __launch_bounds__(256) k_release(const __grid_constant__ Dev d) {
-  phase_release<F32L>(d);
-}
-
-template <bool F32L>
 __global__ void __launch_bounds__(256) k_diffuse(const __grid_constant__ Dev d) {
   __shared__ uint32_t hist[MAX_PASSES][RADIX];
   phase_diffuse<F32L>(d, hist);
@@ -93,9 +88,7 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev 
   for (int step = 0; step < n_steps; ++step) {
     if (blockIdx.x == 0) phase_begin(d, sm.begin);
     grid_sync(d);
-    phase_release<F32L>(d);
-    grid_sync(d);
-    phase_diffuse<F32L>(d, sm.hist);
+    phase_diffuse<F32L>(d, sm.hist);  // includes the release
     grid_sync(d);
     for (int p = 0; p < d.passes; ++p) {
       phase_sort_pass(d, p, sm.sort);
@@ -131,8 +124,7 @@ cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cu
   cudaError_t e = enqueue_begin(d, s);
   if (e != cudaSuccess) return e;
   mark(2 * PH_BEGIN + 1);
-  mark(2 * PH_RELEASE);
-  k_release<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
+  mark(2 * PH_RELEASE);  // the release runs inside the diffusion kernel
   mark(2 * PH_RELEASE + 1);
   mark(2 * PH_DIFFUSE);
   k_diffuse<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);

@@ -19,7 +19,8 @@ __global__ void __launch_bounds__(256) k_match_fast(const __grid_constant__ Dev 
   phase_match_fast(d);
 }
 
-constexpr size_t REACT_SERIAL_DYN_SMEM = 4 * EV_SMEM_CAP * sizeof(uint32_t);
+constexpr size_t REACT_SERIAL_DYN_SMEM = (4 * EV_SMEM_CAP * sizeof(uint32_t) > RC_SMEM_BYTES)
+                                           ? 4 * EV_SMEM_CAP * sizeof(uint32_t) : RC_SMEM_BYTES;
 
 __global__ void __launch_bounds__(REACT_THREADS) k_react_serial(const __grid_constant__ Dev d) {
   __shared__ SerialSmem sm;

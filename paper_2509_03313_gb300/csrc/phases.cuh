@@ -325,93 +325,97 @@ __device__ __forceinline__ void count_add(const Dev& d, uint32_t b, uint32_t typ
 }
 
 // ======================================================================== release
-template <bool F32L>
-__device__ void phase_release(const Dev& d) {
-  if (status_of(d)) return;
-  const uint32_t n_rel = d.g->n_released;
-  const uint32_t base = d.g->n_total - n_rel;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  const uint32_t n_iter = (n_rel + stride - 1) / stride;
-  for (uint32_t it = 0; it < n_iter; ++it) {
-    const uint32_t i = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < n_rel;
-    uint32_t b = 0, type = 0;
-    if (valid) {
-      const uint32_t slot = base + i;
-      b = train_of_release(d, slot);
-      const Train& tr = d.trains[b];
-      const uint32_t k = slot - tr.rel_off;
-      const uint32_t p = tr.pend_base + tr.rel_p0 + k;
-      type = static_cast<uint32_t>(d.p_type[p]);
-      const uint32_t id = tr.rel_id0 + k;
-      const uint32_t tid = (id << 3) | type;
-      const double x = d.px[p], y = d.py[p], z = d.pz[p];
-      if (F32L) {
-        const int n = tr.n_ref;
-        const double h = tr.h_ref, inv_h = static_cast<double>(n) * tr.inv_L;
-        const int ix = cell_index(x, tr.halfL, inv_h, n);
-        const int iy = cell_index(y, tr.halfL, inv_h, n);
-        const int iz = cell_index(z, tr.halfL, inv_h, n);
-        const float ox = static_cast<float>(__dsub_rn(__dadd_rn(x, tr.halfL), __dmul_rn(ix, h)));
-        const float oy = static_cast<float>(__dsub_rn(__dadd_rn(y, tr.halfL), __dmul_rn(iy, h)));
-        const float oz = static_cast<float>(__dsub_rn(__dadd_rn(z, tr.halfL), __dmul_rn(iz, h)));
-        d.s4[slot] = make_float4(ox, oy, oz, __uint_as_float(tid));
-        d.cell_sorted[slot] = tr.cell_base + cell_encode(ix, iy, iz, tr.cb);
-      } else {
-        d.sx[slot] = x;
-        d.sy[slot] = y;
-        d.sz[slot] = z;
-        d.stid[slot] = tid;
-        d.cell_sorted[slot] = tr.cell_base;  // FP64 mode recomputes cells from positions
-      }
-      d.dead[slot] = 0;
-    }
-    count_add(d, b, type, 1, valid);
-  }
-}
 
 // ======================================================================== diffuse
 // Displace every species of an active train (Sec. 2.1 SBS step) with periodic wrap
 // (Eq. 1), compute its hash key, and accumulate the radix histograms of every pass.
-// Species marked dead by the last step's reactions get the sentinel key.
+// Species marked dead by the last step's reactions get the sentinel key. Species
+// released this step (slots [n_total - n_released, n_total)) are first built from the
+// pending queue (the release of Sec. 2.1) by the thread that then diffuses them.
 template <bool F32L>
 __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
   for (int i = threadIdx.x; i < MAX_PASSES * RADIX; i += blockDim.x) (&hist[0][0])[i] = 0u;
   __syncthreads();
-  const bool ok = status_of(d) == 0;
+  // the trip count below must be the same for a whole warp (count_add votes)
+  const bool ok = __shfl_sync(0xffffffffu, status_of(d) == 0 ? 1 : 0, 0) != 0;
   const uint32_t n_total = d.g->n_total;
+  const uint32_t rel_base = n_total - d.g->n_released;
   const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t n_iter = ok ? (n_total + stride - 1) / stride : 0u;
   uint32_t n_dead_local = 0;
-  if (ok) {
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_total; s += stride) {
+  for (uint32_t it = 0; it < n_iter; ++it) {
+    const uint32_t s = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = s < n_total;
+    const bool rel = valid && s >= rel_base;
+    uint32_t rel_b = 0, rel_type = 0;
+    if (valid) {
       uint32_t key;
-      // the occupancy bitmap is rebuilt by this step's gather: clear the words holding
-      // the last step's cells (the first slot of each run of equal cells clears its word;
-      // the last step's search has finished reading them)
-      const uint32_t cell_old = d.cell_sorted[s];
-      if (s == 0 || d.cell_sorted[s - 1] != cell_old) d.occ[cell_old >> 5] = 0u;
-      if (d.dead[s]) {
+      uint32_t cell;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      double px = 0, py = 0, pz = 0;
+      uint32_t tid = 0;
+      bool dead = false;
+      if (rel) {
+        // release: id in (arrival, call order) order, position from the pending queue
+        rel_b = train_of_release(d, s);
+        const Train& tr = d.trains[rel_b];
+        const uint32_t k = s - tr.rel_off;
+        const uint32_t p = tr.pend_base + tr.rel_p0 + k;
+        rel_type = static_cast<uint32_t>(d.p_type[p]);
+        tid = ((tr.rel_id0 + k) << 3) | rel_type;
+        px = d.px[p]; py = d.py[p]; pz = d.pz[p];
+        if (F32L) {
+          const int n = tr.n_ref;
+          const double h = tr.h_ref, inv_h = static_cast<double>(n) * tr.inv_L;
+          const int ix = cell_index(px, tr.halfL, inv_h, n);
+          const int iy = cell_index(py, tr.halfL, inv_h, n);
+          const int iz = cell_index(pz, tr.halfL, inv_h, n);
+          v = make_float4(static_cast<float>(__dsub_rn(__dadd_rn(px, tr.halfL), __dmul_rn(ix, h))),
+                          static_cast<float>(__dsub_rn(__dadd_rn(py, tr.halfL), __dmul_rn(iy, h))),
+                          static_cast<float>(__dsub_rn(__dadd_rn(pz, tr.halfL), __dmul_rn(iz, h))),
+                          __uint_as_float(tid));
+          cell = tr.cell_base + cell_encode(ix, iy, iz, tr.cb);
+          d.s4[s] = v;
+        } else {
+          cell = tr.cell_base;  // FP64 mode recomputes cells from positions
+          d.sx[s] = px; d.sy[s] = py; d.sz[s] = pz; d.stid[s] = tid;
+        }
+        d.cell_sorted[s] = cell;
         d.dead[s] = 0;
+      } else {
+        cell = d.cell_sorted[s];
+        // the occupancy bitmap is rebuilt by this step's gather: clear the words holding
+        // the last step's cells (the first slot of each run of equal cells clears its
+        // word; the last step's search has finished reading them)
+        if (s == 0 || d.cell_sorted[s - 1] != cell) d.occ[cell >> 5] = 0u;
+        dead = d.dead[s] != 0;
+        if (dead) {
+          d.dead[s] = 0;
+        } else if (F32L) {
+          v = d.s4[s];
+        } else {
+          px = d.sx[s]; py = d.sy[s]; pz = d.sz[s]; tid = d.stid[s];
+        }
+      }
+      if (dead) {
         key = d.sentinel;
         ++n_dead_local;
       } else {
-        const uint32_t cell = cell_old;
         const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
         const Train& tr = d.trains[b];
         if (!tr.active) {
-          if (F32L) d.t4[s] = d.s4[s];
-          else { d.tx[s] = d.sx[s]; d.ty[s] = d.sy[s]; d.tz[s] = d.sz[s]; d.ttid[s] = d.stid[s]; }
+          if (F32L) d.t4[s] = v;
+          else { d.tx[s] = px; d.ty[s] = py; d.tz[s] = pz; d.ttid[s] = tid; }
           key = cell;
         } else if (!F32L) {
-          const uint32_t tid = d.stid[s];
           const uint32_t ty = tid_type(tid);
           double g0, g1, g2;
           gauss3_f64(tid_id(tid), tr.step, tr.key0, tr.key1, g0, g1, g2);
           const double sig = tr.sig[ty];
           const double ex = __dmul_rn(sig, g0), ey = __dmul_rn(sig, g1), ez = __dmul_rn(sig, g2);
-          const double x = wrap_box(__dadd_rn(d.sx[s], ex), tr.L, tr.halfL);
-          const double y = wrap_box(__dadd_rn(d.sy[s], ey), tr.L, tr.halfL);
-          const double z = wrap_box(__dadd_rn(d.sz[s], ez), tr.L, tr.halfL);
+          const double x = wrap_box(__dadd_rn(px, ex), tr.L, tr.halfL);
+          const double y = wrap_box(__dadd_rn(py, ey), tr.L, tr.halfL);
+          const double z = wrap_box(__dadd_rn(pz, ez), tr.L, tr.halfL);
           d.tx[s] = x; d.ty[s] = y; d.tz[s] = z; d.ttid[s] = tid;
           d.tdx[s] = ex; d.tdy[s] = ey; d.tdz[s] = ez;
           const int n = tr.n;
@@ -420,11 +424,10 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
           const int iz = cell_index(z, tr.halfL, tr.inv_h, n);
           key = tr.cell_base + cell_encode(ix, iy, iz, tr.cb);
         } else {
-          const float4 v = d.s4[s];
-          const uint32_t tid = __float_as_uint(v.w);
-          const uint32_t ty = tid_type(tid);
+          const uint32_t ftid = __float_as_uint(v.w);
+          const uint32_t ty = tid_type(ftid);
           float g0, g1, g2;
-          gauss3_f32(tid_id(tid), tr.step, tr.key0, tr.key1, g0, g1, g2);
+          gauss3_f32(tid_id(ftid), tr.step, tr.key0, tr.key1, g0, g1, g2);
           const float sig = tr.sigf[ty];
           const int nr = tr.n_ref;
           int ix, iy, iz;
@@ -462,6 +465,7 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
       d.keys0[s] = key;  // the first radix pass takes the slot itself as the value
       for (int p = 0; p < d.passes; ++p) atomicAdd(&hist[p][(key >> (8 * p)) & 255u], 1u);
     }
+    count_add(d, rel_b, rel_type, 1, rel);
   }
   // warp-aggregate the dead count
   for (int o = 16; o > 0; o >>= 1) n_dead_local += __shfl_xor_sync(0xffffffffu, n_dead_local, o);
@@ -989,7 +993,9 @@ struct TpsQueue<false> {
 template <bool F32L, int W>
 struct TpsSmem {
   using T = typename std::conditional<F32L, float, double>::type;
-  T rc2[W][32][MAXT + 1];     // per warp and lane: squared cutoff against each type (-1: none)
+  T ct[W][MAXT * MAXT];       // per warp: squared cutoffs of one train (-1: no reaction) ...
+  int ct_b[W];                // ... that train
+  T rc2[W][32][MAXT + 1];     // per lane rows, for the rare chunk spanning several trains
   uint32_t rs[W][N_FWD][32];  // per lane: its non-empty neighbour ranges [rs, re) ...
   uint32_t re[W][N_FWD][32];
   uint8_t rk[W][N_FWD][32];   // ... and their half-shell offsets
@@ -1061,9 +1067,8 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
   const uint32_t* vf = d.g->sort_any ? (d.g->sort_parity ? d.vals1 : d.vals0) : nullptr;
   const Tables& tb = *d.tables;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  T(&rc2)[MAXT + 1] = sm.rc2[wib][lane];
   TpsQueue<F32L>& q = sm.q[wib];
-  if (lane == 0) q.n = 0;
+  if (lane == 0) { q.n = 0; sm.ct_b[wib] = -1; }
   __syncwarp();
   const uint32_t lanemask_lt = (1u << lane) - 1u;
   const uint32_t n_chunks = (n_live + 31u) / 32u;
@@ -1087,15 +1092,41 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
     const Train& tr = d.trains[b];
     const uint32_t ti = tid_type(tid_i);
     home = home && tr.active && !tr.free_jump && tb.reactive_mask[ti] != 0u;
-#pragma unroll
-    for (int t = 0; t < MAXT; ++t) {
-      const int r = tb.pair_rxn[ti][t];
-      T v = static_cast<T>(-1);
-      if (home && r >= 0) {
-        if constexpr (F32L) v = tr.rc2f[r];
-        else v = tr.rc2[r];
+    // cutoff row of this lane's type: from the warp's table of its train when every
+    // lane of the chunk is in one train (refilled only when the train changes), else
+    // from a per-lane row
+    const int b0 = __shfl_sync(0xffffffffu, b, 0);
+    const T* rc2;
+    if (__all_sync(0xffffffffu, b == b0)) {
+      if (sm.ct_b[wib] != b0) {
+        const Train& t0 = d.trains[b0];
+        for (int qq = lane; qq < MAXT * MAXT; qq += 32) {
+          const int r = tb.pair_rxn[qq / MAXT][qq % MAXT];
+          T v = static_cast<T>(-1);
+          if (r >= 0) {
+            if constexpr (F32L) v = t0.rc2f[r];
+            else v = t0.rc2[r];
+          }
+          sm.ct[wib][qq] = v;
+        }
+        __syncwarp();
+        if (lane == 0) sm.ct_b[wib] = b0;
+        __syncwarp();
       }
-      rc2[t] = v;
+      rc2 = &sm.ct[wib][ti * MAXT];
+    } else {
+      T* row = sm.rc2[wib][lane];
+#pragma unroll
+      for (int t = 0; t < MAXT; ++t) {
+        const int r = tb.pair_rxn[ti][t];
+        T v = static_cast<T>(-1);
+        if (r >= 0) {
+          if constexpr (F32L) v = tr.rc2f[r];
+          else v = tr.rc2[r];
+        }
+        row[t] = v;
+      }
+      rc2 = row;
     }
     if (__any_sync(0xffffffffu, home)) {
       // this lane's non-empty ranges: the own cell's later slots, then the occupied
@@ -1284,12 +1315,15 @@ __device__ __forceinline__ uint32_t event_key(const Dev& d, const Cand& cd) {
   return d.train_bits ? ((b << (32 - d.train_bits)) | cd.id_lo) : cd.id_lo;
 }
 
+// Event value: candidate index (< 2^24) with the reaction's product count in bits 24-25.
+constexpr uint32_t EV_CAND_MASK = 0xFFFFFFu;
+
 __device__ __forceinline__ void commit_event(const Dev& d, uint32_t c, const Cand& cd) {
   d.dead[cd.s_lo] = 1;
   d.dead[cd.s_hi] = 1;
   const uint32_t e = atomicAdd(&d.g->n_events, 1u);
   d.ev_k0[e] = event_key(d, cd);
-  d.ev_v0[e] = c;
+  d.ev_v0[e] = c | (static_cast<uint32_t>(d.tables->n_prod[cd.rxn_train & 255u]) << 24);
 }
 
 static __device__ void phase_match_fast(const Dev& d) {
@@ -1374,6 +1408,120 @@ static __device__ void phase_match_rounds(const Dev& d, MatchSmem& sm) {
   __syncthreads();
 }
 
+// The conflict rounds of phase_match_rounds with everything in shared memory: the
+// conflict pairs, a hash of their slots to local indices, and per local slot the
+// smallest (d1^2) and then smallest (id_lo, id_hi) key of its remaining pairs. Returns
+// false (nothing done) when the conflict list does not fit; the caller then runs the
+// global-memory version. `sbuf` holds RC_SMEM_BYTES.
+constexpr int RC_CAP = 1536;                 // conflict pairs
+constexpr int RC_SLOTS = 2 * RC_CAP;         // distinct slots at most
+constexpr int RC_HASH = 8192;                // >= 2 RC_SLOTS, power of two
+constexpr size_t RC_SMEM_BYTES = static_cast<size_t>(RC_CAP) * (4 + 4 + 4 + 8 + 8) +
+                                 static_cast<size_t>(RC_HASH) * 8 + static_cast<size_t>(RC_SLOTS) * (8 + 8 + 4) +
+                                 static_cast<size_t>(RC_CAP) * 8;
+
+static __device__ bool phase_match_rounds_smem(const Dev& d, MatchSmem& sm, uint32_t* sbuf) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const bool ok = block_status_ok(d);
+  const uint32_t n_c = ok ? d.g->n_conflict : 0u;
+  if (n_c > static_cast<uint32_t>(RC_CAP)) return false;  // uniform
+  // carve the buffer (8-byte arrays first)
+  unsigned long long* kd = reinterpret_cast<unsigned long long*>(sbuf);
+  unsigned long long* kp = kd + RC_CAP;
+  unsigned long long* bd = kp + RC_CAP;
+  unsigned long long* bp = bd + RC_SLOTS;
+  uint32_t* hkey = reinterpret_cast<uint32_t*>(bp + RC_SLOTS);
+  uint32_t* hval = hkey + RC_HASH;
+  uint32_t* lo = hval + RC_HASH;
+  uint32_t* hi = lo + RC_CAP;
+  uint32_t* cix = hi + RC_CAP;
+  uint32_t* alive = cix + RC_CAP;
+  uint32_t* nxt = alive + RC_CAP;
+  uint32_t* ldead = nxt + RC_CAP;
+  for (int i = tid; i < RC_HASH; i += nt) hkey[i] = 0xFFFFFFFFu;
+  for (int i = tid; i < RC_SLOTS; i += nt) ldead[i] = 0u;
+  if (tid == 0) { sm.n_alive = n_c; sm.n_next = 0; }
+  __syncthreads();
+  // load the pairs, reset the accepted-pair counts for the next step, insert the slots
+  for (uint32_t i = tid; i < n_c; i += nt) {
+    const uint32_t c = d.alive0[i];
+    const Cand cd = d.cand[c];
+    d.touch[cd.s_lo] = 0u;
+    d.touch[cd.s_hi] = 0u;
+    cix[i] = c;
+    kd[i] = static_cast<unsigned long long>(__double_as_longlong(cd.d1sq));
+    kp[i] = (static_cast<unsigned long long>(cd.id_lo) << 32) | cd.id_hi;
+    lo[i] = cd.s_lo;
+    hi[i] = cd.s_hi;
+    alive[i] = i;
+  }
+  __syncthreads();
+  // slot -> local index: open addressing; the thread whose CAS claims a bucket numbers it
+  for (uint32_t e = tid; e < 2 * n_c; e += nt) {
+    const uint32_t slot = (e & 1u) ? hi[e >> 1] : lo[e >> 1];
+    uint32_t h = (slot * 2654435761u) & (RC_HASH - 1);
+    for (int probe = 0; probe < RC_HASH; ++probe) {
+      const uint32_t prev = atomicCAS(&hkey[h], 0xFFFFFFFFu, slot);
+      if (prev == 0xFFFFFFFFu) { hval[h] = atomicAdd(&sm.n_next, 1u); break; }
+      if (prev == slot) break;
+      h = (h + 1u) & (RC_HASH - 1);
+    }
+  }
+  __syncthreads();
+  for (uint32_t e = tid; e < 2 * n_c; e += nt) {
+    const uint32_t slot = (e & 1u) ? hi[e >> 1] : lo[e >> 1];
+    uint32_t h = (slot * 2654435761u) & (RC_HASH - 1);
+    for (int probe = 0; probe < RC_HASH && hkey[h] != slot; ++probe) h = (h + 1u) & (RC_HASH - 1);
+    if (e & 1u) hi[e >> 1] = hval[h]; else lo[e >> 1] = hval[h];
+  }
+  __syncthreads();
+  for (uint32_t round = 0; sm.n_alive > 0; ++round) {
+    if (round > n_c) {
+      if (tid == 0) raise_status(d.g, CHEM_ESTATE);
+      break;
+    }
+    const uint32_t na = sm.n_alive;
+    for (uint32_t a = tid; a < na; a += nt) {
+      const uint32_t i = alive[a];
+      bd[lo[i]] = ~0ull; bd[hi[i]] = ~0ull;
+      bp[lo[i]] = ~0ull; bp[hi[i]] = ~0ull;
+    }
+    __syncthreads();
+    for (uint32_t a = tid; a < na; a += nt) {
+      const uint32_t i = alive[a];
+      atomicMin(&bd[lo[i]], kd[i]);
+      atomicMin(&bd[hi[i]], kd[i]);
+    }
+    __syncthreads();
+    for (uint32_t a = tid; a < na; a += nt) {
+      const uint32_t i = alive[a];
+      if (bd[lo[i]] == kd[i]) atomicMin(&bp[lo[i]], kp[i]);
+      if (bd[hi[i]] == kd[i]) atomicMin(&bp[hi[i]], kp[i]);
+    }
+    __syncthreads();
+    for (uint32_t a = tid; a < na; a += nt) {
+      const uint32_t i = alive[a];
+      if (bd[lo[i]] == kd[i] && bp[lo[i]] == kp[i] && bd[hi[i]] == kd[i] && bp[hi[i]] == kp[i]) {
+        ldead[lo[i]] = 1u;
+        ldead[hi[i]] = 1u;
+        commit_event(d, cix[i], d.cand[cix[i]]);
+      }
+    }
+    if (tid == 0) sm.n_next = 0;
+    __syncthreads();
+    for (uint32_t a = tid; a < na; a += nt) {
+      const uint32_t i = alive[a];
+      if (!ldead[lo[i]] && !ldead[hi[i]]) nxt[atomicAdd(&sm.n_next, 1u)] = i;
+    }
+    __syncthreads();
+    if (tid == 0) sm.n_alive = sm.n_next;
+    uint32_t* t = alive; alive = nxt; nxt = t;
+    __syncthreads();
+  }
+  __syncthreads();
+  return true;
+}
+
 // Stable LSD radix sort of n (key, value) pairs by the whole CTA, 8-bit digits over the
 // 32 key bits. Each warp owns one contiguous chunk of the input and scatters it in order
 // (ranks among equal digits from __match_any_sync), so equal digits keep their order.
@@ -1451,10 +1599,10 @@ static __device__ int block_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1,
 // Product-count prefix over the ordered events (`order`, optionally copied to
 // `order_out`), written to `pref`, plus each train's first prefix, event and product
 // counts.
-static __device__ void products_prefix(const Dev& d, ScanSmem& sm, const uint32_t* order, uint32_t* order_out,
-                                uint32_t* pref, uint32_t E, bool ok) {
+static __device__ void products_prefix(const Dev& d, ScanSmem& sm, const uint32_t* okeys, const uint32_t* order,
+                                       uint32_t* order_out, uint32_t* pref, uint32_t E, bool ok) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const Tables& tb = *d.tables;
+  const int tshift = 32 - static_cast<int>(d.train_bits);
   for (uint32_t b = tid; b < d.n_trains; b += nt) { sm.first_pref[b] = 0; sm.prods_tr[b] = 0; sm.evs_tr[b] = 0; }
   if (tid == 0) sm.carry = 0;
   __syncthreads();
@@ -1464,10 +1612,10 @@ static __device__ void products_prefix(const Dev& d, ScanSmem& sm, const uint32_
     uint32_t b = 0, np = 0;
     bool first = false;
     if (valid) {
-      const uint32_t rt = d.cand[order[k]].rxn_train;
-      b = rt >> 8;
-      np = static_cast<uint32_t>(tb.n_prod[rt & 255u]);
-      first = (k == 0) || ((d.cand[order[k - 1]].rxn_train >> 8) != b);
+      // train from the event key's top bits, product count from the value's
+      b = d.train_bits ? okeys[k] >> tshift : 0u;
+      np = order[k] >> 24;
+      first = (k == 0) || (d.train_bits ? (okeys[k - 1] >> tshift) != b : false);
     }
     uint32_t tot;
     const uint32_t ex = block_excl_scan(np, sm.warp_tot, tot) + sm.carry;
@@ -1503,9 +1651,10 @@ struct SerialSmem {
 // the sort runs in shared memory; otherwise in the global event buffers.
 static __device__ void phase_react_serial(const Dev& d, SerialSmem& sm, uint32_t* sbuf) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  phase_match_rounds(d, sm.match);
+  if (sbuf == nullptr || !phase_match_rounds_smem(d, sm.match, sbuf)) phase_match_rounds(d, sm.match);
   const bool ok = block_status_ok(d);
   const uint32_t E = ok ? min(d.g->n_events, d.cap_cand) : 0u;
+  const uint32_t* okeys;
   const uint32_t* order;
   uint32_t* order_out = nullptr;
   uint32_t* pref;
@@ -1517,17 +1666,19 @@ static __device__ void phase_react_serial(const Dev& d, SerialSmem& sm, uint32_t
     for (uint32_t i = tid; i < E; i += nt) { k0[i] = d.ev_k0[i]; v0[i] = d.ev_v0[i]; }
     __syncthreads();
     const int p = block_sort_pairs(k0, v0, k1, v1, E, sm.sort);
+    okeys = p ? k1 : k0;
     order = p ? v1 : v0;
     order_out = d.ev_v0;
     pref = d.ev_k1;
     if (tid == 0) d.g->ev_parity = 0u;
   } else {
     const int p = block_sort_pairs(d.ev_k0, d.ev_v0, d.ev_k1, d.ev_v1, E, sm.sort);
+    okeys = p ? d.ev_k1 : d.ev_k0;
     order = p ? d.ev_v1 : d.ev_v0;
     pref = p ? d.ev_k0 : d.ev_k1;
     if (tid == 0) d.g->ev_parity = static_cast<uint32_t>(p);
   }
-  products_prefix(d, sm.scan, order, order_out, pref, E, ok);
+  products_prefix(d, sm.scan, okeys, order, order_out, pref, E, ok);
 }
 
 template <bool F32L>
@@ -1545,7 +1696,7 @@ __device__ void phase_products(const Dev& d, ProductsSmem& sm) {
   const uint32_t* pref = d.g->ev_parity ? d.ev_k0 : d.ev_k1;
   const uint32_t n_live = d.g->n_total - d.g->n_dead;
   for (uint32_t k = blockIdx.x * nt + tid; k < E; k += gridDim.x * nt) {
-    const Cand cd = d.cand[order[k]];
+    const Cand cd = d.cand[order[k] & EV_CAND_MASK];
     const uint32_t r = cd.rxn_train & 255u, b = cd.rxn_train >> 8;
     const uint32_t np = static_cast<uint32_t>(tb.n_prod[r]);
     Train& tr = d.trains[b];
