@@ -220,7 +220,7 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
   t.key1 = static_cast<uint32_t>(c.seed >> 32) ^ c.train_id;
 }
 
-int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 8 + ctx->d.passes; }
+int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 7 + ctx->d.passes; }
 
 chem_status capture_graph(chem_ctx* ctx) {
   ctx->lc.search_tps = ctx->item_home == 0 ? 1 : 0;
@@ -245,8 +245,9 @@ chem_status capture_graph(chem_ctx* ctx) {
   } else {
     for (int s = 0; s < ctx->steps_per_launch && e == cudaSuccess; ++s) {
       cudaEvent_t* ev = n_ev ? &ctx->events[static_cast<size_t>(s) * 2 * N_PHASES] : nullptr;
-      e = ctx->precision == CHEM_FP64 ? enqueue_step_f64(ctx->d, ctx->lc, ctx->stream, ev)
-                                      : enqueue_step_f32l(ctx->d, ctx->lc, ctx->stream, ev);
+      const bool first = s == 0, last = s + 1 == ctx->steps_per_launch;
+      e = ctx->precision == CHEM_FP64 ? enqueue_step_f64(ctx->d, ctx->lc, ctx->stream, ev, first, last)
+                                      : enqueue_step_f32l(ctx->d, ctx->lc, ctx->stream, ev, first, last);
     }
   }
   cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
@@ -284,7 +285,9 @@ chem_status run_loop(chem_ctx* ctx) {
     const Global& g = *ctx->g_pinned;
     ctx->stats.graph_replays += 1;
     ctx->stats.steps_launched += ctx->graph_steps;
-    ctx->stats.kernel_launches += ctx->persistent ? 1 : static_cast<int64_t>(ctx->graph_steps) * kernels_per_step(ctx);
+    // per replay: one begin kernel, then every step's kernels (the end kernel of each step
+    // but the last also begins the next)
+    ctx->stats.kernel_launches += ctx->persistent ? 1 : 1 + static_cast<int64_t>(ctx->graph_steps) * kernels_per_step(ctx);
     ctx->stats.bytes_d2h += sizeof(Global);
     const uint32_t stepped = g.steps_active - active_before;
     active_before = g.steps_active;

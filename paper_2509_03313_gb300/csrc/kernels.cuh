@@ -85,9 +85,9 @@ template <bool F32L>
 __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev d, int n_steps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PhaseSmem& sm = *reinterpret_cast<PhaseSmem*>(smem_raw);
+  if (blockIdx.x == 0) phase_begin(d, sm.begin);
+  grid_sync(d);
   for (int step = 0; step < n_steps; ++step) {
-    if (blockIdx.x == 0) phase_begin(d, sm.begin);
-    grid_sync(d);
     phase_diffuse<F32L>(d, sm.hist);  // includes the release
     grid_sync(d);
     for (int p = 0; p < d.passes; ++p) {
@@ -110,19 +110,28 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev 
     grid_sync(d);
     phase_products<F32L>(d, sm.products);
     grid_sync(d);
-    if (blockIdx.x == 0) phase_end_step(d, sm.end);
+    if (blockIdx.x == 0) {
+      phase_end_step(d, sm.end);
+      if (step + 1 < n_steps) phase_begin(d, sm.begin);  // the next step's begin
+    }
     grid_sync(d);
   }
 }
 
 // One step as one kernel per phase. With ev != nullptr, CUDA events are recorded
-// before and after each phase (ev[2 * phase], ev[2 * phase + 1]).
+// before and after each phase (ev[2 * phase], ev[2 * phase + 1]); a step that is not the
+// first of a graph was begun by the previous step's end kernel (its time falls in the
+// previous step's react phase).
 template <bool F32L>
-cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev, bool first,
+                           bool last) {
   auto mark = [&](int i) { if (ev) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal); };
+  cudaError_t e = cudaSuccess;
   mark(2 * PH_BEGIN);
-  cudaError_t e = enqueue_begin(d, s);
-  if (e != cudaSuccess) return e;
+  if (first) {
+    e = enqueue_begin(d, s);
+    if (e != cudaSuccess) return e;
+  }
   mark(2 * PH_BEGIN + 1);
   mark(2 * PH_RELEASE);  // the release runs inside the diffusion kernel
   mark(2 * PH_RELEASE + 1);
@@ -146,7 +155,7 @@ cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cu
   e = enqueue_react_head(d, lc, s);
   if (e != cudaSuccess) return e;
   k_products<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
-  e = enqueue_end_step(d, s);
+  e = last ? enqueue_end_step(d, s) : enqueue_end_begin(d, s);
   if (e != cudaSuccess) return e;
   mark(2 * PH_REACT + 1);
   return cudaGetLastError();

@@ -44,6 +44,18 @@ cudaError_t enqueue_end_step(const Dev& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) k_end_begin(const __grid_constant__ Dev d) {
+  __shared__ EndSmem se;
+  __shared__ BeginSmem sb;
+  phase_end_step(d, se);
+  phase_begin(d, sb);
+}
+
+cudaError_t enqueue_end_begin(const Dev& d, cudaStream_t s) {
+  k_end_begin<<<1, 256, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
 __global__ void k_set_t_end(const __grid_constant__ Dev d, const double* t_end) {
   for (uint32_t b = threadIdx.x; b < d.n_trains; b += blockDim.x) d.trains[b].t_end = t_end[b];
 }
@@ -74,8 +86,9 @@ cudaError_t enqueue_set_t_end(const Dev& d, const double* t_end_dev, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev) {
-  return enqueue_phases<false>(d, lc, s, ev);
+cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev, bool first,
+                             bool last) {
+  return enqueue_phases<false>(d, lc, s, ev, first, last);
 }
 
 cudaError_t enqueue_persistent_f64(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s) {

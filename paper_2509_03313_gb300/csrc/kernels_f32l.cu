@@ -4,8 +4,9 @@
 
 namespace chem {
 
-cudaError_t enqueue_step_f32l(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev) {
-  return enqueue_phases<true>(d, lc, s, ev);
+cudaError_t enqueue_step_f32l(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev, bool first,
+                              bool last) {
+  return enqueue_phases<true>(d, lc, s, ev, first, last);
 }
 
 cudaError_t enqueue_persistent_f32l(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s) {

@@ -24,14 +24,21 @@ cudaError_t enqueue_sort_pass(const Dev& d, int pass, int blocks, cudaStream_t s
 // matching (fast path + conflict rounds), event ordering, product prefix
 cudaError_t enqueue_react_head(const Dev& d, const LaunchCfg& lc, cudaStream_t s);
 cudaError_t enqueue_end_step(const Dev& d, cudaStream_t s);
+// end of one step and begin of the next in one one-CTA kernel
+cudaError_t enqueue_end_begin(const Dev& d, cudaStream_t s);
 cudaError_t sort_pass_occupancy(int* blocks_per_sm);
-cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev);
+// One SBS step. `first`: the step begins with its own begin kernel (else the previous
+// step's end kernel began it); `last`: it ends with a plain end kernel (else its end
+// kernel also begins the next step).
+cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev, bool first,
+                             bool last);
 cudaError_t enqueue_persistent_f64(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s);
 cudaError_t persistent_occupancy_f64(int* blocks_per_sm);
 cudaError_t enqueue_set_t_end(const Dev& d, const double* t_end_dev, cudaStream_t s);
 
 // kernels_f32l.cu (FP32-local mode)
-cudaError_t enqueue_step_f32l(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev);
+cudaError_t enqueue_step_f32l(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev, bool first,
+                              bool last);
 cudaError_t enqueue_persistent_f32l(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s);
 cudaError_t persistent_occupancy_f32l(int* blocks_per_sm);
 

@@ -330,7 +330,7 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   if (ok) {
     k_noalloc_setup<<<1, 1, 0, s>>>(d, tb, tr);
     k_noalloc_load<<<lc.stream_blocks, 256, 0, s>>>(d, n, id, type, xyz);
-    ok = cudaGetLastError() == cudaSuccess && enqueue_step_f64(d, lc, s, nullptr) == cudaSuccess;
+    ok = cudaGetLastError() == cudaSuccess && enqueue_step_f64(d, lc, s, nullptr, true, true) == cudaSuccess;
   }
   if (ok) {
     k_noalloc_store<<<1, 1024, 0, s>>>(d, id_out, type_out, xyz_out, n_out, next_id_out, events_out,

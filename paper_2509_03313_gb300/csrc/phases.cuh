@@ -1274,7 +1274,9 @@ struct BlockSortSmem {
 struct ScanSmem {
   uint32_t carry;
   uint32_t warp_tot[REACT_THREADS / 32];
-  uint32_t first_pref[MAX_TRAINS];
+  uint32_t total;
+  uint32_t first_pref[MAX_TRAINS];  // product prefix at the train's first event ...
+  uint32_t first_k[MAX_TRAINS];     // ... and that event's position
   uint32_t prods_tr[MAX_TRAINS];
   uint32_t evs_tr[MAX_TRAINS];
 };
@@ -1289,7 +1291,9 @@ struct EndSmem {
   uint32_t any;
 };
 
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_tot,
+// Exclusive block-wide prefix of v (one value per thread); `total` gets the block sum.
+// Warp totals are scanned once by warp 0.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_tot, uint32_t* total_s,
                                                     uint32_t& total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t x = v;
@@ -1300,14 +1304,22 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_t
   }
   if (lane == 31) warp_tot[w] = x;
   __syncthreads();
-  uint32_t add = 0, tot = 0;
-  for (int i = 0; i < nw; ++i) {
-    if (i < w) add += warp_tot[i];
-    tot += warp_tot[i];
+  if (w == 0) {
+    const uint32_t t = lane < nw ? warp_tot[lane] : 0u;
+    uint32_t y = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    if (lane < nw) warp_tot[lane] = y - t;
+    if (lane == 31) *total_s = y;
   }
   __syncthreads();
-  total = tot;
-  return x - v + add;
+  total = *total_s;
+  const uint32_t r = x - v + warp_tot[w];
+  __syncthreads();
+  return r;
 }
 
 __device__ __forceinline__ uint32_t event_key(const Dev& d, const Cand& cd) {
@@ -1318,10 +1330,22 @@ __device__ __forceinline__ uint32_t event_key(const Dev& d, const Cand& cd) {
 // Event value: candidate index (< 2^24) with the reaction's product count in bits 24-25.
 constexpr uint32_t EV_CAND_MASK = 0xFFFFFFu;
 
-__device__ __forceinline__ void commit_event(const Dev& d, uint32_t c, const Cand& cd) {
+// Consecutive indices from *counter for the lanes with `pred` set, one atomic per warp.
+// Every lane of the warp must call it.
+__device__ __forceinline__ uint32_t warp_reserve(uint32_t* counter, bool pred) {
+  const uint32_t m = __ballot_sync(0xffffffffu, pred);
+  const int lane = threadIdx.x & 31;
+  const int leader = m ? __ffs(m) - 1 : 0;
+  uint32_t base = 0;
+  if (m && lane == leader) base = atomicAdd(counter, static_cast<uint32_t>(__popc(m)));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + static_cast<uint32_t>(__popc(m & ((1u << lane) - 1u)));
+}
+
+// Record accepted pair c as event number e (reserved by the caller).
+__device__ __forceinline__ void commit_event(const Dev& d, uint32_t c, const Cand& cd, uint32_t e) {
   d.dead[cd.s_lo] = 1;
   d.dead[cd.s_hi] = 1;
-  const uint32_t e = atomicAdd(&d.g->n_events, 1u);
   d.ev_k0[e] = event_key(d, cd);
   d.ev_v0[e] = c | (static_cast<uint32_t>(d.tables->n_prod[cd.rxn_train & 255u]) << 24);
 }
@@ -1329,14 +1353,24 @@ __device__ __forceinline__ void commit_event(const Dev& d, uint32_t c, const Can
 static __device__ void phase_match_fast(const Dev& d) {
   const bool ok = block_status_ok(d);  // includes a barrier
   const uint32_t n_c = ok ? min(d.g->n_cand, d.cap_cand) : 0u;
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n_c; c += gridDim.x * blockDim.x) {
-    const Cand cd = d.cand[c];
-    if (d.touch[cd.s_lo] == 1u && d.touch[cd.s_hi] == 1u) {
-      commit_event(d, c, cd);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t c0 = blockIdx.x * blockDim.x; c0 < n_c; c0 += stride) {  // uniform per block
+    const uint32_t c = c0 + threadIdx.x;
+    const bool valid = c < n_c;
+    Cand cd{};
+    bool lone = false;
+    if (valid) {
+      cd = d.cand[c];
+      lone = d.touch[cd.s_lo] == 1u && d.touch[cd.s_hi] == 1u;
+    }
+    const uint32_t e = warp_reserve(&d.g->n_events, valid && lone);
+    const uint32_t a = warp_reserve(&d.g->n_conflict, valid && !lone);
+    if (valid && lone) {
+      commit_event(d, c, cd, e);
       d.touch[cd.s_lo] = 0u;
       d.touch[cd.s_hi] = 0u;
-    } else {
-      d.alive0[atomicAdd(&d.g->n_conflict, 1u)] = c;
+    } else if (valid) {
+      d.alive0[a] = c;
     }
   }
 }
@@ -1385,20 +1419,34 @@ static __device__ void phase_match_rounds(const Dev& d, MatchSmem& sm) {
       if (bd[cd.s_hi] == kd) atomicMin(&bp[cd.s_hi], kp);
     }
     __syncthreads();
-    for (uint32_t i = tid; i < na; i += nt) {
-      const uint32_t c = alive[i];
-      const Cand cd = d.cand[c];
-      const unsigned long long kd = __double_as_longlong(cd.d1sq);
-      const unsigned long long kp = (static_cast<unsigned long long>(cd.id_lo) << 32) | cd.id_hi;
-      if (bd[cd.s_lo] == kd && bp[cd.s_lo] == kp && bd[cd.s_hi] == kd && bp[cd.s_hi] == kp)
-        commit_event(d, c, cd);
+    for (uint32_t i0 = 0; i0 < na; i0 += nt) {  // uniform trip count (warp_reserve)
+      const uint32_t i = i0 + tid;
+      bool win = false;
+      uint32_t c = 0;
+      Cand cd{};
+      if (i < na) {
+        c = alive[i];
+        cd = d.cand[c];
+        const unsigned long long kd = __double_as_longlong(cd.d1sq);
+        const unsigned long long kp = (static_cast<unsigned long long>(cd.id_lo) << 32) | cd.id_hi;
+        win = bd[cd.s_lo] == kd && bp[cd.s_lo] == kp && bd[cd.s_hi] == kd && bp[cd.s_hi] == kp;
+      }
+      const uint32_t e = warp_reserve(&d.g->n_events, win);
+      if (win) commit_event(d, c, cd, e);
     }
     if (tid == 0) sm.n_next = 0;
     __syncthreads();
-    for (uint32_t i = tid; i < na; i += nt) {
-      const uint32_t c = alive[i];
-      const Cand cd = d.cand[c];
-      if (!d.dead[cd.s_lo] && !d.dead[cd.s_hi]) nxt[atomicAdd(&sm.n_next, 1u)] = c;
+    for (uint32_t i0 = 0; i0 < na; i0 += nt) {
+      const uint32_t i = i0 + tid;
+      bool keep = false;
+      uint32_t c = 0;
+      if (i < na) {
+        c = alive[i];
+        const Cand cd = d.cand[c];
+        keep = !d.dead[cd.s_lo] && !d.dead[cd.s_hi];
+      }
+      const uint32_t a = warp_reserve(&sm.n_next, keep);
+      if (keep) nxt[a] = c;
     }
     __syncthreads();
     if (tid == 0) sm.n_alive = sm.n_next;
@@ -1499,19 +1547,33 @@ static __device__ bool phase_match_rounds_smem(const Dev& d, MatchSmem& sm, uint
       if (bd[hi[i]] == kd[i]) atomicMin(&bp[hi[i]], kp[i]);
     }
     __syncthreads();
-    for (uint32_t a = tid; a < na; a += nt) {
-      const uint32_t i = alive[a];
-      if (bd[lo[i]] == kd[i] && bp[lo[i]] == kp[i] && bd[hi[i]] == kd[i] && bp[hi[i]] == kp[i]) {
+    for (uint32_t a0 = 0; a0 < na; a0 += nt) {  // uniform trip count (warp_reserve)
+      const uint32_t a = a0 + tid;
+      bool win = false;
+      uint32_t i = 0;
+      if (a < na) {
+        i = alive[a];
+        win = bd[lo[i]] == kd[i] && bp[lo[i]] == kp[i] && bd[hi[i]] == kd[i] && bp[hi[i]] == kp[i];
+      }
+      const uint32_t e = warp_reserve(&d.g->n_events, win);
+      if (win) {
         ldead[lo[i]] = 1u;
         ldead[hi[i]] = 1u;
-        commit_event(d, cix[i], d.cand[cix[i]]);
+        commit_event(d, cix[i], d.cand[cix[i]], e);
       }
     }
     if (tid == 0) sm.n_next = 0;
     __syncthreads();
-    for (uint32_t a = tid; a < na; a += nt) {
-      const uint32_t i = alive[a];
-      if (!ldead[lo[i]] && !ldead[hi[i]]) nxt[atomicAdd(&sm.n_next, 1u)] = i;
+    for (uint32_t a0 = 0; a0 < na; a0 += nt) {
+      const uint32_t a = a0 + tid;
+      bool keep = false;
+      uint32_t i = 0;
+      if (a < na) {
+        i = alive[a];
+        keep = !ldead[lo[i]] && !ldead[hi[i]];
+      }
+      const uint32_t q = warp_reserve(&sm.n_next, keep);
+      if (keep) nxt[q] = i;
     }
     __syncthreads();
     if (tid == 0) sm.n_alive = sm.n_next;
@@ -1603,30 +1665,36 @@ static __device__ void products_prefix(const Dev& d, ScanSmem& sm, const uint32_
                                        uint32_t* order_out, uint32_t* pref, uint32_t E, bool ok) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int tshift = 32 - static_cast<int>(d.train_bits);
-  for (uint32_t b = tid; b < d.n_trains; b += nt) { sm.first_pref[b] = 0; sm.prods_tr[b] = 0; sm.evs_tr[b] = 0; }
+  for (uint32_t b = tid; b < d.n_trains; b += nt) {
+    sm.first_pref[b] = 0; sm.first_k[b] = 0; sm.prods_tr[b] = 0; sm.evs_tr[b] = 0;
+  }
   if (tid == 0) sm.carry = 0;
   __syncthreads();
   for (uint32_t t0 = 0; t0 < E; t0 += nt) {
     const uint32_t k = t0 + tid;
     const bool valid = k < E;
     uint32_t b = 0, np = 0;
-    bool first = false;
+    bool first = false, last = false;
     if (valid) {
-      // train from the event key's top bits, product count from the value's
+      // train from the event key's top bits, product count from the value's; events are
+      // in train order, so a train's counts are differences at its last event
       b = d.train_bits ? okeys[k] >> tshift : 0u;
       np = order[k] >> 24;
       first = (k == 0) || (d.train_bits ? (okeys[k - 1] >> tshift) != b : false);
+      last = (k + 1 == E) || (d.train_bits ? (okeys[k + 1] >> tshift) != b : false);
     }
     uint32_t tot;
-    const uint32_t ex = block_excl_scan(np, sm.warp_tot, tot) + sm.carry;
+    const uint32_t ex = block_excl_scan(np, sm.warp_tot, &sm.total, tot) + sm.carry;
     if (valid) {
       pref[k] = ex;
       if (order_out) order_out[k] = order[k];
-      if (first) sm.first_pref[b] = ex;
-      atomicAdd(&sm.prods_tr[b], np);
-      atomicAdd(&sm.evs_tr[b], 1u);
+      if (first) { sm.first_pref[b] = ex; sm.first_k[b] = k; }
     }
     __syncthreads();
+    if (valid && last) {
+      sm.prods_tr[b] = ex + np - sm.first_pref[b];
+      sm.evs_tr[b] = k + 1 - sm.first_k[b];
+    }
     if (tid == 0) sm.carry += tot;
     __syncthreads();
   }
