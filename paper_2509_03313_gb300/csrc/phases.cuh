@@ -1197,31 +1197,9 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             else tj[u] = d.stid[ju[u]];
           }
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint32_t jj = ju[u];
-          bool pass = false;
-          float fx = 0.f, fy = 0.f, fz = 0.f, f2 = 0.f;
-          double rx1 = 0, ry1 = 0, rz1 = 0, d1sq = 0;
-          if (vu[u]) {
-            if constexpr (F32L) {
-              const float c2 = rc2[__float_as_uint(vj[u].w) & 7u];
-              fx = cxu[u] + (vj[u].x - vi.x); fy = cyu[u] + (vj[u].y - vi.y); fz = czu[u] + (vj[u].z - vi.z);
-              f2 = fx * fx + fy * fy + fz * fz;
-              pass = f2 < c2;
-            } else {
-              const double c2 = rc2[tj[u] & 7u];
-              if (c2 >= 0.0) {
-                // minimum image of x_j - x_i (Eq. 2); negated later into the reference's
-                // x_hi - x_lo orientation, which is exact for pairs inside the cutoff
-                rx1 = min_image(__dsub_rn(d.sx[jj], xi), tr.L, tr.halfL);
-                ry1 = min_image(__dsub_rn(d.sy[jj], yi), tr.L, tr.halfL);
-                rz1 = min_image(__dsub_rn(d.sz[jj], zi), tr.L, tr.halfL);
-                d1sq = sq3(rx1, ry1, rz1);
-                pass = d1sq < c2;
-              }
-            }
-          }
+        // enqueue the pairs inside the cutoff (queue pushes are warp-wide)
+        auto push = [&](bool pass, uint32_t jj, float fx, float fy, float fz, float f2, double rx1, double ry1,
+                        double rz1, double d1sq) {
           const uint32_t bal = __ballot_sync(0xffffffffu, pass);
           if (bal) {
             const uint32_t base = q.n;
@@ -1235,6 +1213,50 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             if (lane == 0) q.n = base + __popc(bal);
             __syncwarp();
             if (q.n > static_cast<uint32_t>(TpsQueue<F32L>::CAP) - 32u) tps_flush<F32L>(d, tb, q, vf, lane);
+          }
+        };
+        if constexpr (F32L) {
+          // the cutoff test for the four neighbours first; the separation is formed again,
+          // identically, for the rare pairs inside the cutoff
+          auto sep = [&](int u, float& fx, float& fy, float& fz) {
+            fx = cxu[u] + (vj[u].x - vi.x); fy = cyu[u] + (vj[u].y - vi.y); fz = czu[u] + (vj[u].z - vi.z);
+            return fx * fx + fy * fy + fz * fz;
+          };
+          bool pass[4];
+          bool any = false;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float fx, fy, fz;
+            pass[u] = vu[u] && sep(u, fx, fy, fz) < rc2[__float_as_uint(vj[u].w) & 7u];
+            any = any || pass[u];
+          }
+          if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              float fx = 0.f, fy = 0.f, fz = 0.f, f2 = 0.f;
+              if (pass[u]) f2 = sep(u, fx, fy, fz);
+              push(pass[u], ju[u], fx, fy, fz, f2, 0.0, 0.0, 0.0, 0.0);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t jj = ju[u];
+            bool pass = false;
+            double rx1 = 0, ry1 = 0, rz1 = 0, d1sq = 0;
+            if (vu[u]) {
+              const double c2 = rc2[tj[u] & 7u];
+              if (c2 >= 0.0) {
+                // minimum image of x_j - x_i (Eq. 2); negated later into the reference's
+                // x_hi - x_lo orientation, which is exact for pairs inside the cutoff
+                rx1 = min_image(__dsub_rn(d.sx[jj], xi), tr.L, tr.halfL);
+                ry1 = min_image(__dsub_rn(d.sy[jj], yi), tr.L, tr.halfL);
+                rz1 = min_image(__dsub_rn(d.sz[jj], zi), tr.L, tr.halfL);
+                d1sq = sq3(rx1, ry1, rz1);
+                pass = d1sq < c2;
+              }
+            }
+            push(pass, jj, 0.f, 0.f, 0.f, 0.f, rx1, ry1, rz1, d1sq);
           }
         }
       }

@@ -1,0 +1,123 @@
+"""The benchmark configurations at their full sizes, in the launch configuration the
+bench times (FP32-local single trains with the tuning the bench's autotuner picks on
+this workload, batched trains autotuned in the test, FP64 runs default):
+
+* 1e6-species track pulse: the first SBS steps in FP64 mode equal the FP64 reference
+  (every event, every per-step count, all positions); the whole trajectory in FP32-local
+  mode matches FP64-mode G-values within max(1 %, 3 sigma);
+* multi-pulse build-up (10 pulses of 293k species, 0.1 ms apart) and the 64-train
+  dose-rate sweep: exact conservation laws and internal consistency, which hold at any
+  size (the reference cannot run these within a test)."""
+import math
+
+import numpy as np
+import pytest
+
+from harness import assert_fp64_parity, cuda_available, gpu_run, oracle_run
+from paper_2509_03313_gb300 import chem, workloads as W
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not cuda_available(), reason="needs a CUDA GPU")]
+
+# steps per graph replay, hash limit, one thread per home species, one kernel per phase
+BENCH_TUNING = (8, 512, 0, chem.CHEM_LAUNCH_PHASES)
+
+
+def _conserved(wl, tally, injected_types):
+    """Charge, H and O (products' water counted through each reaction's water change)."""
+    c0 = np.bincount(injected_types, minlength=wl.n_types)[:7]
+    c = tally["counts"][:7]
+    ev = tally["events"][:len(wl.reactions)]
+    dw = np.array([r.water_delta for r in wl.reactions], dtype=np.int64)
+    water = int((ev * dw).sum())
+    assert int((c * W.CHARGE).sum()) == int((c0 * W.CHARGE).sum())
+    assert int((c * W.N_H).sum()) + 2 * water == int((c0 * W.N_H).sum())
+    assert int((c * W.N_O).sum()) + water == int((c0 * W.N_O).sum())
+    stoich = np.zeros((len(wl.reactions), 7), dtype=np.int64)
+    for r, rx in enumerate(wl.reactions):
+        stoich[r, rx.a] -= 1
+        stoich[r, rx.b] -= 1
+        for p in rx.products:
+            stoich[r, p] += 1
+    assert np.array_equal(c, c0 + ev @ stoich)
+
+
+def test_tracks_1e6_first_steps_fp64_equal_reference():
+    wl = W.single_pulse_tracks(10_000, n_species=1_000_000)
+    s = wl.schedule
+    t3 = s.dt_min * (1.0 + s.dt_growth + s.dt_growth ** 2)  # three SBS steps
+    o = oracle_run(wl, 10_000, t_end=t3)
+    g = gpu_run(wl, 10_000, t_end=t3, capacity=1_400_000)
+    assert len(o.step_log) == 3
+    assert_fp64_parity(g, o, wl.L)
+
+
+def test_tracks_1e6_fp32_local_g_values_match_fp64():
+    wl = W.single_pulse_tracks(10_000, n_species=1_000_000)
+    g = {chem.CHEM_FP32_LOCAL: [], chem.CHEM_FP64: []}
+    for prec in g:
+        for seed in range(4):
+            r = gpu_run(wl, 500 + seed, precision=prec, record=False, capacity=1_400_000,
+                        tuning=BENCH_TUNING if prec == chem.CHEM_FP32_LOCAL else None)
+            g[prec].append(r["tally"]["G"])
+            _conserved(wl, r["tally"], wl.pulses[0].types)
+    a, b = np.array(g[chem.CHEM_FP32_LOCAL]), np.array(g[chem.CHEM_FP64])
+    for t in (W.H2O2, W.OH, W.E_AQ):
+        diff = abs(a[:, t].mean() - b[:, t].mean())
+        sigma = math.sqrt(a[:, t].var(ddof=1) / len(a) + b[:, t].var(ddof=1) / len(b))
+        assert diff <= max(0.01 * b[:, t].mean(), 3 * sigma), (t, a[:, t], b[:, t])
+
+
+def test_multi_pulse_build_up_full_size():
+    wl = W.multi_pulse(3)
+    types = np.concatenate([p.types for p in wl.pulses])
+    n_total = types.size
+    stops = [k * 1e-4 + 2e-6 for k in range(len(wl.pulses))]  # just after each pulse
+    r = gpu_run(wl, 3, precision=chem.CHEM_FP32_LOCAL, record=False, capacity=n_total + 200_000,
+                t_stops=stops[:-1], t_end=wl.t_end, tuning=BENCH_TUNING)
+    live = [int(t["counts"][:7].sum()) for t in r["tallies"]]
+    # species are carried across the 0.1 ms intervals: every pulse adds to what is left
+    assert all(b > a for a, b in zip(live, live[1:])), live
+    assert r["tally"]["t"] == wl.t_end
+    _conserved(wl, r["tally"], types)
+    ids, st, _ = r["state"]
+    assert np.array_equal(np.bincount(st, minlength=7)[:7], r["tally"]["counts"][:7])
+    assert np.unique(ids).size == ids.size
+
+
+def test_batched_sweep_full_size():
+    import torch
+    wls = W.batched_sweep(64)
+    cfgs, keep = [], []
+    for b, wl in enumerate(wls):
+        s = wl.schedule
+        cap = int(wl.n_species * 1.3) + 4096
+        cfg, k = chem.make_config(wl.L, wl.D, wl.reactions, seed=900 + b, train_id=b,
+                                  precision=chem.CHEM_FP32_LOCAL, dt_min=s.dt_min, dt_max=s.dt_max,
+                                  dt_growth=s.dt_growth, reset_on_release=s.reset_on_release,
+                                  sbs_horizon=s.sbs_horizon, capacity_species=cap,
+                                  capacity_pending=max(wl.n_species, 1),
+                                  capacity_candidates=max(1 << 16, cap // 4),
+                                  stream=torch.cuda.current_stream().cuda_stream,
+                                  allocator=chem.torch_allocator(0))
+        cfgs.append(cfg)
+        keep.append(k)
+    ctx = chem.chem_batch_init(cfgs)
+    try:
+        for b, wl in enumerate(wls):
+            for p in wl.pulses:
+                chem.chem_batch_inject(ctx, b, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        chem.chem_autotune(ctx, 1500.0)
+        # run a step past every arrival (steps are at most 0.1 us) so that every injected
+        # species has been released
+        ends = [max(wl.t_end, max(float(p.t_arrival.max()) for p in wl.pulses)) + 1e-6 for wl in wls]
+        chem.chem_batch_run_until(ctx, ends)
+        for b, wl in enumerate(wls):
+            tal = chem.chem_batch_tally(ctx, b, 7, 9)
+            assert tal["t"] == ends[b]
+            _conserved(wl, tal, np.concatenate([p.types for p in wl.pulses]))
+            ids, st, _ = chem.chem_batch_get_state(ctx, b)
+            assert np.array_equal(np.bincount(st, minlength=7)[:7], tal["counts"][:7])
+            assert np.unique(ids).size == ids.size
+    finally:
+        chem.chem_destroy(ctx)
