@@ -49,6 +49,20 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def aggregate_over_ranks(species_steps, seconds, device=None):
+    """Whole-job species-steps (sum over ranks) and the slowest rank's time (max): the
+    ranks run independent replicas, so this is the only exchange."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(species_steps), float(seconds)
+    a = torch.tensor([float(species_steps)], dtype=torch.float64, device=device)
+    b = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    dist.all_reduce(b, op=dist.ReduceOp.MAX)
+    return float(a[0]), float(b[0])
+
+
 # ------------------------------------------------------------------- CPU reference arm
 def _oracle_worker(args):
     seed, n_species, n_steps = args
@@ -288,13 +302,7 @@ def run_gpu_arm(args):
                              h2d=h2d_per, d2h=8 * 7 + 8 * 7 + 8 * 9 + 16)
     # aggregate over ranks (replicas): sum of species-steps over the max time
     r = results["fp32l"]
-    ss_all, t_max = r["ss"], r["tot"]
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([float(r["ss"]), r["tot"]], dtype=torch.float64, device=dev)
-        a = tt.clone(); dist.all_reduce(a[0:1], op=dist.ReduceOp.SUM)
-        b = tt.clone(); dist.all_reduce(b[1:2], op=dist.ReduceOp.MAX)
-        ss_all, t_max = float(a[0]), float(b[1])
+    ss_all, t_max = aggregate_over_ranks(r["ss"], r["tot"], device=dev)
     if rank != 0:
         return 0
     value = ss_all / t_max

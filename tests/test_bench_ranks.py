@@ -1,0 +1,60 @@
+"""bench.py with N > 1 ranks runs independent replicas: the only exchange is the
+whole-job aggregation (species-steps summed, time = slowest rank). Tested with two
+gloo ranks on the CPU; the reference arm runs on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank, bench.aggregate_over_ranks(1000 * (rank + 1), 0.5 + rank)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_sum_work_and_take_slowest_time():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got == {0: (3000.0, 1.5), 1: (3000.0, 1.5)}
+
+
+def test_single_process_aggregation_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.aggregate_over_ranks(123, 4.5) == (123.0, 4.5)
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    args = type("A", (), {"ref_procs": 1, "species": 1000, "warmup": 3, "steps": 1, "gpus": 2})()
+    assert bench.run_reference_arm(args) == 0
+    assert capsys.readouterr().out == ""
