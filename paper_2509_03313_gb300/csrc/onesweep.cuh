@@ -128,7 +128,9 @@ static __device__ void onesweep_pass(const uint32_t* __restrict__ kin, const uin
       uint32_t e = block_exclusive_scan256(c, sm.warp_tot);
       if (tid < RADIX) sm.tile_off[tid] = e;
     }
-    // decoupled look-back, one thread per digit
+    // decoupled look-back, one thread per digit; the status words of LB_BATCH
+    // predecessors are read together, then consumed newest first until an inclusive
+    // prefix (done) or a word not yet published (read again from there)
     if (tid < RADIX) {
       uint32_t excl = 0;
       if (tile > 0) {
@@ -136,17 +138,26 @@ static __device__ void onesweep_pass(const uint32_t* __restrict__ kin, const uin
         int32_t t = static_cast<int32_t>(tile) - 1;
         bool timed_out = false;
         while (t >= 0) {
-          const unsigned long long wv =
-              ld_relaxed_u64(lookback + static_cast<size_t>(t) * RADIX + tid);
-          const uint32_t ep = static_cast<uint32_t>(wv >> 34);
-          const unsigned long long fl = (wv >> 32) & 3ull;
-          if (ep != (epoch & 0x3FFFFFFFu) || fl == 0ull) {
-            if (clock64() - t0 > SPIN_LIMIT_CYCLES) { timed_out = true; break; }
-            continue;
+          constexpr int LB_BATCH = 8;
+          unsigned long long wv[LB_BATCH];
+#pragma unroll
+          for (int q = 0; q < LB_BATCH; ++q)
+            wv[q] = (q <= t) ? ld_relaxed_u64(lookback + static_cast<size_t>(t - q) * RADIX + tid) : 0ull;
+          int used = 0;
+          bool done = false;
+#pragma unroll
+          for (int q = 0; q < LB_BATCH; ++q) {
+            if (done || used < q || q > t) continue;  // stop at the first gap
+            const uint32_t ep = static_cast<uint32_t>(wv[q] >> 34);
+            const unsigned long long fl = (wv[q] >> 32) & 3ull;
+            if (ep != (epoch & 0x3FFFFFFFu) || fl == 0ull) continue;
+            excl += static_cast<uint32_t>(wv[q]);
+            used = q + 1;
+            if (fl == LB_INC) done = true;
           }
-          excl += static_cast<uint32_t>(wv);
-          if (fl == LB_INC) break;
-          --t;
+          if (done) break;
+          t -= used;
+          if (used == 0 && clock64() - t0 > SPIN_LIMIT_CYCLES) { timed_out = true; break; }
         }
         if (timed_out) raise_status(g, CHEM_ETIMEOUT);
         st_relaxed_u64(lookback + static_cast<size_t>(tile) * RADIX + tid,
