@@ -44,6 +44,35 @@ PHASE_BYTES = {"diffuse": lambda s: 2 * s, "gather": lambda s: 2 * s, "search": 
                "sort": lambda s: 16, "release": lambda s: 0, "begin": lambda s: 0, "react": lambda s: 0}
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_tracks_1e6_fp32l.json")
+
+
+def sources_digest():
+    """SHA-256 over the CUDA sources and the C header, to tell whether a recorded ncu
+    measurement still describes the kernels that run."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2509_03313_gb300", "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh", ".h")))
+    for f in files + [os.path.join(ROOT, "include", "chem.h")]:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel):
+    """Mean DRAM bytes per launch of `kernel` from the committed ncu capture, or None when
+    there is none or the sources changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("sources_sha256") != sources_digest():
+        return None
+    return rec.get("dram_bytes_per_launch", {}).get(kernel)
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -317,6 +346,30 @@ def run_gpu_arm(args):
         # species-steps per pass launch: every pass moves every species once
         dom_bytes = PHASE_BYTES["sort"](sb) * r["ss"] * (phases["sort"]["launches"] / max(1, phases["diffuse"]["launches"]))
     achieved = dom_bytes / max(1e-12, phases[dom]["ms_total"] * 1e-3) / 1e9
+    tuned = list(r["tuned"]) if r["tuned"] is not None else None
+
+    def traffic_of(phase):
+        # DRAM bytes per launch from the committed capture of the same tuning and sources
+        kern = {"search": "k_search_tps", "diffuse": "k_diffuse"}.get(phase)
+        try:
+            with open(TRAFFIC_FILE) as fh:
+                rec_tuning = json.load(fh).get("tuning")
+        except (OSError, ValueError):
+            return None
+        return recorded_traffic(kern) if kern and rec_tuning == tuned else None
+
+    def roofline_of(phase):
+        ph = phases[phase]
+        if ph["ms_total"] <= 0.0:
+            return None
+        nb = PHASE_BYTES[phase](sb) * r["ss"]
+        if phase == "sort":
+            nb *= phases["sort"]["launches"] / max(1, phases["diffuse"]["launches"])
+        ach = nb / (ph["ms_total"] * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": phase, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic_of(phase), "peak_source": peak_src,
+                "algorithmic_bytes": f"{PHASE_BYTES[phase](sb)} B per live species per launch",
+                "avg_launch_ms": ph["ms_total"] / max(1, ph["launches"])}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * r["tot"] / len(r["times"]),
@@ -334,11 +387,8 @@ def run_gpu_arm(args):
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
                 "includes": "chem_reset + chem_inject_pulse (host arrays) + chem_run_until + chem_tally"},
         "gpu_launches": int(r["launches"]),
-        "roofline": None if not have_phases else {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": peak_src,
-                     "algorithmic_bytes": f"{PHASE_BYTES[dom](sb)} B per species per launch",
-                     "avg_launch_ms": phases[dom]["ms_total"] / n_launch},
+        "roofline": roofline_of(dom) if have_phases else None,
+        "roofline_diffuse": roofline_of("diffuse") if have_phases else None,
         "phases_ms": {p: round(v["ms_total"], 3) for p, v in phases.items()},
         "clocks": r["clocks"],
         "G_per_100eV_fp32l": {"H2O2": float(np.mean(r["G_H2O2"])), "OH": float(np.mean(r["G_OH"])),
