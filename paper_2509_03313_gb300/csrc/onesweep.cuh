@@ -7,7 +7,8 @@
 //    digit bases with a 256-wide exclusive scan;
 //  * tiles of 3840 keys are claimed in order through an atomic counter; inside a tile
 //    each warp ranks its keys with __match_any_sync (warp-private digit counters keep
-//    the pass stable), warps are combined through shared memory;
+//    the pass stable; the keys of a tile are nearly sorted, so few digits are distinct),
+//    warps are combined through shared memory;
 //  * decoupled look-back (Merrill & Garland 2016) chains the per-digit tile counts:
 //    a tile publishes its local count (AGGREGATE) at once, then walks back over its
 //    predecessors until it meets an INCLUSIVE prefix, and publishes its own inclusive

@@ -1608,7 +1608,7 @@ static __device__ bool phase_match_rounds_smem(const Dev& d, MatchSmem& sm, uint
 
 // Stable LSD radix sort of n (key, value) pairs by the whole CTA, 8-bit digits over the
 // 32 key bits. Each warp owns one contiguous chunk of the input and scatters it in order
-// (ranks among equal digits from __match_any_sync), so equal digits keep their order.
+// (ranks among equal digits from match_digit8), so equal digits keep their order.
 // A pass whose digit is the same for every key is skipped. The arrays may live in shared
 // or global memory. Returns 0 when the result is in (k0, v0), 1 when in (k1, v1).
 static __device__ int block_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t n,
@@ -1662,7 +1662,7 @@ static __device__ int block_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1,
         val = vin[i];
         dg = (key >> shift) & 255u;
       }
-      const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+      const uint32_t peers = match_digit8(dg, __ballot_sync(0xffffffffu, act));
       if (act) {
         const uint32_t dst = sm.dtot[dg] + sm.whist[w][dg] + __popc(peers & lt);
         kout[dst] = key;

@@ -232,6 +232,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// Lanes of the warp whose 8-bit digit equals this lane's, among the lanes in `active`:
+// eight ballots, a fixed cost whatever the number of distinct digits. Every lane of the
+// warp must call it.
+__device__ __forceinline__ uint32_t match_digit8(uint32_t digit, uint32_t active) {
+  uint32_t peers = active;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const uint32_t bit = (digit >> b) & 1u;
+    const uint32_t m = __ballot_sync(0xffffffffu, bit != 0u);
+    peers &= bit ? m : ~m;
+  }
+  return peers;
+}
+
 __device__ __forceinline__ unsigned long long u53(uint32_t hi, uint32_t lo) {
   return ((static_cast<unsigned long long>(hi) << 32) | lo) >> 11;
 }
