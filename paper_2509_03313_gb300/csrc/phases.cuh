@@ -1159,10 +1159,19 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
         }
       }
       // walk the ranges as one flattened list, four neighbours per iteration whose loads
-      // are in flight together; lanes of one cell stay in step (broadcast loads)
+      // are in flight together; lanes of one cell stay in step (broadcast loads). The
+      // home state is per lane and movable: a lane that has finished its own list takes
+      // the second half of another lane's current range (home data and all), so that
+      // lanes with few neighbours do not idle while one lane walks a dense cell.
       int ri = 0;
       uint32_t j = 0, je = 0;
       float cx = 0.f, cy = 0.f, cz = 0.f;
+      uint32_t hs = s, htid = tid_i;
+      int hb = b;
+      float4 hv = vi;
+      double hx = xi, hy = yi, hz = zi;
+      const T* hrow = rc2;
+      const Train* htr = &tr;
       auto open = [&](int r) {
         j = rs_l[32 * r];
         je = re_l[32 * r];
@@ -1174,6 +1183,54 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       };
       if (nr > 0) open(0);
       while (__any_sync(0xffffffffu, ri < nr)) {
+        const uint32_t idle = __ballot_sync(0xffffffffu, ri >= nr);
+        if (idle != 0u) {
+          const uint32_t rem = (ri < nr) ? je - j : 0u;
+          const uint32_t donors = __ballot_sync(0xffffffffu, rem >= 8u);
+          if (donors != 0u) {
+            const int n_pairs = min(__popc(idle), __popc(donors));
+            const bool take = ((idle >> lane) & 1u) && __popc(idle & lanemask_lt) < n_pairs;
+            const bool give = ((donors >> lane) & 1u) && __popc(donors & lanemask_lt) < n_pairs;
+            int src = lane;
+            if (take) {  // the k-th idle lane borrows from the k-th donor
+              uint32_t m = donors;
+              for (int qq = __popc(idle & lanemask_lt); qq > 0; --qq) m &= m - 1u;
+              src = __ffs(m) - 1;
+            }
+            const uint32_t mid = j + rem / 2u;
+            const uint32_t s2 = __shfl_sync(0xffffffffu, hs, src);
+            const uint32_t t2 = __shfl_sync(0xffffffffu, htid, src);
+            const int b2 = __shfl_sync(0xffffffffu, hb, src);
+            const uint32_t j2 = __shfl_sync(0xffffffffu, mid, src);
+            const uint32_t e2 = __shfl_sync(0xffffffffu, je, src);
+            const unsigned long long row2 =
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(hrow), src);
+            float4 v2;
+            float cx2, cy2, cz2;
+            double x2, y2, z2;
+            if constexpr (F32L) {
+              v2 = make_float4(__shfl_sync(0xffffffffu, hv.x, src), __shfl_sync(0xffffffffu, hv.y, src),
+                               __shfl_sync(0xffffffffu, hv.z, src), __shfl_sync(0xffffffffu, hv.w, src));
+              cx2 = __shfl_sync(0xffffffffu, cx, src);
+              cy2 = __shfl_sync(0xffffffffu, cy, src);
+              cz2 = __shfl_sync(0xffffffffu, cz, src);
+            } else {
+              x2 = __shfl_sync(0xffffffffu, hx, src);
+              y2 = __shfl_sync(0xffffffffu, hy, src);
+              z2 = __shfl_sync(0xffffffffu, hz, src);
+            }
+            if (give) je = mid;  // the donor keeps the first half
+            if (take) {
+              hs = s2; htid = t2; hb = b2;
+              hrow = reinterpret_cast<const T*>(row2);
+              htr = &d.trains[b2];
+              j = j2; je = e2;
+              ri = 0; nr = 1;  // one borrowed range; no further range is opened
+              if constexpr (F32L) { hv = v2; cx = cx2; cy = cy2; cz = cz2; }
+              else { hx = x2; hy = y2; hz = z2; }
+            }
+          }
+        }
         uint32_t ju[4];
         bool vu[4];
         float cxu[4], cyu[4], czu[4];
@@ -1205,7 +1262,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             const uint32_t base = q.n;
             if (pass) {
               const uint32_t pos = base + __popc(bal & lanemask_lt);
-              q.si[pos] = s; q.j[pos] = jj; q.tid_i[pos] = tid_i; q.b[pos] = static_cast<uint32_t>(b);
+              q.si[pos] = hs; q.j[pos] = jj; q.tid_i[pos] = htid; q.b[pos] = static_cast<uint32_t>(hb);
               if constexpr (F32L) { q.fx[pos] = fx; q.fy[pos] = fy; q.fz[pos] = fz; q.f2[pos] = f2; }
               else { q.rx[pos] = rx1; q.ry[pos] = ry1; q.rz[pos] = rz1; q.d2[pos] = d1sq; }
             }
@@ -1219,7 +1276,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           // the cutoff test for the four neighbours first; the separation is formed again,
           // identically, for the rare pairs inside the cutoff
           auto sep = [&](int u, float& fx, float& fy, float& fz) {
-            fx = cxu[u] + (vj[u].x - vi.x); fy = cyu[u] + (vj[u].y - vi.y); fz = czu[u] + (vj[u].z - vi.z);
+            fx = cxu[u] + (vj[u].x - hv.x); fy = cyu[u] + (vj[u].y - hv.y); fz = czu[u] + (vj[u].z - hv.z);
             return fx * fx + fy * fy + fz * fz;
           };
           bool pass[4];
@@ -1227,7 +1284,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             float fx, fy, fz;
-            pass[u] = vu[u] && sep(u, fx, fy, fz) < rc2[__float_as_uint(vj[u].w) & 7u];
+            pass[u] = vu[u] && sep(u, fx, fy, fz) < hrow[__float_as_uint(vj[u].w) & 7u];
             any = any || pass[u];
           }
           if (__any_sync(0xffffffffu, any)) {
@@ -1245,13 +1302,13 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             bool pass = false;
             double rx1 = 0, ry1 = 0, rz1 = 0, d1sq = 0;
             if (vu[u]) {
-              const double c2 = rc2[tj[u] & 7u];
+              const double c2 = hrow[tj[u] & 7u];
               if (c2 >= 0.0) {
                 // minimum image of x_j - x_i (Eq. 2); negated later into the reference's
                 // x_hi - x_lo orientation, which is exact for pairs inside the cutoff
-                rx1 = min_image(__dsub_rn(d.sx[jj], xi), tr.L, tr.halfL);
-                ry1 = min_image(__dsub_rn(d.sy[jj], yi), tr.L, tr.halfL);
-                rz1 = min_image(__dsub_rn(d.sz[jj], zi), tr.L, tr.halfL);
+                rx1 = min_image(__dsub_rn(d.sx[jj], hx), htr->L, htr->halfL);
+                ry1 = min_image(__dsub_rn(d.sy[jj], hy), htr->L, htr->halfL);
+                rz1 = min_image(__dsub_rn(d.sz[jj], hz), htr->L, htr->halfL);
                 d1sq = sq3(rx1, ry1, rz1);
                 pass = d1sq < c2;
               }
