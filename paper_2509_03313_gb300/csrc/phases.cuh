@@ -1129,8 +1129,9 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       rc2 = row;
     }
     if (__any_sync(0xffffffffu, home)) {
-      // this lane's non-empty ranges: the own cell's later slots, then the occupied
-      // forward cells (13 bit tests in the L2-resident bitmap, then their 16-byte entries)
+      // this lane's non-empty ranges: the own cell's later slots, then the forward cells
+      // within reach that are occupied (bit test in the L2-resident bitmap, then their
+      // 16-byte entries)
       uint32_t* rs_l = &sm.rs[wib][0][lane];
       uint32_t* re_l = &sm.re[wib][0][lane];
       uint8_t* rk_l = &sm.rk[wib][0][lane];
@@ -1141,10 +1142,32 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
         cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
         const uint32_t own_end = static_cast<uint32_t>(d.cell_info[cell].y);
         if (s + 1u < own_end) { rs_l[0] = s + 1u; re_l[0] = own_end; rk_l[0] = 0; nr = 1; }
+        // a forward cell whose nearest point is farther from the home than the largest
+        // cutoff of the home's type holds no partner and is not looked up (the gaps are
+        // taken 1e-5 of a cell short, which covers every rounding of the offsets)
+        const float hcell = tr.hf, eps = 1e-5f * tr.hf;
+        float ofx, ofy, ofz;
+        if constexpr (F32L) {
+          ofx = vi.x; ofy = vi.y; ofz = vi.z;
+        } else {
+          ofx = static_cast<float>(__dsub_rn(__dadd_rn(xi, tr.halfL), __dmul_rn(static_cast<double>(ix), tr.h)));
+          ofy = static_cast<float>(__dsub_rn(__dadd_rn(yi, tr.halfL), __dmul_rn(static_cast<double>(iy), tr.h)));
+          ofz = static_cast<float>(__dsub_rn(__dadd_rn(zi, tr.halfL), __dmul_rn(static_cast<double>(iz), tr.h)));
+        }
+        float rcmax2 = -1.f;
+#pragma unroll
+        for (int t = 0; t < MAXT; ++t) rcmax2 = fmaxf(rcmax2, static_cast<float>(rc2[t]));
+        rcmax2 *= 1.0001f;
+        auto gap = [&](int o, float of) {
+          const float g = o > 0 ? hcell - of : (o < 0 ? of : 0.f);
+          return fmaxf(g - eps, 0.f);
+        };
 #pragma unroll
         for (int k = 1; k < N_FWD; ++k) {
           int ox, oy, oz;
           fwd_offset(k, ox, oy, oz);
+          const float gx = gap(ox, ofx), gy = gap(oy, ofy), gz = gap(oz, ofz);
+          if (gx * gx + gy * gy + gz * gz > rcmax2) continue;
           const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, ox, n), step_cell(iy, oy, n),
                                                          step_cell(iz, oz, n), tr.cb);
           if ((d.occ[nc >> 5] >> (nc & 31u)) & 1u) {
