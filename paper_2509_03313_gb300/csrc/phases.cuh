@@ -233,6 +233,16 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     }
   }
   __syncthreads();
+  // the same cutoffs per type pair (the pair search's lookup table)
+  for (uint32_t w = tid; w < d.n_trains * (MAXT * MAXT); w += nt) {
+    const uint32_t b = w / (MAXT * MAXT);
+    const int q = static_cast<int>(w % (MAXT * MAXT));
+    if (sb.dt[b] <= 0.0) continue;
+    Train& tr = d.trains[b];
+    const int r = tb.pair_rxn[q / MAXT][q % MAXT];
+    tr.rc2_tt[q] = r >= 0 ? tr.rc2[r] : -1.0;
+    tr.rc2f_tt[q] = r >= 0 ? tr.rc2f[r] : -1.f;
+  }
   for (uint32_t b = tid; b < d.n_trains; b += nt) {
     if (sb.dt[b] <= 0.0) continue;
     Train& tr = d.trains[b];
@@ -976,7 +986,7 @@ struct TpsQueue;
 
 template <>
 struct TpsQueue<true> {
-  static constexpr int CAP = 96;
+  static constexpr int CAP = 64;
   uint32_t si[CAP], j[CAP], tid_i[CAP], b[CAP];
   float fx[CAP], fy[CAP], fz[CAP], f2[CAP];
   uint32_t n;
@@ -995,7 +1005,6 @@ struct TpsSmem {
   using T = typename std::conditional<F32L, float, double>::type;
   T ct[W][MAXT * MAXT];       // per warp: squared cutoffs of one train (-1: no reaction) ...
   int ct_b[W];                // ... that train
-  T rc2[W][32][MAXT + 1];     // per lane rows, for the rare chunk spanning several trains
   uint32_t rs[W][N_FWD][32];  // per lane: its non-empty neighbour ranges [rs, re) ...
   uint32_t re[W][N_FWD][32];
   uint8_t rk[W][N_FWD][32];   // ... and their half-shell offsets
@@ -1101,32 +1110,17 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       if (sm.ct_b[wib] != b0) {
         const Train& t0 = d.trains[b0];
         for (int qq = lane; qq < MAXT * MAXT; qq += 32) {
-          const int r = tb.pair_rxn[qq / MAXT][qq % MAXT];
-          T v = static_cast<T>(-1);
-          if (r >= 0) {
-            if constexpr (F32L) v = t0.rc2f[r];
-            else v = t0.rc2[r];
-          }
-          sm.ct[wib][qq] = v;
+          if constexpr (F32L) sm.ct[wib][qq] = t0.rc2f_tt[qq];
+          else sm.ct[wib][qq] = t0.rc2_tt[qq];
         }
         __syncwarp();
         if (lane == 0) sm.ct_b[wib] = b0;
         __syncwarp();
       }
       rc2 = &sm.ct[wib][ti * MAXT];
-    } else {
-      T* row = sm.rc2[wib][lane];
-#pragma unroll
-      for (int t = 0; t < MAXT; ++t) {
-        const int r = tb.pair_rxn[ti][t];
-        T v = static_cast<T>(-1);
-        if (r >= 0) {
-          if constexpr (F32L) v = tr.rc2f[r];
-          else v = tr.rc2[r];
-        }
-        row[t] = v;
-      }
-      rc2 = row;
+    } else {  // the rare chunk spanning several trains reads its rows from global memory
+      if constexpr (F32L) rc2 = &tr.rc2f_tt[ti * MAXT];
+      else rc2 = &tr.rc2_tt[ti * MAXT];
     }
     if (__any_sync(0xffffffffu, home)) {
       // this lane's non-empty ranges: the own cell's later slots, then the forward cells

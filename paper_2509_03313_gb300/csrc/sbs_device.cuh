@@ -87,6 +87,8 @@ struct Train {
   float hf, inv_hf;
   double rc2[MAXR];
   float rc2f[MAXR];
+  double rc2_tt[MAXT * MAXT];  // squared cutoff of each type pair (-1: no reaction)
+  float rc2f_tt[MAXT * MAXT];
   double sig[MAXT];        // sqrt(2 D dt) per type
   float sigf[MAXT];
   double ddt[MAXR];        // D_AB dt per reaction (bridge denominator)
