@@ -1356,6 +1356,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
 //  5. phase_end_step (one CTA): FP64 clock, step counter, dt growth, step records.
 struct MatchSmem {
   uint32_t n_alive, n_next;
+  uint32_t n_won, won_base;
 };
 
 // Events ordered in shared memory by the one-CTA react kernel (4 arrays of this size).
@@ -1619,18 +1620,22 @@ static __device__ bool phase_match_rounds_smem(const Dev& d, MatchSmem& sm, uint
     if (e & 1u) hi[e >> 1] = hval[h]; else lo[e >> 1] = hval[h];
   }
   __syncthreads();
+  // winners are listed in shared memory (the hash values are no longer needed) and
+  // recorded as events after the last round with one reservation
+  uint32_t* won = hval;
+  if (tid == 0) sm.n_won = 0;
+  for (uint32_t a = tid; a < n_c; a += nt) {
+    const uint32_t i = alive[a];
+    bd[lo[i]] = ~0ull; bd[hi[i]] = ~0ull;
+    bp[lo[i]] = ~0ull; bp[hi[i]] = ~0ull;
+  }
+  __syncthreads();
   for (uint32_t round = 0; sm.n_alive > 0; ++round) {
     if (round > n_c) {
       if (tid == 0) raise_status(d.g, CHEM_ESTATE);
       break;
     }
     const uint32_t na = sm.n_alive;
-    for (uint32_t a = tid; a < na; a += nt) {
-      const uint32_t i = alive[a];
-      bd[lo[i]] = ~0ull; bd[hi[i]] = ~0ull;
-      bp[lo[i]] = ~0ull; bp[hi[i]] = ~0ull;
-    }
-    __syncthreads();
     for (uint32_t a = tid; a < na; a += nt) {
       const uint32_t i = alive[a];
       atomicMin(&bd[lo[i]], kd[i]);
@@ -1651,15 +1656,17 @@ static __device__ bool phase_match_rounds_smem(const Dev& d, MatchSmem& sm, uint
         i = alive[a];
         win = bd[lo[i]] == kd[i] && bp[lo[i]] == kp[i] && bd[hi[i]] == kd[i] && bp[hi[i]] == kp[i];
       }
-      const uint32_t e = warp_reserve(&d.g->n_events, win);
+      const uint32_t q = warp_reserve(&sm.n_won, win);
       if (win) {
         ldead[lo[i]] = 1u;
         ldead[hi[i]] = 1u;
-        commit_event(d, cix[i], d.cand[cix[i]], e);
+        won[q] = i;
       }
     }
     if (tid == 0) sm.n_next = 0;
     __syncthreads();
+    // survivors (both species still free) move to the next round with their slots'
+    // minima reset; nothing reads the minima in this pass
     for (uint32_t a0 = 0; a0 < na; a0 += nt) {
       const uint32_t a = a0 + tid;
       bool keep = false;
@@ -1669,12 +1676,87 @@ static __device__ bool phase_match_rounds_smem(const Dev& d, MatchSmem& sm, uint
         keep = !ldead[lo[i]] && !ldead[hi[i]];
       }
       const uint32_t q = warp_reserve(&sm.n_next, keep);
-      if (keep) nxt[q] = i;
+      if (keep) {
+        nxt[q] = i;
+        bd[lo[i]] = ~0ull; bd[hi[i]] = ~0ull;
+        bp[lo[i]] = ~0ull; bp[hi[i]] = ~0ull;
+      }
     }
     __syncthreads();
     if (tid == 0) sm.n_alive = sm.n_next;
     uint32_t* t = alive; alive = nxt; nxt = t;
     __syncthreads();
+  }
+  if (tid == 0) sm.won_base = atomicAdd(&d.g->n_events, sm.n_won);
+  __syncthreads();
+  for (uint32_t q = tid; q < sm.n_won; q += nt) {
+    const uint32_t c = cix[won[q]];
+    commit_event(d, c, d.cand[c], sm.won_base + q);
+  }
+  __syncthreads();
+  return true;
+}
+
+// Sort of n (key, value) pairs by the whole CTA, in shared memory (keys are distinct
+// here; equal keys would be ordered by value): one counting pass over 2048 buckets of
+// the key range (bucket = (key - min) >> shift), then each key's rank inside its bucket
+// by comparison with the bucket's other keys (buckets hold a handful of keys for the
+// id-like keys sorted here). The result is in (k0, v0); (k1, v1) is scratch. Returns
+// false, with nothing changed, when a bucket holds more than 64 keys (clustered keys)
+// or the CTA is not 1024 threads; the caller then uses block_sort_pairs.
+constexpr int BUCKETS = 2048;
+static __device__ bool block_bucket_sort(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t n,
+                                         BlockSortSmem& sm, ScanSmem& ss) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, w = tid >> 5;
+  if (2 * nt != BUCKETS) return false;     // two buckets per thread in the scan below
+  uint32_t* cnt = &sm.whist[0][0];         // BUCKETS counts, then exclusive starts
+  uint32_t* cur = cnt + BUCKETS;           // scatter cursors, then bucket ends
+  uint32_t* red = cnt + 2 * BUCKETS;       // per-warp min / max / largest bucket
+  // key range
+  uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+  for (uint32_t i = tid; i < n; i += nt) { mn = min(mn, k0[i]); mx = max(mx, k0[i]); }
+  mn = __reduce_min_sync(0xffffffffu, mn);
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane == 0) { red[w] = mn; red[32 + w] = mx; }
+  for (int i = tid; i < BUCKETS; i += nt) cnt[i] = 0u;
+  __syncthreads();
+  mn = 0xFFFFFFFFu; mx = 0u;
+  for (int q = 0; q < (nt >> 5); ++q) { mn = min(mn, red[q]); mx = max(mx, red[32 + q]); }
+  const uint32_t range = n ? mx - mn : 0u;
+  const int bits = range ? 32 - __clz(range) : 0;
+  const int shift = bits > 11 ? bits - 11 : 0;
+  for (uint32_t i = tid; i < n; i += nt) atomicAdd(&cnt[(k0[i] - mn) >> shift], 1u);
+  __syncthreads();
+  // largest bucket (clustered keys would make the in-bucket ranks quadratic)
+  uint32_t big = 0u;
+  for (int i = tid; i < BUCKETS; i += nt) big = max(big, cnt[i]);
+  big = __reduce_max_sync(0xffffffffu, big);
+  if (lane == 0) red[64 + w] = big;
+  // exclusive starts: each thread scans two consecutive buckets
+  const uint32_t c0 = cnt[2 * tid], c1 = cnt[2 * tid + 1];
+  uint32_t tot;
+  const uint32_t ex = block_excl_scan(c0 + c1, ss.warp_tot, &ss.total, tot);
+  big = 0u;
+  for (int q = 0; q < (nt >> 5); ++q) big = max(big, red[64 + q]);
+  if (big > 64u) return false;  // uniform: every thread read the same values
+  cnt[2 * tid] = ex; cnt[2 * tid + 1] = ex + c0;
+  cur[2 * tid] = ex; cur[2 * tid + 1] = ex + c0;
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += nt) {
+    const uint32_t b = (k0[i] - mn) >> shift;
+    const uint32_t p = atomicAdd(&cur[b], 1u);
+    k1[p] = k0[i];
+    v1[p] = v0[i];
+  }
+  __syncthreads();
+  for (uint32_t p = tid; p < n; p += nt) {
+    const uint32_t k = k1[p], v = v1[p];
+    const uint32_t b = (k - mn) >> shift;
+    const uint32_t lo = cnt[b], hi = cur[b];
+    uint32_t r = 0;
+    for (uint32_t q = lo; q < hi; ++q) r += (k1[q] < k || (k1[q] == k && v1[q] < v)) ? 1u : 0u;
+    k0[lo + r] = k;
+    v0[lo + r] = v;
   }
   __syncthreads();
   return true;
@@ -1764,43 +1846,40 @@ static __device__ void products_prefix(const Dev& d, ScanSmem& sm, const uint32_
   for (uint32_t b = tid; b < d.n_trains; b += nt) {
     sm.first_pref[b] = 0; sm.first_k[b] = 0; sm.prods_tr[b] = 0; sm.evs_tr[b] = 0;
   }
-  if (tid == 0) sm.carry = 0;
+  // each thread takes one contiguous segment of the ordered events: its product count,
+  // one block-wide scan of the segment sums, then the per-event prefixes in the segment
+  const uint32_t seg = (E + static_cast<uint32_t>(nt) - 1u) / static_cast<uint32_t>(nt);
+  const uint32_t k0 = min(E, static_cast<uint32_t>(tid) * seg), k1 = min(E, k0 + seg);
+  uint32_t local = 0;
+  for (uint32_t k = k0; k < k1; ++k) local += order[k] >> 24;
+  uint32_t total;
+  uint32_t ex = block_excl_scan(local, sm.warp_tot, &sm.total, total);  // includes barriers
+  // train boundaries: a train's counts are differences at its last event (events are in
+  // train order)
+  for (uint32_t k = k0; k < k1; ++k) {
+    const uint32_t v = order[k];
+    pref[k] = ex;
+    if (order_out) order_out[k] = v;
+    const uint32_t b = d.train_bits ? okeys[k] >> tshift : 0u;
+    if (k == 0 || (d.train_bits && (okeys[k - 1] >> tshift) != b)) { sm.first_pref[b] = ex; sm.first_k[b] = k; }
+    ex += v >> 24;
+  }
   __syncthreads();
-  for (uint32_t t0 = 0; t0 < E; t0 += nt) {
-    const uint32_t k = t0 + tid;
-    const bool valid = k < E;
-    uint32_t b = 0, np = 0;
-    bool first = false, last = false;
-    if (valid) {
-      // train from the event key's top bits, product count from the value's; events are
-      // in train order, so a train's counts are differences at its last event
-      b = d.train_bits ? okeys[k] >> tshift : 0u;
-      np = order[k] >> 24;
-      first = (k == 0) || (d.train_bits ? (okeys[k - 1] >> tshift) != b : false);
-      last = (k + 1 == E) || (d.train_bits ? (okeys[k + 1] >> tshift) != b : false);
-    }
-    uint32_t tot;
-    const uint32_t ex = block_excl_scan(np, sm.warp_tot, &sm.total, tot) + sm.carry;
-    if (valid) {
-      pref[k] = ex;
-      if (order_out) order_out[k] = order[k];
-      if (first) { sm.first_pref[b] = ex; sm.first_k[b] = k; }
-    }
-    __syncthreads();
-    if (valid && last) {
-      sm.prods_tr[b] = ex + np - sm.first_pref[b];
+  for (uint32_t k = k0; k < k1; ++k) {
+    const uint32_t b = d.train_bits ? okeys[k] >> tshift : 0u;
+    if (k + 1 == E || (d.train_bits && (okeys[k + 1] >> tshift) != b)) {
+      sm.prods_tr[b] = pref[k] + (order[k] >> 24) - sm.first_pref[b];
       sm.evs_tr[b] = k + 1 - sm.first_k[b];
     }
-    if (tid == 0) sm.carry += tot;
-    __syncthreads();
   }
+  __syncthreads();
   for (uint32_t b = tid; b < d.n_trains; b += nt) {
     Train& tr = d.trains[b];
     tr.pref0 = sm.first_pref[b];
     tr.prods_step = sm.prods_tr[b];
     tr.n_events_step = sm.evs_tr[b];
   }
-  if (tid == 0 && ok) d.g->n_products = sm.carry;
+  if (tid == 0 && ok) d.g->n_products = total;
   __syncthreads();
 }
 
@@ -1829,7 +1908,8 @@ static __device__ void phase_react_serial(const Dev& d, SerialSmem& sm, uint32_t
     uint32_t* v1 = sbuf + 3 * EV_SMEM_CAP;
     for (uint32_t i = tid; i < E; i += nt) { k0[i] = d.ev_k0[i]; v0[i] = d.ev_v0[i]; }
     __syncthreads();
-    const int p = block_sort_pairs(k0, v0, k1, v1, E, sm.sort);
+    const int p = block_bucket_sort(k0, v0, k1, v1, E, sm.sort, sm.scan) ? 0
+                                                                           : block_sort_pairs(k0, v0, k1, v1, E, sm.sort);
     okeys = p ? k1 : k0;
     order = p ? v1 : v0;
     order_out = d.ev_v0;
