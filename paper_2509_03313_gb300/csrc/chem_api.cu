@@ -657,7 +657,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     return fail(ctx, CHEM_EINVAL, "too many hash cells");
   }
   d.precision = ctx->precision;
-  d.max_tiles = static_cast<uint32_t>(cap / SORT_TILE + 2);
+  d.max_tiles = static_cast<uint32_t>(cap / SORT_TILE_MIN + 2);
   bool ok = true;
   auto A = [&](size_t bytes) {
     void* p = dev_alloc(ctx, bytes);

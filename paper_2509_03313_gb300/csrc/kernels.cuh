@@ -17,7 +17,7 @@ union PhaseSmem {
   TpsSmem<true, 8> tps32;
   TpsSmem<false, 8> tps64;
   uint32_t hist[MAX_PASSES][RADIX];
-  SortSmem sort;
+  SortSmemP sort;
 };
 
 // Grid-wide barrier of the persistent kernel. The wait is bounded: past the limit the
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_products(const __grid_constant__ Dev d)
 }
 
 template <bool F32L>
-__global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Dev d, int n_steps) {
+__global__ void __launch_bounds__(PERSIST_THREADS) k_persistent(const __grid_constant__ Dev d, int n_steps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PhaseSmem& sm = *reinterpret_cast<PhaseSmem*>(smem_raw);
   if (blockIdx.x == 0) phase_begin(d, sm.begin);
@@ -165,7 +165,7 @@ template <bool F32L>
 cudaError_t enqueue_persistent(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(lc.persistent_blocks);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(PERSIST_THREADS);
   cfg.dynamicSmemBytes = sizeof(PhaseSmem);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -181,7 +181,7 @@ cudaError_t persistent_occupancy(int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k_persistent<F32L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sizeof(PhaseSmem)));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_persistent<F32L>, 256,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_persistent<F32L>, PERSIST_THREADS,
                                                        sizeof(PhaseSmem));
 }
 

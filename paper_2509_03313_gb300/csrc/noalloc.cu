@@ -25,7 +25,7 @@ constexpr uint32_t NA_MAX_CAND = CHEM_NOALLOC_MAX_SPECIES;
 constexpr uint32_t NA_MAX_EVENTS = CHEM_NOALLOC_MAX_SPECIES / 2;
 constexpr int NA_CELLS_AXIS = 32;
 constexpr uint32_t NA_CELLS = NA_CELLS_AXIS * NA_CELLS_AXIS * NA_CELLS_AXIS;
-constexpr uint32_t NA_TILES = NA_MAX_SPECIES / SORT_TILE + 2;
+constexpr uint32_t NA_TILES = NA_MAX_SPECIES / SORT_TILE_MIN + 2;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 

@@ -21,17 +21,22 @@
 
 namespace chem {
 
-struct SortSmem {
-  uint32_t wcnt[SORT_THREADS / 32][RADIX];
+// NT threads per CTA, tiles of NT * SORT_ITEMS keys.
+template <int NT>
+struct SortSmemT {
+  static constexpr int TILE = NT * SORT_ITEMS;
+  uint32_t wcnt[NT / 32][RADIX];
   uint32_t gbase[RADIX];      // global exclusive digit base
   uint32_t tile_cnt[RADIX];
   uint32_t tile_off[RADIX];   // exclusive digit offsets inside the tile
   uint32_t tile_out[RADIX];   // gbase + look-back prefix
-  uint32_t k[SORT_TILE];
-  uint32_t v[SORT_TILE];
+  uint32_t k[TILE];
+  uint32_t v[TILE];
   uint32_t tile;
-  uint32_t warp_tot[SORT_THREADS / 32];
+  uint32_t warp_tot[NT / 32];
 };
+using SortSmem = SortSmemT<SORT_THREADS>;      // the per-pass kernel
+using SortSmemP = SortSmemT<PERSIST_THREADS>;  // the persistent kernel
 
 constexpr unsigned long long LB_AGG = 1ull, LB_INC = 2ull;
 
@@ -58,13 +63,15 @@ __device__ __forceinline__ uint32_t block_exclusive_scan256(uint32_t v, uint32_t
 }
 
 // One pass over n keys by digit (key >> shift) & 255. ghist = this digit's histogram
-// over all n keys; vin == nullptr means value = input index. Must be called by all
-// SORT_THREADS threads of every CTA.
-static __device__ void onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+// over all n keys; vin == nullptr means value = input index. Must be called by all NT
+// threads of every CTA.
+template <int NT>
+__device__ void onesweep_pass(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
                               int shift, const uint32_t* ghist, uint32_t* tile_ctr,
                               unsigned long long* lookback, uint32_t epoch, Global* g,
-                              SortSmem& sm) {
+                              SortSmemT<NT>& sm) {
+  constexpr int SORT_TILE = SortSmemT<NT>::TILE;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
   {
@@ -114,7 +121,7 @@ static __device__ void onesweep_pass(const uint32_t* __restrict__ kin, const uin
     if (tid < RADIX) {
       uint32_t s = 0;
 #pragma unroll
-      for (int ww = 0; ww < SORT_THREADS / 32; ++ww) {
+      for (int ww = 0; ww < NT / 32; ++ww) {
         const uint32_t c = sm.wcnt[ww][tid];
         sm.wcnt[ww][tid] = s;
         s += c;
@@ -179,7 +186,7 @@ static __device__ void onesweep_pass(const uint32_t* __restrict__ kin, const uin
       }
     }
     __syncthreads();
-    for (uint32_t p = tid; p < tile_n; p += SORT_THREADS) {
+    for (uint32_t p = tid; p < tile_n; p += NT) {
       const uint32_t k = sm.k[p];
       const uint32_t d = (k >> shift) & 255u;
       const uint32_t o = sm.tile_out[d] + (p - sm.tile_off[d]);

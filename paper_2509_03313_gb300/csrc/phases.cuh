@@ -511,7 +511,8 @@ __device__ __forceinline__ bool block_status_ok(const Dev& d) {
   return __syncthreads_and(threadIdx.x == 0 ? (status_of(d) == 0) : 1) != 0;
 }
 
-static __device__ void phase_sort_pass(const Dev& d, int pass, SortSmem& sm) {
+template <int NT>
+__device__ void phase_sort_pass(const Dev& d, int pass, SortSmemT<NT>& sm) {
   if (!block_status_ok(d)) return;
   const uint32_t n = d.g->n_total;
   int before = 0;

@@ -29,9 +29,11 @@ constexpr int MAXR = CHEM_MAX_RXN;
 constexpr int MAX_TRAINS = 256;
 constexpr int RADIX = 256;
 constexpr int MAX_PASSES = 4;
-constexpr int SORT_THREADS = 256;
+constexpr int SORT_THREADS = 512;    // threads of the per-pass sort kernel
+constexpr int PERSIST_THREADS = 256; // threads of the persistent step kernel
 constexpr int SORT_ITEMS = 15;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 3840 keys per tile
+// the smallest sort tile (persistent kernel): sizes the look-back buffer
+constexpr int SORT_TILE_MIN = PERSIST_THREADS * SORT_ITEMS;
 constexpr int REACT_THREADS = 1024;
 constexpr int ITEM_HOME = 64;   // home species per pair-search work item (one cell)
 constexpr int N_FWD = 14;       // own cell + 13 forward neighbour cells (half shell)
