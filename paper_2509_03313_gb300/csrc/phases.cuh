@@ -91,12 +91,13 @@ __device__ __forceinline__ void gauss3_f32(uint32_t id, uint32_t step, uint32_t 
   const float u2 = static_cast<float>(a.y >> 8) * TWO_POW_M24F;
   const float u3 = static_cast<float>((a.z >> 8) + 1u) * TWO_POW_M24F;
   const float u4 = static_cast<float>(a.w >> 8) * TWO_POW_M24F;
-  const float r = sqrtf(-2.0f * logf(u1));
+  // hardware approximations (a few ulp): the FP32-local normals need no more
+  const float r = sqrtf(-2.0f * __logf(u1));
   float s, c;
-  sincospif(2.0f * u2, &s, &c);
+  __sincosf(6.2831853f * u2, &s, &c);
   g0 = r * c;
   g1 = r * s;
-  g2 = sqrtf(-2.0f * logf(u3)) * cospif(2.0f * u4);
+  g2 = sqrtf(-2.0f * __logf(u3)) * __cosf(6.2831853f * u4);
 }
 
 // Uniform in [0, 1) for the pair (id_lo, id_hi) at `step` (counter tag 2).
