@@ -58,3 +58,51 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
     args = type("A", (), {"ref_procs": 1, "species": 1000, "warmup": 3, "steps": 1, "gpus": 2})()
     assert bench.run_reference_arm(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_shard_trains_covers_every_train_once_and_balances():
+    sys.path.insert(0, ROOT)
+    import bench
+    import numpy as np
+    sizes = list(np.geomspace(1e4, 2e6, 64).astype(int))
+    for world in (1, 2, 3, 8):
+        parts = bench.shard_trains(sizes, world)
+        flat = sorted(b for p in parts for b in p)
+        assert flat == list(range(64))
+        loads = [sum(sizes[b] for b in p) for p in parts]
+        assert max(loads) - min(loads) <= max(sizes)
+
+
+def _batched_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import numpy as np
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        counts = np.zeros((4, 7), dtype=np.int64)
+        for b in bench.shard_trains([10, 20, 30, 40], world)[rank]:
+            counts[b] = b + 1
+        ss, t, c = bench.gather_batched(100 * (rank + 1), 2.0 + rank, counts)
+        q.put((rank, ss, t, c.tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_gather_the_sharded_sweep():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batched_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ss, t, c in got:
+        assert ss == 300.0 and t == 3.0
+        assert c == [[b + 1] * 7 for b in range(4)]
