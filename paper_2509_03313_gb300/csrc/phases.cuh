@@ -1205,7 +1205,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
         const uint32_t idle = __ballot_sync(0xffffffffu, ri >= nr);
         if (idle != 0u) {
           const uint32_t rem = (ri < nr) ? je - j : 0u;
-          const uint32_t donors = __ballot_sync(0xffffffffu, rem >= 8u);
+          const uint32_t donors = __ballot_sync(0xffffffffu, rem >= 4u);
           if (donors != 0u) {
             const int n_pairs = min(__popc(idle), __popc(donors));
             const bool take = ((idle >> lane) & 1u) && __popc(idle & lanemask_lt) < n_pairs;
