@@ -671,6 +671,9 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     d.tz = static_cast<double*>(A(cap * 8)); d.ttid = static_cast<uint32_t*>(A(cap * 4));
     d.tdx = static_cast<double*>(A(cap * 8)); d.tdy = static_cast<double*>(A(cap * 8));
     d.tdz = static_cast<double*>(A(cap * 8));
+    // FP32 cell offsets of the same species for the pair search's prefilter
+    d.s4 = static_cast<float4*>(A(cap * 16));
+    d.t4 = static_cast<float4*>(A(cap * 16));
   } else {
     d.s4 = static_cast<float4*>(A(cap * 16));
     d.t4 = static_cast<float4*>(A(cap * 16));

@@ -277,6 +277,18 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     tr.hf = static_cast<float>(h);
     tr.inv_hf = static_cast<float>(inv_h);
   }
+  __syncthreads();
+  // FP32 cutoffs widened past any error of FP32 cell offsets (a few 1e-7 of a cell per
+  // component): a pair the FP32 test rejects is outside the FP64 cutoff
+  for (uint32_t w = tid; w < d.n_trains * (MAXT * MAXT); w += nt) {
+    const uint32_t b = w / (MAXT * MAXT);
+    const int q = static_cast<int>(w % (MAXT * MAXT));
+    if (sb.dt[b] <= 0.0) continue;
+    Train& tr = d.trains[b];
+    const float rc = tr.rc2f_tt[q] >= 0.f ? sqrtf(tr.rc2f_tt[q]) : -1.f;
+    const float rw = rc * 1.00001f + 2e-6f * tr.hf;
+    tr.rc2w_tt[q] = rc >= 0.f ? rw * rw * 1.00001f : -1.f;
+  }
 
   if (tid == 0) {
     Global* g = d.g;
@@ -434,6 +446,13 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
           const int iy = cell_index(y, tr.halfL, tr.inv_h, n);
           const int iz = cell_index(z, tr.halfL, tr.inv_h, n);
           key = tr.cell_base + cell_encode(ix, iy, iz, tr.cb);
+          if (d.t4) {  // FP32 offsets from the cell's corner for the pair search's prefilter
+            d.t4[s] = make_float4(
+                static_cast<float>(__dsub_rn(__dadd_rn(x, tr.halfL), __dmul_rn(static_cast<double>(ix), tr.h))),
+                static_cast<float>(__dsub_rn(__dadd_rn(y, tr.halfL), __dmul_rn(static_cast<double>(iy), tr.h))),
+                static_cast<float>(__dsub_rn(__dadd_rn(z, tr.halfL), __dmul_rn(static_cast<double>(iz), tr.h))),
+                __uint_as_float(tid));
+          }
         } else {
           const uint32_t ftid = __float_as_uint(v.w);
           const uint32_t ty = tid_type(ftid);
@@ -555,6 +574,7 @@ __device__ void phase_gather(const Dev& d) {
       d.s4[s] = d.t4[i];
     } else {
       d.sx[s] = d.tx[i]; d.sy[s] = d.ty[i]; d.sz[s] = d.tz[i]; d.stid[s] = d.ttid[i];
+      if (d.s4) d.s4[s] = d.t4[i];
     }
     d.cell_sorted[s] = key;
     int* ci = reinterpret_cast<int*>(&d.cell_info[key]);
@@ -1004,7 +1024,7 @@ struct TpsQueue<false> {
 
 template <bool F32L, int W>
 struct TpsSmem {
-  using T = typename std::conditional<F32L, float, double>::type;
+  using T = float;            // FP32 cutoffs (FP64 mode: widened, for its FP32 prefilter)
   T ct[W][MAXT * MAXT];       // per warp: squared cutoffs of one train (-1: no reaction) ...
   int ct_b[W];                // ... that train
   uint32_t rs[W][N_FWD][32];  // per lane: its non-empty neighbour ranges [rs, re) ...
@@ -1094,10 +1114,16 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
     uint32_t tid_i = 0, cell = 0;
     float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
     double xi = 0, yi = 0, zi = 0;
+    // FP64 mode tests pairs first on FP32 cell offsets against widened cutoffs (when the
+    // context keeps them), then exactly in FP64
+    const bool pref = F32L || d.s4 != nullptr;
     if (home) {
       cell = d.cell_sorted[s];
       if constexpr (F32L) { vi = d.s4[s]; tid_i = __float_as_uint(vi.w); }
-      else { xi = d.sx[s]; yi = d.sy[s]; zi = d.sz[s]; tid_i = d.stid[s]; }
+      else {
+        xi = d.sx[s]; yi = d.sy[s]; zi = d.sz[s]; tid_i = d.stid[s];
+        if (pref) vi = d.s4[s];
+      }
     }
     const int b = (d.n_trains == 1 || !home) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
     const Train& tr = d.trains[b];
@@ -1113,7 +1139,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
         const Train& t0 = d.trains[b0];
         for (int qq = lane; qq < MAXT * MAXT; qq += 32) {
           if constexpr (F32L) sm.ct[wib][qq] = t0.rc2f_tt[qq];
-          else sm.ct[wib][qq] = t0.rc2_tt[qq];
+          else sm.ct[wib][qq] = t0.rc2w_tt[qq];
         }
         __syncwarp();
         if (lane == 0) sm.ct_b[wib] = b0;
@@ -1122,7 +1148,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       rc2 = &sm.ct[wib][ti * MAXT];
     } else {  // the rare chunk spanning several trains reads its rows from global memory
       if constexpr (F32L) rc2 = &tr.rc2f_tt[ti * MAXT];
-      else rc2 = &tr.rc2_tt[ti * MAXT];
+      else rc2 = &tr.rc2w_tt[ti * MAXT];
     }
     if (__any_sync(0xffffffffu, home)) {
       // this lane's non-empty ranges: the own cell's later slots, then the forward cells
@@ -1194,11 +1220,9 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       auto open = [&](int r) {
         j = rs_l[32 * r];
         je = re_l[32 * r];
-        if constexpr (F32L) {
-          int ox, oy, oz;
-          fwd_offset(rk_l[32 * r], ox, oy, oz);
-          cx = ox * tr.hf; cy = oy * tr.hf; cz = oz * tr.hf;
-        }
+        int ox, oy, oz;
+        fwd_offset(rk_l[32 * r], ox, oy, oz);
+        cx = ox * tr.hf; cy = oy * tr.hf; cz = oz * tr.hf;
       };
       if (nr > 0) open(0);
       while (__any_sync(0xffffffffu, ri < nr)) {
@@ -1224,16 +1248,14 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             const uint32_t e2 = __shfl_sync(0xffffffffu, je, src);
             const unsigned long long row2 =
                 __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(hrow), src);
-            float4 v2;
-            float cx2, cy2, cz2;
-            double x2, y2, z2;
-            if constexpr (F32L) {
-              v2 = make_float4(__shfl_sync(0xffffffffu, hv.x, src), __shfl_sync(0xffffffffu, hv.y, src),
-                               __shfl_sync(0xffffffffu, hv.z, src), __shfl_sync(0xffffffffu, hv.w, src));
-              cx2 = __shfl_sync(0xffffffffu, cx, src);
-              cy2 = __shfl_sync(0xffffffffu, cy, src);
-              cz2 = __shfl_sync(0xffffffffu, cz, src);
-            } else {
+            const float4 v2 =
+                make_float4(__shfl_sync(0xffffffffu, hv.x, src), __shfl_sync(0xffffffffu, hv.y, src),
+                            __shfl_sync(0xffffffffu, hv.z, src), __shfl_sync(0xffffffffu, hv.w, src));
+            const float cx2 = __shfl_sync(0xffffffffu, cx, src);
+            const float cy2 = __shfl_sync(0xffffffffu, cy, src);
+            const float cz2 = __shfl_sync(0xffffffffu, cz, src);
+            double x2 = 0, y2 = 0, z2 = 0;
+            if constexpr (!F32L) {
               x2 = __shfl_sync(0xffffffffu, hx, src);
               y2 = __shfl_sync(0xffffffffu, hy, src);
               z2 = __shfl_sync(0xffffffffu, hz, src);
@@ -1245,8 +1267,8 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
               htr = &d.trains[b2];
               j = j2; je = e2;
               ri = 0; nr = 1;  // one borrowed range; no further range is opened
-              if constexpr (F32L) { hv = v2; cx = cx2; cy = cy2; cz = cz2; }
-              else { hx = x2; hy = y2; hz = z2; }
+              hv = v2; cx = cx2; cy = cy2; cz = cz2;
+              if constexpr (!F32L) { hx = x2; hy = y2; hz = z2; }
             }
           }
         }
@@ -1269,8 +1291,12 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           vj[u] = make_float4(0.f, 0.f, 0.f, 0.f);
           tj[u] = 0u;
           if (vu[u]) {
-            if constexpr (F32L) vj[u] = d.s4[ju[u]];
-            else tj[u] = d.stid[ju[u]];
+            if (pref) {
+              vj[u] = d.s4[ju[u]];
+              tj[u] = __float_as_uint(vj[u].w);
+            } else {
+              tj[u] = d.stid[ju[u]];
+            }
           }
         }
         // enqueue the pairs inside the cutoff (queue pushes are warp-wide)
@@ -1321,8 +1347,16 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             bool pass = false;
             double rx1 = 0, ry1 = 0, rz1 = 0, d1sq = 0;
             if (vu[u]) {
-              const double c2 = hrow[tj[u] & 7u];
-              if (c2 >= 0.0) {
+              const uint32_t tjj = tj[u] & 7u;
+              const float cw = hrow[tjj];  // widened FP32 bound, -1 when the types do not react
+              bool near = cw >= 0.f;
+              if (near && pref) {
+                const float fx = cxu[u] + (vj[u].x - hv.x), fy = cyu[u] + (vj[u].y - hv.y),
+                            fz = czu[u] + (vj[u].z - hv.z);
+                near = fx * fx + fy * fy + fz * fz < cw;
+              }
+              if (near) {
+                const double c2 = htr->rc2_tt[tid_type(htid) * MAXT + tjj];
                 // minimum image of x_j - x_i (Eq. 2); negated later into the reference's
                 // x_hi - x_lo orientation, which is exact for pairs inside the cutoff
                 rx1 = min_image(__dsub_rn(d.sx[jj], hx), htr->L, htr->halfL);

@@ -91,6 +91,7 @@ struct Train {
   float rc2f[MAXR];
   double rc2_tt[MAXT * MAXT];  // squared cutoff of each type pair (-1: no reaction)
   float rc2f_tt[MAXT * MAXT];
+  float rc2w_tt[MAXT * MAXT];  // FP32 bound above rc2_tt by more than any FP32-offset error
   double sig[MAXT];        // sqrt(2 D dt) per type
   float sigf[MAXT];
   double ddt[MAXR];        // D_AB dt per reaction (bridge denominator)
