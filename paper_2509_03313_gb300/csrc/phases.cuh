@@ -1158,9 +1158,9 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       uint32_t* re_l = &sm.re[wib][0][lane];
       uint8_t* rk_l = &sm.rk[wib][0][lane];
       int nr = 0;
+      uint32_t kmask = 0;  // forward cells (bits 1..13) within reach of this home
+      int ix = 0, iy = 0, iz = 0;
       if (home) {
-        const int n = tr.n;
-        int ix, iy, iz;
         cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
         const uint32_t own_end = static_cast<uint32_t>(d.cell_info[cell].y);
         if (s + 1u < own_end) { rs_l[0] = s + 1u; re_l[0] = own_end; rk_l[0] = 0; nr = 1; }
@@ -1189,7 +1189,17 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           int ox, oy, oz;
           fwd_offset(k, ox, oy, oz);
           const float gx = gap(ox, ofx), gy = gap(oy, ofy), gz = gap(oz, ofz);
-          if (gx * gx + gy * gy + gz * gz > rcmax2) continue;
+          if (gx * gx + gy * gy + gz * gz <= rcmax2) kmask |= 1u << k;
+        }
+      }
+      // look up only the cells within reach (warp-uniform loop over each lane's set bits)
+      while (__any_sync(0xffffffffu, kmask != 0u)) {
+        if (kmask != 0u) {
+          const int k = __ffs(kmask) - 1;
+          kmask &= kmask - 1u;
+          int ox, oy, oz;
+          fwd_offset(k, ox, oy, oz);
+          const int n = tr.n;
           const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, ox, n), step_cell(iy, oy, n),
                                                          step_cell(iz, oz, n), tr.cb);
           if ((d.occ[nc >> 5] >> (nc & 31u)) & 1u) {
