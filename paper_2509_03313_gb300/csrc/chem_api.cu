@@ -21,10 +21,44 @@ namespace {
 constexpr double N_AVOGADRO = 6.02214076e23;
 constexpr double PI = 3.141592653589793;
 
+// One train's pending species on the host (arrival, position, type), in page-locked
+// memory so that the copy to the device queue runs at full link speed.
+struct PendingBuf {
+  size_t cap = 0;
+  double* t = nullptr;   // one block: t, x, y, z (cap each), then type
+  double* x = nullptr;
+  double* y = nullptr;
+  double* z = nullptr;
+  int32_t* type = nullptr;
+  bool reserve(size_t want) {
+    if (want <= cap) return true;
+    release();
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, want * (4 * sizeof(double) + sizeof(int32_t)), cudaHostAllocDefault) != cudaSuccess)
+      return false;
+    t = static_cast<double*>(p);
+    x = t + want; y = x + want; z = y + want;
+    type = reinterpret_cast<int32_t*>(z + want);
+    cap = want;
+    return true;
+  }
+  void release() {
+    if (t) cudaFreeHost(t);
+    t = x = y = z = nullptr;
+    type = nullptr;
+    cap = 0;
+  }
+};
+
+// Mirror of the device queue [0, p_tail) of one train; the merge of a new injection
+// writes the spare buffer, which then becomes the current one.
 struct PendingHost {
-  std::vector<double> t, x, y, z;
-  std::vector<int32_t> type;
-  size_t size() const { return t.size(); }
+  PendingBuf buf[2];
+  int cur = 0;
+  size_t n = 0;
+  size_t size() const { return n; }
+  void clear() { n = 0; }
+  void release() { buf[0].release(); buf[1].release(); n = 0; }
 };
 
 struct TrainHost {
@@ -113,6 +147,7 @@ void release_all(chem_ctx* ctx) {
     else cudaFree(a.first);
   }
   ctx->allocs.clear();
+  for (TrainHost& h : ctx->th) h.pend.release();
   if (ctx->g_pinned) cudaFreeHost(ctx->g_pinned);
   if (ctx->t_end_pinned) cudaFreeHost(ctx->t_end_pinned);
   ctx->g_pinned = nullptr;
@@ -339,38 +374,53 @@ chem_status inject_one(chem_ctx* ctx, int b, int64_t n, const int32_t* type, con
   }
   (void)L;
   // drop what the device already released, merge the new species stably by arrival
+  // (still-pending species first on equal arrival, new ones in call order)
   PendingHost& p = h.pend;
   const size_t head = t.p_head;
-  PendingHost m;
   const size_t keep = p.size() - head;
   const size_t tot = keep + static_cast<size_t>(n);
   if (tot > t.pend_cap) return fail(ctx, CHEM_ECAPACITY, "pending queue of train %d would hold %zu > %u",
                                     b, tot, t.pend_cap);
-  std::vector<size_t> order(tot);
-  for (size_t i = 0; i < tot; ++i) order[i] = i;
-  auto tval = [&](size_t i) { return i < keep ? p.t[head + i] : t_arr[i - keep]; };
-  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return tval(a) < tval(c); });
-  m.t.resize(tot); m.x.resize(tot); m.y.resize(tot); m.z.resize(tot); m.type.resize(tot);
+  PendingBuf& src = p.buf[p.cur];
+  PendingBuf& dst = p.buf[1 - p.cur];
+  if (!dst.reserve(static_cast<size_t>(t.pend_cap))) return fail(ctx, CHEM_ENOMEM, "page-locked pending buffer");
+  // the new species in arrival order: the identity when already sorted (a pulse in
+  // arrival order, or all at one time), else a stable sort of (arrival, index)
+  std::vector<std::pair<double, uint32_t>> by_t;
+  const bool sorted_new = std::is_sorted(t_arr, t_arr + n);
+  if (!sorted_new) {
+    by_t.resize(static_cast<size_t>(n));
+    for (int64_t i = 0; i < n; ++i) by_t[static_cast<size_t>(i)] = {t_arr[i], static_cast<uint32_t>(i)};
+    std::stable_sort(by_t.begin(), by_t.end(),
+                     [](const std::pair<double, uint32_t>& a, const std::pair<double, uint32_t>& c) {
+                       return a.first < c.first;
+                     });
+  }
+  size_t i = 0, j = 0;
   for (size_t k = 0; k < tot; ++k) {
-    const size_t i = order[k];
-    if (i < keep) {
-      m.t[k] = p.t[head + i]; m.x[k] = p.x[head + i]; m.y[k] = p.y[head + i]; m.z[k] = p.z[head + i];
-      m.type[k] = p.type[head + i];
+    const size_t jn = j < static_cast<size_t>(n) ? (sorted_new ? j : by_t[j].second) : 0;
+    const bool take_old = i < keep && (j >= static_cast<size_t>(n) || src.t[head + i] <= t_arr[jn]);
+    if (take_old) {
+      const size_t q = head + i++;
+      dst.t[k] = src.t[q]; dst.x[k] = src.x[q]; dst.y[k] = src.y[q]; dst.z[k] = src.z[q];
+      dst.type[k] = src.type[q];
     } else {
-      const size_t j = i - keep;
-      m.t[k] = t_arr[j]; m.x[k] = xyz[3 * j]; m.y[k] = xyz[3 * j + 1]; m.z[k] = xyz[3 * j + 2];
-      m.type[k] = type[j];
+      dst.t[k] = t_arr[jn];
+      dst.x[k] = xyz[3 * jn]; dst.y[k] = xyz[3 * jn + 1]; dst.z[k] = xyz[3 * jn + 2];
+      dst.type[k] = type[jn];
+      ++j;
     }
   }
-  p = std::move(m);
+  p.cur = 1 - p.cur;
+  p.n = tot;
   if (tot) {
     ctx->stats.bytes_h2d += static_cast<int64_t>(tot * (4 * sizeof(double) + sizeof(int32_t)));
     const size_t off = t.pend_base;
-    CK(cudaMemcpyAsync(ctx->d.pt + off, p.t.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.px + off, p.x.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.py + off, p.y.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.pz + off, p.z.data(), tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->d.p_type + off, p.type.data(), tot * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.pt + off, dst.t, tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.px + off, dst.x, tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.py + off, dst.y, tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.pz + off, dst.z, tot * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d.p_type + off, dst.type, tot * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
   }
   t.p_head = 0;
   t.p_tail = static_cast<uint32_t>(tot);
@@ -821,7 +871,7 @@ chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds) {
     TrainHost& h = ctx->th[b];
     if (seeds) h.cfg.seed = seeds[b];
     h.E_dep = 0.0;
-    h.pend = PendingHost();
+    h.pend.clear();
     init_train_dynamic(tr[b], h.cfg, tr[b].n_alloc);
   }
   s = init_global(ctx);
