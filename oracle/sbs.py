@@ -36,7 +36,10 @@ Where the paper is silent the following readings are used, identically in the li
 * products at the diffusion-weighted encounter point, ids assigned in ascending id_lo
   order and table order; products diffuse from the next step;
 * optional free-diffusion jump (no reactions) once sbs_horizon has passed since the
-  last release, up to the next arrival or the end time.
+  last release, up to the next arrival or the end time;
+* the beam-off (homogeneous) stage of Sec. 2.2 with its own readings in
+  ``oracle/homogeneous.py``; its survivors are re-created ahead of the pending species
+  at the next release.
 """
 from __future__ import annotations
 
@@ -190,7 +193,8 @@ class SBSOracle:
             if self.pair_rxn[a, b] >= 0:
                 raise ValueError("two reactions for one type pair")
             self.pair_rxn[a, b] = self.pair_rxn[b, a] = r
-            self.rx.append(dict(a=a, b=b, D_AB=D_AB, R=R, products=tuple(products), water=water))
+            self.rx.append(dict(a=a, b=b, D_AB=D_AB, R=R, products=tuple(products), water=water,
+                                k_tab=float(k_tab)))
         self.n_rxn = len(self.rx)
         self.R = np.array([x["R"] for x in self.rx], dtype=np.float64)
         self.D_AB = np.array([x["D_AB"] for x in self.rx], dtype=np.float64)
@@ -211,6 +215,10 @@ class SBSOracle:
         self.p_types = np.zeros(0, dtype=np.int64)
         self.p_pos = np.zeros((0, 3), dtype=np.float64)
         self.p_t = np.zeros(0, dtype=np.float64)
+        # Survivors of the last homogeneous stage, re-created as particles at the next
+        # release (types in ascending order), and the number of stages taken.
+        self.mat_types = np.zeros(0, dtype=np.int64)
+        self.hx_stage = 0
         self.t = 0.0
         self.step = 0
         self.dt_cur = self.dt_min
@@ -244,8 +252,18 @@ class SBSOracle:
     # -- one SBS step --------------------------------------------------------------
     def _release(self):
         n = int(np.searchsorted(self.p_t, self.t, side="right"))
-        if n == 0:
+        m = self.mat_types.shape[0]
+        if n + m == 0:
             return 0
+        if m:
+            # survivors of a homogeneous stage first, at uniform positions
+            from .homogeneous import materialised_positions
+            mat_ids = np.arange(self.next_id, self.next_id + m, dtype=np.int64)
+            self.next_id += m
+            self.ids = np.concatenate([self.ids, mat_ids])
+            self.types = np.concatenate([self.types, self.mat_types])
+            self.pos = np.concatenate([self.pos, materialised_positions(mat_ids, self.L, self.key)])
+            self.mat_types = np.zeros(0, dtype=np.int64)
         new_ids = np.arange(self.next_id, self.next_id + n, dtype=np.int64)
         self.next_id += n
         self.ids = np.concatenate([self.ids, new_ids])
@@ -255,7 +273,7 @@ class SBSOracle:
         self.t_last_release = self.t
         if self.reset_on_release:
             self.dt_cur = self.dt_min
-        return n
+        return n + m
 
     def _choose_dt(self, t_end: float):
         next_arrival = self.p_t[0] if self.p_t.shape[0] else math.inf
@@ -368,9 +386,38 @@ class SBSOracle:
             n += 1
         return n
 
+    # -- homogeneous stage (Sec. 2.2) ------------------------------------------------
+    def run_homogeneous(self, t_end: float):
+        """Beam-off stage: the species (and pending ones already due) become molecule
+        numbers, the rate equations of Table 1 (Eq. 3, Eq. 4) run for t_end - t, and the
+        survivors wait to be re-created uniformly at the next step (see
+        ``oracle/homogeneous.py`` for the readings). Returns (e, E): real extents and
+        integer events of the stage."""
+        from .homogeneous import stage, water_change
+        if not (t_end > self.t):
+            return None
+        n_due = int(np.searchsorted(self.p_t, self.t, side="right"))
+        if n_due < self.p_t.shape[0] and self.p_t[n_due] < t_end:
+            raise ValueError("species arrive during the homogeneous stage")
+        n0 = self.counts() + np.bincount(self.p_types[:n_due], minlength=self.n_types)
+        self.p_t, self.p_types, self.p_pos = (self.p_t[n_due:], self.p_types[n_due:],
+                                              self.p_pos[n_due:])
+        reactions = [(x["a"], x["b"], x["k_tab"], x["products"], x["water"]) for x in self.rx]
+        e, E, n = stage(n0, self.L, t_end - self.t, reactions, self.hx_stage, self.key)
+        self.hx_stage += 1
+        self.events_total += E
+        self.water += water_change(E, reactions)
+        self.ids = np.zeros(0, dtype=np.int64)
+        self.types = np.zeros(0, dtype=np.int64)
+        self.pos = np.zeros((0, 3), dtype=np.float64)
+        self.mat_types = np.repeat(np.arange(self.n_types, dtype=np.int64), n)
+        self.t = float(t_end)
+        return e, E
+
     # -- outputs -------------------------------------------------------------------
     def counts(self):
-        return np.bincount(self.types, minlength=self.n_types).astype(np.int64)
+        return (np.bincount(self.types, minlength=self.n_types) +
+                np.bincount(self.mat_types, minlength=self.n_types)).astype(np.int64)
 
     def g_values(self):
         """G = molecules per 100 eV deposited."""
