@@ -202,6 +202,40 @@ chem_status chem_batch_get_state(chem_ctx* ctx, int32_t train, int64_t cap, int3
 chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds);
 int32_t chem_batch_size(const chem_ctx* ctx);
 
+/* ---- homogeneous (beam-off) stage ------------------------------------------------
+ * Sec. 2.2: during the beam-off time between pulses, and for 10 s after the last pulse,
+ * the paper follows the species as a well-mixed system with the rate equations of
+ * Table 1 (Eq. 3, Eq. 4) instead of step by step. For every train whose clock is below
+ * t_end_s[b] (trains at or past it are left alone):
+ *  - its species counts, plus pending species already due (arrival <= clock), become
+ *    molecule numbers in the box volume L^3; its particles are removed;
+ *  - the rate equations are integrated for the reaction extents e_r (events): de_r/dt =
+ *    kappa_r n_a n_b, kappa_r = k_tab / (N_A V), (k_tab / 2) / (N_A V) for a self
+ *    reaction, n = n0 + nu e; stiff-stable extrapolated linearly implicit Euler on the
+ *    device (per step 1e-12 relative + 1e-8 events);
+ *  - the extents are rounded to whole events without bias (floor(e_r) plus one with
+ *    probability frac(e_r), uniform from Philox4x32-10 at counter (stage, r, 0, 4));
+ *    while a count would be negative, the lowest-index reaction consuming the lowest
+ *    negative species gives back one event; counts, event tallies and the water balance
+ *    take the whole events, so charge and atoms stay exactly conserved;
+ *  - the clock moves to t_end_s[b]. chem_tally reports the survivors at once; they are
+ *    re-created as particles when the train takes its next step: ids from the next id
+ *    in ascending type order, ahead of the species released in that step, uniform
+ *    positions -L/2 + L u from counters (id, 0, 0, 3) (x from words 0-1, y from words
+ *    2-3) and (id, 1, 0, 3) (z), then released like injected species (the step time
+ *    resets to dt_min when dt_reset_on_release is set). chem_get_state lists them only
+ *    from that step on.
+ * A pending species arriving strictly between the clock and t_end_s[b] is an error:
+ * CHEM_EINVAL, nothing changed. CHEM_ECAPACITY (sticky) if the integrator exceeds its
+ * step limit. Blocks until the device has finished. */
+chem_status chem_run_homogeneous(chem_ctx* ctx, double t_end_s);
+chem_status chem_batch_run_homogeneous(chem_ctx* ctx, const double* t_end_s);
+/* The last homogeneous stage of a train: extents[n_rxn] real extents (events) before
+ * rounding, events[n_rxn] the whole events applied, *integrator_steps the accepted
+ * steps. Any output pointer may be NULL. */
+chem_status chem_batch_homogeneous_report(chem_ctx* ctx, int32_t train, double* extents, int64_t* events,
+                                          int64_t* integrator_steps);
+
 /* Choose, by timing short runs from the current state, the launch form (one kernel per
  * phase in a graph, or the persistent cooperative kernel), the steps per graph replay,
  * the hash resolution limit (cells per axis at small cutoffs, i.e. the cell size) and

@@ -1,6 +1,6 @@
 """In-tree build of the CUDA library (libchem.so) for sm_103a with nvcc.
 
-The three translation units compile in parallel; FP64-mode kernels are built with
+The translation units compile in parallel; FP64-mode kernels are built with
 --fmad=false and all host code with -ffp-contract=off so that no multiply-add is
 contracted on either side (the GPU machine is aarch64, where GCC would otherwise fuse).
 """
@@ -24,6 +24,7 @@ UNITS = {
     "kernels_exact.cu": ["--fmad=false"],
     "kernels_f32l.cu": [],
     "noalloc.cu": ["--fmad=false"],
+    "homog.cu": [],
 }
 
 

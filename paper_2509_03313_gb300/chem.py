@@ -84,7 +84,8 @@ EXPORTS = ["chem_init", "chem_inject_pulse", "chem_run_until", "chem_tally", "ch
            "chem_get_events", "chem_get_step_log", "chem_reset", "chem_last_error", "chem_destroy",
            "chem_batch_init", "chem_batch_inject", "chem_batch_run_until", "chem_batch_tally",
            "chem_batch_get_state", "chem_batch_reset", "chem_batch_size", "chem_autotune", "chem_set_tuning",
-           "chem_version", "chem_get_stats", "chem_set_profiling", "chem_step_noalloc"]
+           "chem_version", "chem_get_stats", "chem_set_profiling", "chem_step_noalloc",
+           "chem_run_homogeneous", "chem_batch_run_homogeneous", "chem_batch_homogeneous_report"]
 
 
 class ChemError(RuntimeError):
@@ -124,6 +125,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "chem_set_profiling": (i32, [vp, i32]),
         "chem_step_noalloc": (i32, [P(chem_config), ctypes.c_uint32, dbl, dbl, ctypes.c_uint32, i32,
                                     vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "chem_run_homogeneous": (i32, [vp, dbl]),
+        "chem_batch_run_homogeneous": (i32, [vp, vp]),
+        "chem_batch_homogeneous_report": (i32, [vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -275,6 +279,25 @@ def chem_run_until(ctx, t_end: float):
 def chem_batch_run_until(ctx, t_end):
     t = np.ascontiguousarray(t_end, dtype=np.float64)
     _check(ctx, lib().chem_batch_run_until(ctx, _ptr(t)))
+
+
+def chem_run_homogeneous(ctx, t_end: float):
+    """Homogeneous (beam-off) stage of every train up to t_end (rate equations, Sec. 2.2)."""
+    _check(ctx, lib().chem_run_homogeneous(ctx, float(t_end)))
+
+
+def chem_batch_run_homogeneous(ctx, t_end):
+    t = np.ascontiguousarray(t_end, dtype=np.float64)
+    _check(ctx, lib().chem_batch_run_homogeneous(ctx, _ptr(t)))
+
+
+def chem_batch_homogeneous_report(ctx, train: int = 0, n_rxn: int = 16):
+    """(real extents, whole events, integrator steps) of the train's last homogeneous stage."""
+    e = np.zeros(n_rxn, np.float64)
+    E = np.zeros(n_rxn, np.int64)
+    st = np.zeros(1, np.int64)
+    _check(ctx, lib().chem_batch_homogeneous_report(ctx, int(train), _ptr(e), _ptr(E), _ptr(st)))
+    return e, E, int(st[0])
 
 
 def chem_batch_size(ctx) -> int:

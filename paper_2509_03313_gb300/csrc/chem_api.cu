@@ -249,6 +249,17 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
   (void)n_max;
   t.n_ref = 0;  // chosen by the first step
   t.h_ref = 0.0;
+  t.hx_sel = 0;
+  t.hx_stage = 0;
+  t.mat_n = 0;
+  t.rel_mat = 0;
+  t.hx_t_end = 0.0;
+  t.hx_steps = 0;
+  for (int i = 0; i < MAXT; ++i) t.mat_cum[i] = 0;
+  for (int i = 0; i < MAXR; ++i) {
+    t.hx_e[i] = 0.0;
+    t.hx_E[i] = 0;
+  }
   t.active = 0;
   t.free_jump = 0;
   t.key0 = static_cast<uint32_t>(c.seed & 0xFFFFFFFFull);
@@ -350,6 +361,75 @@ chem_status run_loop(chem_ctx* ctx) {
     if (it > (1ll << 40)) return fail(ctx, CHEM_ESTATE, "run loop made no progress");
   }
   return CHEM_OK;
+}
+
+// Homogeneous stage (Sec. 2.2) of every train b with t_end[b] > its clock. Pending
+// species already due join the stage; one arriving inside it is an error (EINVAL, nothing
+// changed).
+chem_status homogeneous_run(chem_ctx* ctx, const double* t_end) {
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  if (!t_end) return CHEM_EINVAL;
+  for (int b = 0; b < ctx->B; ++b)
+    if (!std::isfinite(t_end[b])) return CHEM_EINVAL;
+  std::vector<Train> tr;
+  s = download_trains(ctx, tr);
+  if (s) return s;
+  std::vector<size_t> due_end(ctx->B, 0);
+  bool any = false;
+  for (int b = 0; b < ctx->B; ++b) {
+    const Train& t = tr[b];
+    if (!(t_end[b] > t.t)) continue;
+    const PendingHost& p = ctx->th[b].pend;
+    const PendingBuf& buf = p.buf[p.cur];
+    const double* first = buf.t ? buf.t + t.p_head : nullptr;
+    const double* last = buf.t ? buf.t + p.size() : nullptr;
+    const size_t i = t.p_head + static_cast<size_t>(first ? std::upper_bound(first, last, t.t) - first : 0);
+    if (i < p.size() && buf.t[i] < t_end[b]) {
+      ctx->err = "species arrive during the homogeneous stage";
+      return CHEM_EINVAL;
+    }
+    due_end[b] = i;
+    any = true;
+  }
+  if (!any) return CHEM_OK;
+  for (int b = 0; b < ctx->B; ++b) {
+    Train& t = tr[b];
+    t.hx_sel = 0;
+    if (!(t_end[b] > t.t)) continue;
+    const PendingHost& p = ctx->th[b].pend;
+    const PendingBuf& buf = p.buf[p.cur];
+    for (size_t i = t.p_head; i < due_end[b]; ++i) t.counts[buf.type[i]] += 1;
+    t.p_head = static_cast<uint32_t>(due_end[b]);
+    t.hx_sel = 1;
+    t.hx_t_end = t_end[b];
+  }
+  s = upload_trains(ctx, tr);
+  if (s) return s;
+  CK(enqueue_homogeneous(ctx->d, ctx->lc.stream_blocks, ctx->stream));
+  ctx->stats.kernel_launches += 2;
+  s = download_global(ctx);
+  if (s) return s;
+  const Global& g = *ctx->g_pinned;
+  if (g.status != 0) {
+    return fail(ctx, static_cast<chem_status>(g.status), "homogeneous stage: %s (status %d)",
+                g.err_where == 0x4858u ? "rate-equation integrator step limit" : "device error", g.status);
+  }
+  return CHEM_OK;
+}
+
+chem_status homogeneous_report(chem_ctx* ctx, int b, double* extents, int64_t* events, int64_t* steps) {
+  if (!ctx) return CHEM_EINVAL;
+  if (b < 0 || b >= ctx->B) return CHEM_EINVAL;
+  std::vector<Train> tr;
+  chem_status s = download_trains(ctx, tr);
+  if (s) return s;
+  for (int r = 0; r < ctx->tables.n_rxn; ++r) {
+    if (extents) extents[r] = tr[b].hx_e[r];
+    if (events) events[r] = tr[b].hx_E[r];
+  }
+  if (steps) *steps = tr[b].hx_steps;
+  return ctx->status;
 }
 
 chem_status inject_one(chem_ctx* ctx, int b, int64_t n, const int32_t* type, const double* xyz,
@@ -586,6 +666,9 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     T.n_prod[r] = x.n_prod;
     for (int q = 0; q < 3; ++q) T.prod[r][q] = q < x.n_prod ? x.prod[q] : 0;
     T.water[r] = x.water_delta;
+    T.rxn_a[r] = x.a;
+    T.rxn_b[r] = x.b;
+    T.k_tab[r] = x.k_tab;
   }
 
   // ---- per-train constants and global sizes
@@ -817,6 +900,22 @@ chem_status chem_run_until(chem_ctx* ctx, double t_end_s) {
   if (s) return s;
   std::vector<double> t(ctx->B, t_end_s);
   return chem_batch_run_until(ctx, t.data());
+}
+
+chem_status chem_batch_run_homogeneous(chem_ctx* ctx, const double* t_end_s) {
+  return homogeneous_run(ctx, t_end_s);
+}
+
+chem_status chem_run_homogeneous(chem_ctx* ctx, double t_end_s) {
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  std::vector<double> t(ctx->B, t_end_s);
+  return homogeneous_run(ctx, t.data());
+}
+
+chem_status chem_batch_homogeneous_report(chem_ctx* ctx, int32_t train, double* extents, int64_t* events,
+                                          int64_t* integrator_steps) {
+  return homogeneous_report(ctx, train, extents, events, integrator_steps);
 }
 
 chem_status chem_batch_tally(chem_ctx* ctx, int32_t train, int64_t* counts, double* G, int64_t* events,

@@ -36,6 +36,9 @@ cudaError_t enqueue_persistent_f64(const Dev& d, const LaunchCfg& lc, int n_step
 cudaError_t persistent_occupancy_f64(int* blocks_per_sm);
 cudaError_t enqueue_set_t_end(const Dev& d, const double* t_end_dev, cudaStream_t s);
 
+// homog.cu: homogeneous (beam-off) stage of the trains with Train::hx_sel set
+cudaError_t enqueue_homogeneous(const Dev& d, int blocks, cudaStream_t s);
+
 // kernels_f32l.cu (FP32-local mode)
 cudaError_t enqueue_step_f32l(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cudaEvent_t* ev, bool first,
                               bool last);

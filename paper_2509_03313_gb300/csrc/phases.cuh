@@ -150,6 +150,7 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     double dt_cur = tr.dt_cur;
     const uint32_t p_head = tr.p_head, p_tail = tr.p_tail, pend_base = tr.pend_base;
     const uint32_t next_id = tr.next_id, id_limit = tr.id_limit;
+    const uint32_t mat = tr.mat_n;  // survivors of a homogeneous stage (already counted)
     const int reset = tr.reset_on_release;
     long long live = 0;
     for (int ty = 0; ty < MAXT; ++ty) live += (ty < tb.n_types) ? tr.counts[ty] : 0;
@@ -168,7 +169,7 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
       }
       rel = lo - p_head;
       double t_last = t_lr;
-      if (rel > 0) {
+      if (rel + mat > 0) {
         t_last = t;
         tr.t_last_release = t;
         if (reset) dt_cur = dt_min;
@@ -192,21 +193,25 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
       tr.dt = dt;
       tr.t_next = t_next;
       tr.t_start = t;
-      tr.rel_n = rel;
+      // releases: the re-created survivors first, then the arrived species
+      tr.rel_n = rel + mat;
+      tr.rel_mat = mat;
+      tr.mat_n = 0;
       tr.rel_id0 = next_id;
       tr.rel_p0 = p_head;
       tr.p_head = p_head + rel;
-      tr.next_id = next_id + rel;
+      tr.next_id = next_id + rel + mat;
       tr.n_live_step = live + rel;
       tr.n_events_step = 0;
-      if (next_id + rel > id_limit) raise_status(d.g, CHEM_ECAPACITY);
+      if (static_cast<unsigned long long>(next_id) + rel + mat > id_limit) raise_status(d.g, CHEM_ECAPACITY);
       atomicOr(&sb.any, 1u);
     } else {
       tr.rel_n = 0;
+      tr.rel_mat = 0;
     }
     tr.active = act ? 1 : 0;
     tr.free_jump = free_jump;
-    sb.rel[b] = rel;
+    sb.rel[b] = act ? rel + mat : 0u;
     sb.dt[b] = act ? dt : 0.0;
   }
   __syncthreads();
@@ -348,6 +353,27 @@ __device__ __forceinline__ void count_add(const Dev& d, uint32_t b, uint32_t typ
 }
 
 // ======================================================================== release
+// Position of a survivor of a homogeneous stage re-created with id `id`: uniform in the
+// box, -L/2 + L u per axis with u from counter (id, 0, 0, 3) words (0,1) -> x, (2,3) -> y
+// and counter (id, 1, 0, 3) words (0,1) -> z, then Eq. 1.
+__device__ __forceinline__ void recreated_position(const Train& tr, uint32_t id, double& x, double& y,
+                                                   double& z) {
+  const uint4 a = philox4x32_10(make_uint4(id, 0u, 0u, 3u), tr.key0, tr.key1);
+  const uint4 c = philox4x32_10(make_uint4(id, 1u, 0u, 3u), tr.key0, tr.key1);
+  const double ux = __dmul_rn(static_cast<double>(u53(a.x, a.y)), TWO_POW_M53);
+  const double uy = __dmul_rn(static_cast<double>(u53(a.z, a.w)), TWO_POW_M53);
+  const double uz = __dmul_rn(static_cast<double>(u53(c.x, c.y)), TWO_POW_M53);
+  x = wrap_box(__dadd_rn(-tr.halfL, __dmul_rn(tr.L, ux)), tr.L, tr.halfL);
+  y = wrap_box(__dadd_rn(-tr.halfL, __dmul_rn(tr.L, uy)), tr.L, tr.halfL);
+  z = wrap_box(__dadd_rn(-tr.halfL, __dmul_rn(tr.L, uz)), tr.L, tr.halfL);
+}
+
+// Type of the k-th re-created survivor (ascending type order).
+__device__ __forceinline__ uint32_t recreated_type(const Train& tr, uint32_t k) {
+  uint32_t ty = 0;
+  while (ty + 1 < static_cast<uint32_t>(MAXT) && k >= tr.mat_cum[ty]) ++ty;
+  return ty;
+}
 
 // ======================================================================== diffuse
 // Displace every species of an active train (Sec. 2.1 SBS step) with periodic wrap
@@ -371,6 +397,7 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
     const bool valid = s < n_total;
     const bool rel = valid && s >= rel_base;
     uint32_t rel_b = 0, rel_type = 0;
+    bool rel_new = false;  // a released species not yet in the train's counts
     if (valid) {
       uint32_t key;
       uint32_t cell;
@@ -379,14 +406,21 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
       uint32_t tid = 0;
       bool dead = false;
       if (rel) {
-        // release: id in (arrival, call order) order, position from the pending queue
+        // release: re-created survivors of a homogeneous stage first, then the pending
+        // queue; ids in that order (arrival, call order within the queue)
         rel_b = train_of_release(d, s);
         const Train& tr = d.trains[rel_b];
         const uint32_t k = s - tr.rel_off;
-        const uint32_t p = tr.pend_base + tr.rel_p0 + k;
-        rel_type = static_cast<uint32_t>(d.p_type[p]);
+        if (k < tr.rel_mat) {
+          rel_type = recreated_type(tr, k);
+          recreated_position(tr, tr.rel_id0 + k, px, py, pz);
+        } else {
+          const uint32_t p = tr.pend_base + tr.rel_p0 + (k - tr.rel_mat);
+          rel_type = static_cast<uint32_t>(d.p_type[p]);
+          px = d.px[p]; py = d.py[p]; pz = d.pz[p];
+          rel_new = true;
+        }
         tid = ((tr.rel_id0 + k) << 3) | rel_type;
-        px = d.px[p]; py = d.py[p]; pz = d.pz[p];
         if (F32L) {
           const int n = tr.n_ref;
           const double h = tr.h_ref, inv_h = static_cast<double>(n) * tr.inv_L;
@@ -495,7 +529,7 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
       d.keys0[s] = key;  // the first radix pass takes the slot itself as the value
       for (int p = 0; p < d.passes; ++p) atomicAdd(&hist[p][(key >> (8 * p)) & 255u], 1u);
     }
-    count_add(d, rel_b, rel_type, 1, rel);
+    count_add(d, rel_b, rel_type, 1, rel_new);
   }
   // warp-aggregate the dead count
   for (int o = 16; o > 0; o >>= 1) n_dead_local += __shfl_xor_sync(0xffffffffu, n_dead_local, o);

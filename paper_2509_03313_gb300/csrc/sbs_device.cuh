@@ -53,7 +53,8 @@ struct Tables {
   int n_prod[MAXR];
   int prod[MAXR][3];
   int water[MAXR];
-  double w_lo[MAXR];            // unused placeholder for alignment
+  int rxn_a[MAXR], rxn_b[MAXR]; // reactant types of each reaction
+  double k_tab[MAXR];           // rate constant as tabulated (L mol^-1 s^-1; self: 2k)
 };
 
 // Per-train state. Constants are written at init; the clock and tallies live here on
@@ -102,6 +103,17 @@ struct Train {
   long long n_live_step;
   uint32_t n_events_step;
   uint32_t pad_;
+  // homogeneous (beam-off) stage: set by the host for the stage being launched, then
+  // its results; the survivors wait in mat_n until the next release re-creates them
+  int hx_sel;
+  uint32_t hx_stage;       // stages taken so far (Philox counter of the rounding)
+  uint32_t mat_n;          // survivors to re-create at the next release
+  uint32_t rel_mat;        // of this step's releases, the re-created survivors (first)
+  uint32_t mat_cum[MAXT];  // survivors of types <= t (inclusive prefix)
+  double hx_t_end;
+  double hx_e[MAXR];       // real extents of the last stage (events)
+  long long hx_E[MAXR];    // whole events of the last stage
+  long long hx_steps;      // accepted integrator steps of the last stage
 };
 
 // Context-wide counters.

@@ -218,6 +218,22 @@ def multi_pulse(seed: int, n_pulses: int = 10, period_s: float = 1e-4, fwhm_s: f
                     t_end=(n_pulses - 1) * period_s + fwhm_s + 1e-6)
 
 
+def hybrid_stages(n_pulses: int, period_s: float, fwhm_s: float, tail_s: float = 10.0,
+                  sbs_after_s: float = 0.0) -> List[tuple]:
+    """The alternation of Sec. 2.2: step-by-step chemistry while the beam is on (each
+    pulse [T_k, T_k + fwhm_s), extended by sbs_after_s), the rate equations for the rest
+    of the beam-off time up to the next pulse, and for tail_s after the last pulse.
+    Returns the calls in order as (kind, t_end) with kind "sbs" or "ode"."""
+    out = []
+    for k in range(n_pulses):
+        t_on = k * period_s + fwhm_s + sbs_after_s
+        out.append(("sbs", t_on))
+        t_next = (k + 1) * period_s if k + 1 < n_pulses else t_on + tail_s
+        if t_next > t_on:
+            out.append(("ode", t_next))
+    return out
+
+
 def dose_rate_sweep(n_trains: int = 64, seed: int = 0, n_min: int = 10_000,
                     n_max: int = 2_000_000, n_pulses: int = 10, fwhm_s: float = 1e-6,
                     sbs_horizon: float = 1e-3) -> List[dict]:
