@@ -363,6 +363,9 @@ def run_gpu_arm(args):
     ss_all, t_max = aggregate_over_ranks(r["ss"], r["tot"], device=dev)
     # the batched sweep: every rank runs its share of the trains
     bres = None if args.no_batched else run_batched(args, chem, W, torch, stream, alloc, flush, rank, world, dev)
+    # the same sweep with every pulse and the beam-off stages (rate equations), 10 s tail
+    hres = None if args.no_hybrid else run_hybrid(args, chem, W, torch, stream, alloc, rank, world, dev,
+                                                  tuned=bres.get("autotuned") if bres else None)
     if rank != 0:
         return 0
     value = ss_all / t_max
@@ -446,6 +449,8 @@ def run_gpu_arm(args):
         line["batched"] = bres
         if "fp64" in line and bres.get("value"):
             line["speedup_batched_fp32l_over_plain_fp64"] = bres["value"] / line["fp64"]["value"]
+    if hres is not None:
+        line["hybrid"] = hres
     line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     return 0
@@ -519,6 +524,125 @@ def run_batched(args, chem, W, torch, stream, alloc, flush, rank=0, world=1, dev
                         "species log-spaced 1e4-2e6 per 10 pulses, pulses of 4 bunches, 10 us window"}
 
 
+def sum_over_ranks(rows, device=None):
+    """Element-wise sum of a float array over the ranks (each train's row is filled on
+    the one rank that ran it, zeros elsewhere)."""
+    import torch
+    import torch.distributed as dist
+    a = torch.as_tensor(np.asarray(rows, dtype=np.float64), device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    return a.cpu().numpy()
+
+
+def run_trains(chem, hybrid, wls_all, plans_all, stream, alloc, rank, world, device, tuned=None):
+    """Run the (kind, t_end) plans of this rank's share of the trains in one batched
+    FP32-local context. Returns (species-steps, slowest wall seconds, slowest seconds in
+    the rate-equation stages, most integrator steps of one stage, rows) with rows[b] =
+    post-irradiation counts (7), E_dep, radicals at the end of the second-to-last pulse
+    and (real, before rounding) when the last pulse starts: summed over the ranks."""
+    import torch
+    mine = shard_trains([w.n_species for w in wls_all], world)[rank]
+    wls = [wls_all[b] for b in mine]
+    plans = [plans_all[b] for b in mine]
+    cfgs, keep = [], []
+    for b, wl in zip(mine, wls):
+        s = wl.schedule
+        n = wl.n_species
+        cfg, k = chem.make_config(
+            wl.L, wl.D, wl.reactions, seed=91 + b, train_id=b, precision=chem.CHEM_FP32_LOCAL,
+            dt_min=s.dt_min, dt_max=s.dt_max, dt_growth=s.dt_growth,
+            capacity_species=int(n * 0.8) + 4096, capacity_pending=n + 16,
+            capacity_candidates=max(4096, n // 4), cells_per_axis_max=128,
+            stream=stream.cuda_stream, allocator=alloc)
+        cfgs.append(cfg)
+        keep.append(k)
+    rows = np.zeros((len(wls_all), 10))
+    ss, wall, ode, steps_max = 0, 0.0, 0.0, 0
+    if wls:
+        ctx = chem.chem_batch_init(cfgs)
+        try:
+            if tuned:
+                chem.chem_set_tuning(ctx, *[int(tuned[k]) for k in ("steps_per_launch", "cells_per_axis_limit",
+                                                                     "species_per_item", "launch_mode")])
+            for i, wl in enumerate(wls):
+                for p in wl.pulses:
+                    chem.chem_batch_inject(ctx, i, p.types, p.xyz, p.t_arrival, p.energy_eV)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            run = hybrid.run_plans(ctx, plans)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            steps_max = max(chem.chem_batch_homogeneous_report(ctx, i)[2] for i in range(len(wls)))
+        finally:
+            chem.chem_destroy(ctx)
+        ss, ode = run["species_steps"], run["seconds"]["ode"]
+        frac = hybrid.buildup_fraction(run, nu=hybrid.stoichiometry(7, wls[0].reactions))
+        for i, b in enumerate(mine):
+            rows[b, :7] = run["counts"][-1, i]
+            rows[b, 7] = sum(p.energy_eV for p in wls[i].pulses)
+            rows[b, 8] = frac[i]
+    ss_all, wall_all, _ = gather_batched(ss, wall, np.zeros(1, np.int64), device=device)
+    _, ode_all, _ = gather_batched(0, ode, np.zeros(1, np.int64), device=device)
+    _, steps_all, _ = gather_batched(0, float(steps_max), np.zeros(1, np.int64), device=device)
+    return ss_all, wall_all, ode_all, int(steps_all), sum_over_ranks(rows, device=device)
+
+
+def run_hybrid(args, chem, W, torch, stream, alloc, rank=0, world=1, device=None, tuned=None):
+    """Sec. 2.2 alternation on the GPU: step-by-step chemistry while the beam is on, the
+    rate equations for the rest of each interval and for 10 s after the last pulse.
+    (1) The 64 trains of the dose-rate sweep with all 10 pulses: post-irradiation
+    G(H2O2) per train and the radical build-up before the last pulse, whose onset gives
+    the SDR/UHDR threshold of Sec. 3. (2) Separate irradiations of 1-20 pulses at 1 and
+    1e4 Gy/s: the H2O2 yield as the slope of post-irradiation concentration against dose
+    (Fig. Concentration-Dose). Timed end to end on the host clock (every call syncs);
+    trains are split between the ranks."""
+    from paper_2509_03313_gb300 import hybrid
+    wls_all, plans_all = W.hybrid_sweep(scale=args.hybrid_scale)
+    descs = W.dose_rate_sweep()
+    ss, wall, ode, steps, rows = run_trains(chem, hybrid, wls_all, plans_all, stream, alloc, rank, world,
+                                            device, tuned)
+    g_h2o2 = rows[:, 6] * 100.0 / rows[:, 7]
+    per_dp = {}
+    for dp in sorted({d["pulse_dose_rate"] for d in descs}):
+        idx = [d["train"] for d in descs if d["pulse_dose_rate"] == dp]
+        dav = [descs[q]["avg_dose_rate"] for q in idx]
+        per_dp[f"{dp:g}"] = {
+            "avg_dose_rate_Gy_s": [round(v, 4) for v in dav],
+            "G_H2O2_post": [round(float(g_h2o2[q]), 4) for q in idx],
+            "radical_buildup": [round(float(rows[q, 8]), 5) for q in idx],
+            "threshold_avg_dose_rate": hybrid.threshold_dose_rate(dav, rows[idx, 8]),
+        }
+    out = {"value": ss / wall, "unit": UNIT, "trains": len(wls_all),
+           "species": int(sum(w.n_species for w in wls_all)), "wall_s": wall, "ode_s": ode,
+           "integrator_steps_max": steps,
+           "mode": "FP32-local SBS while the beam is on; rate equations (GPU) between pulses and for 10 s after",
+           "timing": "host clock around the whole alternation, species-steps of the SBS stages",
+           "per_pulse_dose_rate": per_dp,
+           "workload": "dose-rate sweep: 64 trains, Dav log-spaced 0.01-1e5 Gy/s at Dp 2e5 and 1e6 Gy/s, "
+                       "species log-spaced 1e4-2e6 over 10 pulses of 4 bunches each, all pulses, 10 s tail"}
+    if not args.no_dose_series:
+        wls_d, plans_d, meta = W.dose_series()
+        ss_d, wall_d, ode_d, _, rows_d = run_trains(chem, hybrid, wls_d, plans_d, stream, alloc, rank, world,
+                                                    device, tuned)
+        series = {}
+        for dav in sorted({m["avg_dose_rate"] for m in meta}):
+            idx = [q for q, m in enumerate(meta) if m["avg_dose_rate"] == dav]
+            L = wls_d[idx[0]].L
+            dose = rows_d[idx, 7] * 1.602176634e-19 / (L ** 3 * 1e-24)  # J per kg of water
+            conc = hybrid.concentration(rows_d[idx, 6], L)
+            slope, g = hybrid.dose_slope_yield(dose, conc)
+            series[f"{dav:g}"] = {"pulses": [meta[q]["n_pulses"] for q in idx],
+                                  "dose_Gy": [round(float(v), 4) for v in dose],
+                                  "H2O2_post_M": [float(v) for v in conc],
+                                  "yield_mol_per_J": slope, "yield_per_100eV": g}
+        out["dose_series"] = {"workload": "1, 5, 10, 15, 20 pulses of 1e5 species (about 1 Gy each) at "
+                                          "Dp 1e6 Gy/s, Dav 1 and 1e4 Gy/s, each followed by 10 s",
+                              "wall_s": wall_d, "ode_s": ode_d, "species_steps_per_s": ss_d / wall_d,
+                              "per_avg_dose_rate": series}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,6 +667,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-scale", type=float, default=1.0)
     ap.add_argument("--batch-reps", type=int, default=2)
+    ap.add_argument("--no-hybrid", action="store_true")
+    ap.add_argument("--hybrid-scale", type=float, default=1.0)
+    ap.add_argument("--no-dose-series", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference_arm(args)

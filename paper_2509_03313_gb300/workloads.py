@@ -262,6 +262,61 @@ def dose_rate_sweep(n_trains: int = 64, seed: int = 0, n_min: int = 10_000,
     return out
 
 
+def hybrid_sweep(n_trains: int = 64, seed: int = 0, scale: float = 1.0, bunches: int = 4,
+                 fwhm_s: float = 1e-6, n_min: int = 10_000, n_max: int = 2_000_000,
+                 n_pulses: int = 10, tail_s: float = 10.0):
+    """The dose-rate sweep of ``dose_rate_sweep`` with every pulse delivered (no window):
+    each of the n_pulses square pulses (period Dp / Dav) arrives as ``bunches`` equally
+    spaced bunches of tracks. Returns (workloads, plans): plans[b] is the (kind, t_end)
+    alternation of ``hybrid_stages`` for train b, ending tail_s after its last pulse."""
+    wls, plans = [], []
+    for desc in dose_rate_sweep(n_trains, seed, int(n_min * scale), int(n_max * scale),
+                                n_pulses=n_pulses, fwhm_s=fwhm_s):
+        L = desc["L"]
+        n_tracks = max(2, int(round(160 * (L / 5000.0) ** 2)))
+        per_track = max(1, desc["species_per_pulse"] // n_tracks)
+        pulses = []
+        for k in range(n_pulses):
+            t0 = k * desc["period_s"]
+            for q in range(bunches):
+                pulses.append(track_pulse(max(1, n_tracks // bunches), L, per_track, desc["seed"],
+                                          t0=t0 + fwhm_s * q / bunches, stream=10_000 + 100 * k + q))
+        wls.append(Workload(f"hybrid{desc['train']}", L, pulses,
+                            Schedule(dt_min=1e-11, dt_max=1e-7, dt_growth=LOG_GROWTH_20_PER_DECADE),
+                            t_end=(n_pulses - 1) * desc["period_s"] + fwhm_s + tail_s))
+        plans.append(hybrid_stages(n_pulses, desc["period_s"], fwhm_s, tail_s))
+    return wls, plans
+
+
+def dose_series(avg_dose_rates=(1.0, 1e4), pulse_dose_rate: float = 1e6,
+                n_pulses=(1, 5, 10, 15, 20), species_per_pulse: int = 100_000,
+                fwhm_s: float = 1e-6, bunches: int = 4, tail_s: float = 10.0, seed: int = 0):
+    """Separate irradiations of 1, 5, 10, 15 and 20 pulses at each average dose rate, each
+    followed by tail_s of beam-off (Fig. Concentration-Dose: post-irradiation H2O2 after
+    1-20 Gy). One train per (dose rate, pulse count); the box holds species_per_pulse
+    per pulse at the density of the sweep, so each pulse deposits about
+    pulse_dose_rate * fwhm_s of dose. Returns (workloads, plans, meta) with meta[b] =
+    {"avg_dose_rate", "n_pulses", "period_s"}."""
+    L = 5000.0 * (species_per_pulse / 3e5) ** (1.0 / 3.0)
+    n_tracks = max(2, int(round(160 * (L / 5000.0) ** 2)))
+    per_track = max(1, species_per_pulse // n_tracks)
+    wls, plans, meta = [], [], []
+    for i, dav in enumerate(avg_dose_rates):
+        T = pulse_dose_rate * fwhm_s / dav
+        for n in n_pulses:
+            pulses = []
+            for k in range(n):
+                for q in range(bunches):
+                    pulses.append(track_pulse(max(1, n_tracks // bunches), L, per_track, seed + 7 * i,
+                                              t0=k * T + fwhm_s * q / bunches, stream=10_000 + 100 * k + q))
+            wls.append(Workload(f"dose{i}_{n}", L, pulses,
+                                Schedule(dt_min=1e-11, dt_max=1e-7, dt_growth=LOG_GROWTH_20_PER_DECADE),
+                                t_end=(n - 1) * T + fwhm_s + tail_s))
+            plans.append(hybrid_stages(n, T, fwhm_s, tail_s))
+            meta.append({"avg_dose_rate": float(dav), "n_pulses": int(n), "period_s": float(T)})
+    return wls, plans, meta
+
+
 def batched_sweep(n_trains: int = 64, seed: int = 0, scale: float = 1.0, t_sim: float = 10e-6,
                   bunches: int = 4, fwhm_s: float = 1e-6, n_min: int = 10_000,
                   n_max: int = 2_000_000) -> List[Workload]:

@@ -250,3 +250,37 @@ def test_ten_second_tail_at_a_million_species():
     e_ref = H.extents(counts.astype(float), L, 10.0, W.WATER_REACTIONS)
     np.testing.assert_allclose(e[:9], e_ref, rtol=EXT_RTOL, atol=EXT_ATOL)
     assert 0 < steps < 5000
+
+
+def test_pulse_train_driver_matches_reference_per_call():
+    from paper_2509_03313_gb300 import hybrid
+    specs = [(2, 1e-4, 500.0, 31), (3, 3e-5, 700.0, 32)]
+    wls, plans, cfgs, keep = [], [], [], []
+    for b, (n_p, period, L, seed) in enumerate(specs):
+        pulses = W.pulse_train(n_p, period, 1e-6, n_tracks=4, L=L, species_per_track=100, seed=seed)
+        wl = W.Workload(f"drv{b}", L, pulses,
+                        W.Schedule(dt_min=1e-11, dt_max=1e-7, dt_growth=W.LOG_GROWTH_20_PER_DECADE),
+                        t_end=0.0)
+        wls.append(wl)
+        plans.append(W.hybrid_stages(n_p, period, 1e-6, tail_s=0.5))
+        c, k = _config(wl, seed, chem.CHEM_FP64, train_id=b)
+        cfgs.append(c)
+        keep.append(k)
+    ctx = chem.chem_batch_init(cfgs)
+    try:
+        for b, wl in enumerate(wls):
+            for p in wl.pulses:
+                chem.chem_batch_inject(ctx, b, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        run = hybrid.run_plans(ctx, plans)
+    finally:
+        chem.chem_destroy(ctx)
+    for b, (wl, plan) in enumerate(zip(wls, plans)):
+        o = sbs.from_workload(wl, seed=specs[b][3], train_id=b)
+        for i, (kind, t) in enumerate(plan):
+            if kind == "sbs":
+                o.run_until(t)
+            else:
+                o.run_homogeneous(t)
+            np.testing.assert_array_equal(run["counts"][i, b], o.counts(), err_msg=f"train {b} call {i}")
+            np.testing.assert_array_equal(run["events"][i, b], o.events_total)
+            assert run["t"][i, b] == o.t
