@@ -1,0 +1,71 @@
+"""Pins of the well-mixed stochastic reference (Gillespie's direct method) used by the
+volume-scaling study: exponential waiting times of single pairs (A + B and A + A with the
+tabulated 2k), the mean of many molecules against the closed-form rate equations, and
+exact conservation of charge and atoms with the water balance."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import gillespie as G
+from oracle import sbs
+from paper_2509_03313_gb300 import workloads as W
+
+L = 100.0
+NV = sbs.N_AVOGADRO * L ** 3 * 1e-24
+
+
+def _first_event_times(n0, rx, seeds):
+    ts = np.logspace(-12, 0, 400)
+    out = []
+    for s in seeds:
+        counts, _, _ = G.ssa(n0, L, rx, ts, seed=s)
+        moved = np.nonzero(np.any(counts != counts[0], axis=1))[0]
+        out.append(ts[moved[0]] if moved.size else np.inf)
+    return np.array(out), ts
+
+
+def test_single_pair_waits_exponentially():
+    k = 2.0e10
+    times, ts = _first_event_times([1, 1, 0], [(0, 1, k, (2,), 0)], range(400))
+    rate = k / NV
+    # the first sampled time after the event: compare the empirical CDF on the grid
+    cdf = np.array([(times <= t).mean() for t in ts])
+    assert np.abs(cdf - (1.0 - np.exp(-rate * ts))).max() < 0.09
+
+
+def test_self_pair_rate_is_half_the_tabulated_value_per_pair():
+    k_tab = 2.0e10
+    times, ts = _first_event_times([2, 0], [(0, 0, k_tab, (1,), 0)], range(400))
+    rate = k_tab / NV  # (k_tab / 2) / (N_A V) * 2 * 1
+    cdf = np.array([(times <= t).mean() for t in ts])
+    assert np.abs(cdf - (1.0 - np.exp(-rate * ts))).max() < 0.09
+
+
+def test_many_molecules_follow_the_rate_equations():
+    k = 1.0e10
+    a0, b0 = 3000, 1000
+    T = np.array([1e-8, 1e-7, 1e-6])
+    kappa = k / NV
+    runs = np.array([G.ssa([a0, b0, 0], L, [(0, 1, k, (2,), 0)], T, seed=s)[0][:, 1] for s in range(20)])
+    d = a0 - b0
+    b_ode = d / ((a0 / b0) * np.exp(kappa * d * T) - 1.0)
+    mean, sem = runs.mean(axis=0), runs.std(axis=0, ddof=1) / math.sqrt(runs.shape[0])
+    assert np.all(np.abs(mean - b_ode) <= 4 * sem + 0.01 * b_ode + 0.5)
+    # A + A: 1/n = 1/n0 + 2 kappa' t with kappa' = (k_tab/2)/(N_A V), up to the n(n-1) term
+    runs = np.array([G.ssa([4000, 0], L, [(0, 0, k, (1,), 0)], T, seed=s)[0][:, 0] for s in range(20)])
+    n_ode = 4000 / (1.0 + 2.0 * (0.5 * k / NV) * 4000 * T)
+    mean, sem = runs.mean(axis=0), runs.std(axis=0, ddof=1) / math.sqrt(runs.shape[0])
+    assert np.all(np.abs(mean - n_ode) <= 4 * sem + 0.01 * n_ode + 0.5)
+
+
+def test_water_table_conserves_charge_and_atoms():
+    n0 = W.MIX_COUNTS
+    counts, water, events = G.ssa(n0, 200.0, W.WATER_REACTIONS, [1e-9, 1e-7, 1e-5], seed=3)
+    for row in counts:
+        assert int(row @ W.CHARGE) == int(n0 @ W.CHARGE)
+    last = counts[-1]
+    assert int(last @ W.N_H) + 2 * water == int(n0 @ W.N_H)
+    assert int(last @ W.N_O) + water == int(n0 @ W.N_O)
+    assert events.sum() > 100
