@@ -29,9 +29,15 @@ Where the paper is silent the following readings are used, identically in the li
   seed high word XOR train id), counter = (id, step, 0, tag) for tag 0 and 1, 53-bit
   uniforms, Box-Muller;
 * pair search cutoff R_cut = R + c * sqrt(2 D_AB dt); encounters during the step are
-  caught by the Brownian-bridge probability exp(-(d0 - R)(d1 - R) / (D_AB dt)) of a
-  crossing between the start (d0) and end (d1) separations, accepted against a uniform
-  drawn from counter (id_lo, step, id_hi, 2);
+  caught by the probability that the pair's relative Brownian path, conditioned on its
+  start (d0) and end (d1) separations, touched the reaction sphere:
+  p = (exp(-a) - exp(-b)) / (1 - exp(-b)), a = (d0 - R)(d1 - R) / (D_AB dt),
+  b = d0 d1 / (D_AB dt) (p = 1 when d0 or d1 <= R), accepted against a uniform drawn
+  from counter (id_lo, step, id_hi, 2). This is the ratio of the absorbing-sphere and
+  free Green's functions of the angle-averaged relative motion (the image solution
+  behind Eq. kdiff1 and Eq. PDF0), so the expected number of reactions per step is that
+  of a fully absorbing sphere of radius R, i.e. rate 4 pi R D_AB (1 + R / sqrt(pi D_AB t)),
+  at any dt. For R >> sqrt(D_AB dt) it tends to the planar bridge exp(-a);
 * one reaction per species per step, closest pair first, lower ids breaking ties;
 * products at the diffusion-weighted encounter point, ids assigned in ascending id_lo
   order and table order; products diffuse from the next step;
@@ -129,6 +135,25 @@ def acceptance_uniform(id_lo, id_hi, step: int, key):
     st = np.full_like(id_lo, np.uint64(step & 0xFFFFFFFF))
     c0, c1, _, _ = philox4x32_10((id_lo, st, id_hi, np.full_like(id_lo, np.uint64(2))), key)
     return uniform_closed0(c0, c1)
+
+
+def touch_probability(d0, d1, R, DABdt):
+    """Probability that the relative Brownian path of a pair, started at separation d0
+    and ended at d1 after a step with D_AB dt = DABdt, touched the sphere of radius R,
+    given only those two separations: 1 - G_abs / G_free with the angle-averaged Green's
+    functions of free diffusion and of diffusion outside a fully absorbing sphere (image
+    solutions in r times density), i.e. (exp(-a) - exp(-b)) / (1 - exp(-b)) with
+    a = (d0 - R)(d1 - R) / DABdt, b = d0 d1 / DABdt; 1 when either end is inside. Written
+    as exp(-a) expm1(-c) / expm1(-b), c = b - a = R (d0 + d1 - R) / DABdt."""
+    d0 = np.asarray(d0, dtype=np.float64)
+    d1 = np.asarray(d1, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    with np.errstate(over="ignore", under="ignore", divide="ignore", invalid="ignore"):
+        a = ((d0 - R) * (d1 - R)) / DABdt
+        b = (d0 * d1) / DABdt
+        c = (R * ((d0 + d1) - R)) / DABdt
+        p = np.exp(-a) * (np.expm1(-c) / np.expm1(-b))
+    return np.where((d1 <= R) | (d0 <= R), 1.0, p)
 
 
 def wrap(x, L: float):
@@ -318,9 +343,7 @@ class SBSOracle:
         d1 = np.sqrt(d1sq)
         r0 = r1 - (delta[hi] - delta[lo])
         d0 = np.sqrt(sq_norm(r0))
-        with np.errstate(over="ignore", under="ignore"):
-            p_bridge = np.exp(-((d0 - R) * (d1 - R)) / (self.D_AB[rxn] * dt))
-        p = np.where((d1 <= R) | (d0 <= R), 1.0, p_bridge)
+        p = touch_probability(d0, d1, R, self.D_AB[rxn] * dt)
         u = acceptance_uniform(self.ids[lo], self.ids[hi], self.step, self.key)
         keep = u < p
         return lo[keep], hi[keep], rxn[keep], d1sq[keep], r1[keep]

@@ -250,7 +250,48 @@ def _pairs_on_lattice(n_side, spacing, r0, seed):
     return a, b, n_side * spacing
 
 
-@pytest.mark.parametrize("dt", [1e-12, 1e-11])
+def test_touch_probability_limits():
+    R, Ddt = 0.5, 4.0
+    d0 = np.array([0.6, 1.0, 3.0, 8.0])
+    d1 = np.array([0.7, 2.0, 1.5, 9.0])
+    p = sbs.touch_probability(d0, d1, R, Ddt)
+    planar = np.exp(-(d0 - R) * (d1 - R) / Ddt)
+    assert np.all((p > 0) & (p <= planar))
+    np.testing.assert_allclose(p, sbs.touch_probability(d1, d0, R, Ddt))  # time reversal
+    assert np.all(sbs.touch_probability([0.4, 0.6], [0.6, 0.5], R, Ddt) == 1.0)
+    # a point target is never touched; a sphere much larger than the step looks flat
+    assert np.all(sbs.touch_probability(d0, d1, 1e-12, Ddt) < 1e-11)
+    big = 1000.0
+    np.testing.assert_allclose(sbs.touch_probability(big + d0, big + d1, big, Ddt),
+                               np.exp(-d0 * d1 / Ddt), rtol=5e-3)
+    # decreasing in the end separation
+    q = sbs.touch_probability(1.0, np.linspace(0.6, 10.0, 50), R, Ddt)
+    assert np.all(np.diff(q) < 0)
+
+
+def test_touch_probability_matches_simulated_paths():
+    """Brute force: fine-grained free relative paths from distance d0; the fraction that
+    came within R, binned by end distance, against the formula (discrete monitoring
+    misses a little, so the simulated fraction sits slightly below)."""
+    rng = np.random.default_rng(5)
+    R, D, dt, d0 = 1.0, 1.0, 4.0, 2.0
+    n, sub = 40000, 1000
+    h = dt / sub
+    pos = np.zeros((n, 3))
+    pos[:, 0] = d0
+    hit = np.zeros(n, bool)
+    for _ in range(sub):
+        pos += rng.normal(0.0, math.sqrt(2 * D * h), size=(n, 3))
+        hit |= (pos * pos).sum(axis=1) <= R * R
+    d1 = np.sqrt((pos * pos).sum(axis=1))
+    for lo, hi in ((1.2, 2.0), (2.0, 3.0), (3.0, 4.5), (4.5, 7.0)):
+        m = (d1 >= lo) & (d1 < hi)
+        sim = hit[m].mean()
+        ref = sbs.touch_probability(d0, d1[m], R, D * dt).mean()
+        assert abs(sim - ref) < 4 * math.sqrt(ref * (1 - ref) / m.sum()) + 0.04 * ref, (lo, sim, ref)
+
+
+@pytest.mark.parametrize("dt", [1e-12, 1e-11, 1e-10, 1e-9])
 def test_first_passage_probability_of_one_pair(dt):
     """P(react by t | r0) = (R/r0) erfc((r0 - R) / sqrt(4 D_AB t)) (Eq. PDF0, read with
     the standard sign) for isolated A + B pairs."""
@@ -262,7 +303,7 @@ def test_first_passage_probability_of_one_pair(dt):
     n = a.shape[0]
     o = sbs.SBSOracle(D, rx, L, seed=77, dt_min=dt, dt_max=dt, record=False)
     o.inject(np.r_[np.zeros(n), np.ones(n)].astype(int), np.r_[a, b], np.zeros(2 * n))
-    for t in (0.1e-9, 0.5e-9):
+    for t in ((0.1e-9, 0.5e-9) if dt < 1e-10 else (1e-9, 5e-9)):
         o.run_until(t)
         p_sim = o.events_total[0] / n
         p_exact = (R / r0) * special.erfc((r0 - R) / math.sqrt(4 * 14.6e9 * t))
@@ -277,7 +318,7 @@ def _ode_counts(D, rx, counts0, L, times):
     return c / kinetics.molar(1.0, L)
 
 
-@pytest.mark.parametrize("dt", [5e-12, 1e-10])
+@pytest.mark.parametrize("dt", [5e-12, 1e-10, 2e-9])
 def test_smoluchowski_rate_A_plus_B(dt):
     D = np.array([9.3e9, 5.3e9])
     rx = [(0, 1, 11.0e10, (), 0)]
