@@ -366,6 +366,7 @@ def run_gpu_arm(args):
     # the same sweep with every pulse and the beam-off stages (rate equations), 10 s tail
     hres = None if args.no_hybrid else run_hybrid(args, chem, W, torch, stream, alloc, rank, world, dev,
                                                   tuned=bres.get("autotuned") if bres else None)
+    vres = None if args.no_volume else run_volume_scaling(args, chem, W, torch, stream, alloc, rank, world, dev)
     if rank != 0:
         return 0
     value = ss_all / t_max
@@ -451,6 +452,8 @@ def run_gpu_arm(args):
             line["speedup_batched_fp32l_over_plain_fp64"] = bres["value"] / line["fp64"]["value"]
     if hres is not None:
         line["hybrid"] = hres
+    if vres is not None:
+        line["volume_scaling"] = vres
     line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     return 0
@@ -643,6 +646,83 @@ def run_hybrid(args, chem, W, torch, stream, alloc, rank=0, world=1, device=None
     return out
 
 
+def run_volume_scaling(args, chem, W, torch, stream, alloc, rank=0, world=1, device=None):
+    """Volume-scaling study of Sec. 2.3 on the GPU: one mixture concentration in boxes of
+    0.2, 0.5 and 1.0 um (8, 4 and 2 seeds) followed to 1 ms by the FP32-local SBS in one
+    batched context per rank; mean concentrations per box at 1 ms, their largest
+    relative spread across the boxes, and the ratio of the SBS to the GPU rate equations
+    from the same initial mixture (the paper: SBS above the well-mixed kinetics by up to
+    20 % for H2 and 12 % for H2O2)."""
+    boxes = {200.0: 8, 500.0: 4, 1000.0: 2}
+    trains = [(L, s) for L, n in boxes.items() for s in range(n)]
+    wls_all = [W.volume_scaling(L, seed=100 + s) for L, s in trains]
+    mine = shard_trains([w.n_species for w in wls_all], world)[rank]
+    rows = np.zeros((len(trains), 7))
+    ss, wall = 0, 0.0
+    if mine:
+        cfgs, keep = [], []
+        for b in mine:
+            wl = wls_all[b]
+            sch = wl.schedule
+            n = wl.n_species
+            c, k = chem.make_config(wl.L, wl.D, wl.reactions, seed=300 + b, train_id=b,
+                                    precision=chem.CHEM_FP32_LOCAL, dt_min=sch.dt_min, dt_max=sch.dt_max,
+                                    dt_growth=sch.dt_growth, capacity_species=2 * n + 4096,
+                                    capacity_pending=n, capacity_candidates=max(4096, n),
+                                    stream=stream.cuda_stream, allocator=alloc)
+            cfgs.append(c)
+            keep.append(k)
+        ctx = chem.chem_batch_init(cfgs)
+        try:
+            for i, b in enumerate(mine):
+                p = wls_all[b].pulses[0]
+                chem.chem_batch_inject(ctx, i, p.types, p.xyz, p.t_arrival, p.energy_eV)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            chem.chem_batch_run_until(ctx, [wls_all[b].t_end for b in mine])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            for i, b in enumerate(mine):
+                tal = chem.chem_batch_tally(ctx, i, 7, 9)
+                L = trains[b][0]
+                rows[b] = tal["counts"][:7] / (6.02214076e23 * L ** 3 * 1e-24)
+                ss += tal["species_steps"]
+        finally:
+            chem.chem_destroy(ctx)
+    ss_all, wall_all, _ = gather_batched(ss, wall, np.zeros(1, np.int64), device=device)
+    rows = sum_over_ranks(rows, device=device)
+    # the rate equations on the GPU from the 1 um box's initial mixture (deterministic)
+    wl = W.volume_scaling(1000.0, seed=100)
+    cfg, keep = chem.make_config(wl.L, wl.D, wl.reactions, seed=5, capacity_species=2 * wl.n_species,
+                                 capacity_pending=wl.n_species, capacity_candidates=4096,
+                                 stream=stream.cuda_stream, allocator=alloc)
+    ctx = chem.chem_init(cfg)
+    try:
+        p = wl.pulses[0]
+        chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        chem.chem_run_homogeneous(ctx, wl.t_end)
+        ode = chem.chem_tally(ctx, 7, 9)["counts"][:7] / (6.02214076e23 * wl.L ** 3 * 1e-24)
+    finally:
+        chem.chem_destroy(ctx)
+    means = {}
+    for L in boxes:
+        idx = [b for b, (LL, _) in enumerate(trains) if LL == L]
+        means[L] = rows[idx].mean(axis=0)
+    m = np.array([means[L] for L in boxes])
+    # species with at least 20 molecules per smallest box (fewer is counting noise)
+    big = m.min(axis=0) > 20.0 / (6.02214076e23 * min(boxes) ** 3 * 1e-24)
+    spread = float(((m.max(axis=0) - m.min(axis=0)) / m.mean(axis=0))[big].max()) if big.any() else None
+    return {"value": ss_all / wall_all if wall_all > 0 else None, "unit": UNIT, "wall_s": wall_all,
+            "boxes_nm": list(boxes), "seeds": list(boxes.values()),
+            "conc_1ms_M": {f"{L:g}": [float(v) for v in means[L]] for L in boxes},
+            "max_rel_spread_across_boxes": spread,
+            "spread_species": "those with >= 20 molecules in the 0.2 um box at 1 ms",
+            "sbs_over_rate_equations_1ms": {"H2": float(means[1000.0][5] / ode[5]),
+                                            "H2O2": float(means[1000.0][6] / ode[6])},
+            "workload": "2,000 species (e 600, OH 600, H 120, H3O+ 600, OH- 80) per (0.2 um)^3, boxes of "
+                        "0.2/0.5/1.0 um, log dt from 1 ps to 1 ms, FP32-local"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -670,6 +750,7 @@ def main():
     ap.add_argument("--no-hybrid", action="store_true")
     ap.add_argument("--hybrid-scale", type=float, default=1.0)
     ap.add_argument("--no-dose-series", action="store_true")
+    ap.add_argument("--no-volume", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference_arm(args)

@@ -149,7 +149,9 @@ chem_status chem_inject_pulse(chem_ctx* ctx, int64_t n, const int32_t* type, con
 /* Advance to t_end_s (the last step is trimmed to land on it). Each step: release
  * arrived species, diffuse with periodic wrap (Eq. 1), rebuild the spatial hash, find
  * reactive pairs within the cutoff under the minimum image (Eq. 2) and accept them with
- * the Brownian-bridge probability, keep one reaction per species (closest pair first,
+ * the probability that their relative path touched the reaction sphere during the step
+ * given both separations (the absorbing-sphere kinetics of Eq. kdiff1 in expectation at
+ * any dt), keep one reaction per species (closest pair first,
  * lower ids break ties), write products and tallies, advance the FP64 clock.
  * Blocks until the device has finished. */
 chem_status chem_run_until(chem_ctx* ctx, double t_end_s);

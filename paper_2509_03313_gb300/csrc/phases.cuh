@@ -107,10 +107,20 @@ __device__ __forceinline__ double pair_uniform(uint32_t id_lo, uint32_t id_hi, u
   return __dmul_rn(static_cast<double>(u53(c.x, c.y)), TWO_POW_M53);
 }
 
-// Brownian-bridge encounter probability (p = 1 when either end is inside R).
+// Probability that the pair's relative Brownian path touched the reaction sphere during
+// the step, given its start and end separations d0, d1 (p = 1 when either is inside R):
+// 1 - G_abs / G_free for the angle-averaged relative motion (image solutions of r times
+// the density, outside a fully absorbing sphere and free), i.e.
+// (exp(-a) - exp(-b)) / (1 - exp(-b)) with a = (d0 - R)(d1 - R) / (D_AB dt) and
+// b = d0 d1 / (D_AB dt), evaluated as exp(-a) expm1(-c) / expm1(-b), c = b - a =
+// R (d0 + d1 - R) / (D_AB dt). Its expectation is the absorbing-sphere rate behind
+// Eq. kdiff1 at any dt; for R >> sqrt(D_AB dt) it is the planar bridge exp(-a).
 __device__ __forceinline__ double bridge_p(double d0, double d1, double R, double DABdt) {
   if (d1 <= R || d0 <= R) return 1.0;
-  return exp(__ddiv_rn(-__dmul_rn(__dsub_rn(d0, R), __dsub_rn(d1, R)), DABdt));
+  const double a = __ddiv_rn(__dmul_rn(__dsub_rn(d0, R), __dsub_rn(d1, R)), DABdt);
+  const double b = __ddiv_rn(__dmul_rn(d0, d1), DABdt);
+  const double c = __ddiv_rn(__dmul_rn(R, __dsub_rn(__dadd_rn(d0, d1), R)), DABdt);
+  return __dmul_rn(exp(-a), __ddiv_rn(expm1(-c), expm1(-b)));
 }
 
 __device__ __forceinline__ int cell_index(double x, double halfL, double inv_h, int n) {
@@ -724,14 +734,15 @@ __device__ __forceinline__ void emit_candidate(const Dev& d, uint32_t s_lo, uint
   d.cand[c] = cd;
 }
 
-// Accept iff u < p with p evaluated in FP64 from the FP32 squared distances:
-// p = 1 when d0 <= R or d1 <= R, else exp(-(d0 - R)(d1 - R) / (D_AB dt)). The uniform
-// u = (w0:w1 >> 11) 2^-53 of the pair's Philox block lies in [k 2^-24, (k + 1) 2^-24)
-// with k = w0 >> 8, bounds that are exact in FP32. An FP32 estimate of p decides
-// whenever those bounds clear it by twice its error bound (FP32 rounding of d0, d1, R
-// and of the products, cancellation in d - R, and the documented __expf error);
-// otherwise u and p are formed in FP64, so the outcome is always that of the FP64 test.
-// The fast path uses no FP64 arithmetic (a slow pipe on this part).
+// Accept iff u < p with p = bridge_p evaluated in FP64 from the FP32 squared distances.
+// The uniform u = (w0:w1 >> 11) 2^-53 of the pair's Philox block lies in
+// [k 2^-24, (k + 1) 2^-24) with k = w0 >> 8, bounds that are exact in FP32. An FP32
+// estimate of p decides whenever those bounds clear it by twice its error bound (FP32
+// rounding of d0, d1, R and of the products, cancellation in d - R, the documented
+// __expf error, and a few ulp for the two expm1f and their quotient, whose arguments
+// suffer no cancellation since d0 + d1 - R > R); otherwise u and p are formed in FP64,
+// so the outcome is always that of the FP64 test. The fast path uses no FP64
+// arithmetic (a slow pipe on this part).
 __device__ __forceinline__ bool accept_f32(float d0sq, float d1sq, int r, const Tables& tb, const Train& tr,
                                           uint32_t id_lo, uint32_t id_hi) {
   const float d1f = sqrtf(d1sq), d0f = sqrtf(d0sq);
@@ -742,10 +753,11 @@ __device__ __forceinline__ bool accept_f32(float d0sq, float d1sq, int r, const 
     const float a = d0f - Rf, b = d1f - Rf, inv = tr.inv_ddt_f[r];
     const float x = a * b * inv;
     if (x > 60.f) {
-      if ((w.x | (w.y >> 11)) != 0u) return false;  // p < 1e-26 < 2^-53 <= u
+      if ((w.x | (w.y >> 11)) != 0u) return false;  // p <= exp(-a) < 1e-26 < 2^-53 <= u
     } else {
-      const float p = __expf(-x);
-      const float err = 1.2e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x);
+      const float cb = d0f * d1f * inv, cc = Rf * (d0f + d1f - Rf) * inv;
+      const float p = __expf(-x) * (expm1f(-cc) / expm1f(-cb));
+      const float err = 1.2e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x) + 3e-6f;
       const float band = 2.f * err * p;
       const float ulo = static_cast<float>(w.x >> 8) * 5.9604645e-8f;  // k 2^-24 <= u
       if (ulo >= p + band) return false;
@@ -772,8 +784,9 @@ __device__ __forceinline__ bool accept_f64(double d0sq, double d1sq, int r, cons
     if (x > 60.f) {
       if ((w.x | (w.y >> 11)) != 0u) return false;
     } else {
-      const float p = __expf(-x);
-      const float err = 2.4e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x);
+      const float cb = d0f * d1f * inv, cc = Rf * (d0f + d1f - Rf) * inv;
+      const float p = __expf(-x) * (expm1f(-cc) / expm1f(-cb));
+      const float err = 2.4e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x) + 4e-6f;
       const float band = 2.f * err * p;
       const float ulo = static_cast<float>(w.x >> 8) * 5.9604645e-8f;
       if (ulo >= p + band) return false;

@@ -317,6 +317,20 @@ def dose_series(avg_dose_rates=(1.0, 1e4), pulse_dose_rate: float = 1e6,
     return wls, plans, meta
 
 
+def volume_scaling(L: float, seed: int, counts_at_200nm: Sequence[int] = MIX_COUNTS,
+                   t_end: float = 1e-3, dt_min: float = 1e-12, dt_max: float = 1.5e-8) -> Workload:
+    """Volume-scaling study (Sec. 2.3, verification of the periodic boundaries): one
+    homogeneous mixture concentration in cubes of side L (0.2, 0.5 and 1.0 um), i.e.
+    counts_at_200nm scaled by (L / 200 nm)^3 (2,000 species at 0.2 um, 250,000 at 1 um),
+    followed to t_end = 1 ms with log-growing dt from 1 ps up to dt_max. The default
+    dt_max is just below the smallest box's cap (every cutoff <= L/3 allows 1.6e-8 s at
+    0.2 um), so all boxes take the same steps and only their size differs."""
+    counts = np.round(np.asarray(counts_at_200nm, dtype=np.float64) * (L / 200.0) ** 3).astype(np.int64)
+    pulse = uniform_mixture(counts, L, seed, energy_eV=float(counts.sum()) * 100.0 / 6.0)
+    return Workload(f"volume_L{int(L)}", L, [pulse],
+                    Schedule(dt_min=dt_min, dt_max=dt_max, dt_growth=LOG_GROWTH_20_PER_DECADE), t_end=t_end)
+
+
 def batched_sweep(n_trains: int = 64, seed: int = 0, scale: float = 1.0, t_sim: float = 10e-6,
                   bunches: int = 4, fwhm_s: float = 1e-6, n_min: int = 10_000,
                   n_max: int = 2_000_000) -> List[Workload]:

@@ -220,7 +220,9 @@ def test_fp32_local_stage_conserves_and_counts_whole_events():
             chem.chem_run_homogeneous(ctx, t)
             after = chem.chem_tally(ctx, 7, 9)
             e, E, steps = chem.chem_batch_homogeneous_report(ctx, 0)
-            assert np.all(np.abs(E[:9] - e[:9]) <= 1.0)
+            # rounding moves an extent by less than one event; take-backs only lower it
+            assert np.all(E[:9] <= np.ceil(np.maximum(e[:9], 0.0)))
+            assert np.all(E[:9] >= 0)
             np.testing.assert_array_equal(after["counts"][:7], before["counts"][:7] + nu @ E[:9])
             np.testing.assert_array_equal(after["events"][:9], before["events"][:9] + E[:9])
         # the tally's water balance is internal; charge needs none

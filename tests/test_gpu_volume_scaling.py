@@ -1,0 +1,118 @@
+"""Volume-scaling study (Sec. 2.3): the SBS with periodic boundaries must give the same
+concentrations in boxes of 0.2, 0.5 and 1.0 um (no finite-size effect, pin P7), stay
+close to a well-mixed stochastic simulation (the paper's Kinetiscope comparison, here an
+independent Gillespie implementation; the paper saw up to 20 % for H2 and 12 % for H2O2 at
+1 ms), and the GPU rate equations must agree with that stochastic simulation within 1 %
+(the paper's NumODE vs Kinetiscope check)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import gillespie as G
+from oracle import sbs
+from paper_2509_03313_gb300 import chem, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+BOXES = {200.0: 8, 500.0: 4, 1000.0: 2}   # box side (nm): seeds
+CHECK = [1e-7, 1e-6, 1e-5, 1e-4, 1e-3]
+
+
+def _molar(counts, L):
+    return np.asarray(counts, float) / (sbs.N_AVOGADRO * L ** 3 * 1e-24)
+
+
+@pytest.fixture(scope="module")
+def sbs_runs():
+    import torch
+    trains = [(L, s) for L, n in BOXES.items() for s in range(n)]
+    wls = [W.volume_scaling(L, seed=100 + s) for L, s in trains]
+    cfgs, keep = [], []
+    for b, wl in enumerate(wls):
+        sch = wl.schedule
+        n = wl.n_species
+        c, k = chem.make_config(
+            wl.L, wl.D, wl.reactions, seed=300 + b, train_id=b, precision=chem.CHEM_FP32_LOCAL,
+            dt_min=sch.dt_min, dt_max=sch.dt_max, dt_growth=sch.dt_growth, capacity_species=2 * n + 4096,
+            capacity_pending=n, capacity_candidates=max(4096, n), stream=torch.cuda.current_stream().cuda_stream,
+            allocator=chem.torch_allocator(0))
+        cfgs.append(c)
+        keep.append(k)
+    ctx = chem.chem_batch_init(cfgs)
+    conc = np.zeros((len(CHECK), len(trains), 7))
+    try:
+        for b, wl in enumerate(wls):
+            p = wl.pulses[0]
+            chem.chem_batch_inject(ctx, b, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        for i, t in enumerate(CHECK):
+            chem.chem_batch_run_until(ctx, [t] * len(trains))
+            for b, (L, _) in enumerate(trains):
+                tal = chem.chem_batch_tally(ctx, b, 7, 9)
+                assert tal["t"] == t
+                conc[i, b] = _molar(tal["counts"][:7], L)
+    finally:
+        chem.chem_destroy(ctx)
+    return trains, conc
+
+
+def _box_stats(trains, conc, L):
+    idx = [b for b, (LL, _) in enumerate(trains) if LL == L]
+    c = conc[:, idx, :]
+    return c.mean(axis=1), c.std(axis=1, ddof=1) / math.sqrt(len(idx))
+
+
+def test_concentrations_do_not_depend_on_the_box(sbs_runs):
+    trains, conc = sbs_runs
+    c_small, e_small = _box_stats(trains, conc, 200.0)
+    one = _molar(1.0, 200.0)
+    bad = []
+    for L in (500.0, 1000.0):
+        c, e = _box_stats(trains, conc, L)
+        for i, t in enumerate(CHECK):
+            for sp in range(7):
+                if c_small[i, sp] <= 20 * one:  # at least 20 molecules in the smallest box
+                    continue
+                diff = abs(c[i, sp] - c_small[i, sp])
+                bound = 4 * math.hypot(e[i, sp], e_small[i, sp]) + 0.03 * c_small[i, sp]
+                if diff > bound:
+                    bad.append((L, t, W.SPECIES[sp], c_small[i, sp], c[i, sp], diff / c_small[i, sp]))
+    assert not bad, bad
+
+
+def test_sbs_stays_close_to_the_well_mixed_stochastic_simulation(sbs_runs):
+    trains, conc = sbs_runs
+    c_sbs, _ = _box_stats(trains, conc, 500.0)
+    wl = W.volume_scaling(500.0, seed=100)
+    n0 = np.bincount(wl.pulses[0].types, minlength=7)
+    ssa = np.array([G.ssa(n0, 500.0, W.WATER_REACTIONS, CHECK, seed=s)[0] for s in range(3)])
+    c_ssa = _molar(ssa.mean(axis=0), 500.0)
+    last = CHECK.index(1e-3)
+    for sp in (W.H2, W.H2O2):
+        ratio = c_sbs[last, sp] / c_ssa[last, sp]
+        assert 0.75 < ratio < 1.33, (W.SPECIES[sp], ratio)
+
+
+def test_gpu_rate_equations_match_the_stochastic_simulation():
+    import torch
+    wl = W.volume_scaling(500.0, seed=100)
+    n0 = np.bincount(wl.pulses[0].types, minlength=7)
+    cfg, keep = chem.make_config(wl.L, wl.D, wl.reactions, seed=5, capacity_species=2 * wl.n_species,
+                                 capacity_pending=wl.n_species, capacity_candidates=4096,
+                                 stream=torch.cuda.current_stream().cuda_stream,
+                                 allocator=chem.torch_allocator(0))
+    ctx = chem.chem_init(cfg)
+    ode = []
+    try:
+        p = wl.pulses[0]
+        chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        for t in CHECK:
+            chem.chem_run_homogeneous(ctx, t)
+            ode.append(chem.chem_tally(ctx, 7, 9)["counts"][:7])
+    finally:
+        chem.chem_destroy(ctx)
+    ode = np.array(ode, float)
+    ssa = np.array([G.ssa(n0, 500.0, W.WATER_REACTIONS, CHECK, seed=s)[0] for s in range(4)], float)
+    mean, sem = ssa.mean(axis=0), ssa.std(axis=0, ddof=1) / 2.0
+    big = mean > 200
+    assert np.all(np.abs(ode - mean)[big] <= (0.01 * mean + 4 * sem + 2.0)[big])
