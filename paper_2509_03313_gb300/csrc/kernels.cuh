@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256, 4) k_search(const __grid_constant__ Dev d
 constexpr int TPS_WARPS = 4;  // warps per CTA of the one-thread-per-species search
 
 template <bool F32L>
-__global__ void __launch_bounds__(32 * TPS_WARPS, F32L ? 7 : 5) k_search_tps(const __grid_constant__ Dev d) {
+__global__ void __launch_bounds__(32 * TPS_WARPS, F32L ? 6 : 5) k_search_tps(const __grid_constant__ Dev d) {
   __shared__ TpsSmem<F32L, TPS_WARPS> sm;
   phase_search_tps<F32L, TPS_WARPS>(d, sm);
 }

@@ -266,11 +266,16 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     const int n_max = tr.n_max, fj = tr.free_jump;
     int n_ref = tr.n_ref;
     const double rcmax = __longlong_as_double(static_cast<long long>(sb.rcmax_bits[b]));
-    // finest admissible grid: cells at least the largest cutoff (with slack)
-    int n_target = n_max;
+    // finest admissible grid: cells at least the largest cutoff (with slack), or at least
+    // half of it when the pair search may look two cells out (then at least 5 cells)
+    int n_target = n_max, n_one = n_max;
     if (rcmax > 0.0) {
-      const float nf = floorf(static_cast<float>(L) / (static_cast<float>(rcmax) * CELL_SLACK_F));
-      n_target = max(3, min(n_max, static_cast<int>(fminf(nf, 1048576.f))));
+      const float cut = static_cast<float>(rcmax) * CELL_SLACK_F;
+      const float nf1 = floorf(static_cast<float>(L) / cut);
+      const float nf2 = floorf(2.f * static_cast<float>(L) / cut);
+      n_one = max(3, min(n_max, static_cast<int>(fminf(nf1, 1048576.f))));
+      const int n_two = min(n_max, static_cast<int>(fminf(nf2, 1048576.f)));
+      n_target = (d.max_reach >= 2 && n_two >= 5) ? n_two : n_one;
     }
     if (n_ref == 0) {  // first step after init or reset
       n_ref = n_target;
@@ -284,9 +289,24 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
       if (n > n_target) n = max(3, (5 * n_target) / 6);
       else if (2 * n < n_target) n = n_target;
     }
+    // cells the search looks out: 1 when a cell covers the largest cutoff; 2 needs at
+    // least 5 cells per axis (no cell met twice) and cells of half the cutoff
+    int reach = 1;
+    if (!fj && rcmax > 0.0) {
+      const double cut = rcmax * static_cast<double>(CELL_SLACK_F);
+      const double hn = L / static_cast<double>(n);
+      if (hn < cut) {
+        if (d.max_reach >= 2 && n >= 5 && 2.0 * hn >= cut) {
+          reach = 2;
+        } else {
+          n = n_one;
+        }
+      }
+    }
     const double h = __ddiv_rn(L, static_cast<double>(n));
     const double inv_h = __dmul_rn(static_cast<double>(n), inv_L);
     tr.n = n;
+    tr.reach = reach;
     tr.h = h;
     tr.inv_h = inv_h;
     tr.hf = static_cast<float>(h);
@@ -653,6 +673,37 @@ __device__ void phase_gather(const Dev& d) {
 // the half shell are flattened into one neighbour list; lanes stride over it (coalesced
 // loads) and each lane tests its neighbour against every home species (shared-memory
 // broadcast). With at least 3 cells per axis each unordered pair is visited once.
+
+// Half-shell offsets within two cells: entry 0 is the own cell, 1..13 the cells one away
+// in fwd_offset's order, 14..62 the cells two away; each keeps the offsets (dz, dy, dx)
+// that are lexicographically positive, so every unordered pair of cells is met once.
+struct FwdOffsets {
+  signed char x[N_FWD2], y[N_FWD2], z[N_FWD2];
+  int count;
+};
+constexpr FwdOffsets make_fwd_offsets() {
+  FwdOffsets t{};
+  int k = 1;
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) { t.x[k] = static_cast<signed char>(dx); t.y[k] = static_cast<signed char>(dy); t.z[k] = 1; ++k; }
+  for (int dx = -1; dx <= 1; ++dx) { t.x[k] = static_cast<signed char>(dx); t.y[k] = 1; t.z[k] = 0; ++k; }
+  t.x[k] = 1; t.y[k] = 0; t.z[k] = 0; ++k;
+  for (int dz = 0; dz <= 2; ++dz)
+    for (int dy = -2; dy <= 2; ++dy)
+      for (int dx = -2; dx <= 2; ++dx) {
+        const bool pos = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+        const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy;
+        const int m = ax > ay ? (ax > dz ? ax : dz) : (ay > dz ? ay : dz);
+        if (pos && m == 2) {
+          t.x[k] = static_cast<signed char>(dx); t.y[k] = static_cast<signed char>(dy);
+          t.z[k] = static_cast<signed char>(dz); ++k;
+        }
+      }
+  t.count = k;
+  return t;
+}
+static_assert(make_fwd_offsets().count == N_FWD2, "62 forward cells within two cells");
+static __constant__ FwdOffsets c_fwd = make_fwd_offsets();
 
 // Half-shell offsets: 0 = own cell, 1..9 dz = +1, 10..12 (dz, dy) = (0, +1), 13 (0, 0, +1).
 __device__ __forceinline__ void fwd_offset(int k, int& dx, int& dy, int& dz) {
@@ -1077,6 +1128,8 @@ struct TpsSmem {
   uint32_t rs[W][N_FWD][32];  // per lane: its non-empty neighbour ranges [rs, re) ...
   uint32_t re[W][N_FWD][32];
   uint8_t rk[W][N_FWD][32];   // ... and their half-shell offsets
+  unsigned long long km[W][32];  // per lane: cells still to look up (bit 0 own cell, 1..62 forward)
+  uint32_t cl[W][32];         // per lane: its home's cell
   TpsQueue<F32L> q[W];
 };
 
@@ -1200,17 +1253,16 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
     if (__any_sync(0xffffffffu, home)) {
       // this lane's non-empty ranges: the own cell's later slots, then the forward cells
       // within reach that are occupied (bit test in the L2-resident bitmap, then their
-      // 16-byte entries)
+      // 16-byte entries), collected and walked in batches of at most N_FWD ranges
       uint32_t* rs_l = &sm.rs[wib][0][lane];
       uint32_t* re_l = &sm.re[wib][0][lane];
       uint8_t* rk_l = &sm.rk[wib][0][lane];
-      int nr = 0;
-      uint32_t kmask = 0;  // forward cells (bits 1..13) within reach of this home
-      int ix = 0, iy = 0, iz = 0;
+      // bit 0: the own cell's later slots; bits 1..62: forward cells within reach
+      unsigned long long kmask = 0ull;
       if (home) {
+        int ix, iy, iz;
         cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
-        const uint32_t own_end = static_cast<uint32_t>(d.cell_info[cell].y);
-        if (s + 1u < own_end) { rs_l[0] = s + 1u; re_l[0] = own_end; rk_l[0] = 0; nr = 1; }
+        if (s + 1u < static_cast<uint32_t>(d.cell_info[cell].y)) kmask = 1ull;
         // a forward cell whose nearest point is farther from the home than the largest
         // cutoff of the home's type holds no partner and is not looked up (the gaps are
         // taken 1e-5 of a cell short, which covers every rounding of the offsets)
@@ -1228,62 +1280,78 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
         for (int t = 0; t < MAXT; ++t) rcmax2 = fmaxf(rcmax2, static_cast<float>(rc2[t]));
         rcmax2 *= 1.0001f;
         auto gap = [&](int o, float of) {
-          const float g = o > 0 ? hcell - of : (o < 0 ? of : 0.f);
+          const float g = o > 0 ? static_cast<float>(o) * hcell - of
+                                : (o < 0 ? of + static_cast<float>(-o - 1) * hcell : 0.f);
           return fmaxf(g - eps, 0.f);
         };
-#pragma unroll
-        for (int k = 1; k < N_FWD; ++k) {
-          int ox, oy, oz;
-          fwd_offset(k, ox, oy, oz);
-          const float gx = gap(ox, ofx), gy = gap(oy, ofy), gz = gap(oz, ofz);
-          if (gx * gx + gy * gy + gz * gz <= rcmax2) kmask |= 1u << k;
+        const int n_fwd = tr.reach == 2 ? N_FWD2 : N_FWD;
+        for (int k = 1; k < n_fwd; ++k) {
+          const float gx = gap(c_fwd.x[k], ofx), gy = gap(c_fwd.y[k], ofy), gz = gap(c_fwd.z[k], ofz);
+          if (gx * gx + gy * gy + gz * gz <= rcmax2) kmask |= 1ull << k;
         }
       }
-      // look up only the cells within reach (warp-uniform loop over each lane's set bits)
-      while (__any_sync(0xffffffffu, kmask != 0u)) {
-        if (kmask != 0u) {
-          const int k = __ffs(kmask) - 1;
-          kmask &= kmask - 1u;
-          int ox, oy, oz;
-          fwd_offset(k, ox, oy, oz);
-          const int n = tr.n;
-          const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, ox, n), step_cell(iy, oy, n),
-                                                         step_cell(iz, oz, n), tr.cb);
-          if ((d.occ[nc >> 5] >> (nc & 31u)) & 1u) {
-            const int4 ci = d.cell_info[nc];
-            if (static_cast<uint32_t>(ci.z) == epoch && ci.y > ci.x) {
-              rs_l[32 * nr] = static_cast<uint32_t>(ci.x);
-              re_l[32 * nr] = static_cast<uint32_t>(ci.y);
-              rk_l[32 * nr] = static_cast<uint8_t>(k);
-              ++nr;
-            }
-          }
-        }
-      }
-      // walk the ranges as one flattened list, four neighbours per iteration whose loads
-      // are in flight together; lanes of one cell stay in step (broadcast loads). The
-      // home state is per lane and movable: a lane that has finished its own list takes
-      // the second half of another lane's current range (home data and all), so that
-      // lanes with few neighbours do not idle while one lane walks a dense cell.
-      int ri = 0;
-      uint32_t j = 0, je = 0;
-      float cx = 0.f, cy = 0.f, cz = 0.f;
+      // kept in shared memory while the ranges are walked (registers are the walk's)
+      sm.km[wib][lane] = kmask;
+      sm.cl[wib][lane] = cell;
+      // the walk's home state is per lane and movable: a lane that has finished its own
+      // list takes the second half of another lane's current range (home data and all),
+      // so that lanes with few neighbours do not idle while one lane walks a dense cell
       uint32_t hs = s, htid = tid_i;
       int hb = b;
       float4 hv = vi;
       double hx = xi, hy = yi, hz = zi;
       const T* hrow = rc2;
       const Train* htr = &tr;
+      while (__any_sync(0xffffffffu, sm.km[wib][lane] != 0ull)) {
+      int nr = 0;
+      // look up only the cells within reach (warp-uniform loop over each lane's set bits)
+      {
+      unsigned long long kmask = sm.km[wib][lane];
+      const uint32_t cell = sm.cl[wib][lane];
+      while (__any_sync(0xffffffffu, kmask != 0ull && nr < N_FWD)) {
+        if (kmask != 0ull && nr < N_FWD) {
+          const int k = __ffsll(static_cast<long long>(kmask)) - 1;
+          kmask &= kmask - 1ull;
+          if (k == 0) {
+            rs_l[0] = s + 1u;
+            re_l[0] = static_cast<uint32_t>(d.cell_info[cell].y);
+            rk_l[0] = 0;
+            nr = 1;
+          } else {
+            const int n = tr.n;
+            int ix, iy, iz;
+            cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
+            const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, c_fwd.x[k], n), step_cell(iy, c_fwd.y[k], n),
+                                                           step_cell(iz, c_fwd.z[k], n), tr.cb);
+            if ((d.occ[nc >> 5] >> (nc & 31u)) & 1u) {
+              const int4 ci = d.cell_info[nc];
+              if (static_cast<uint32_t>(ci.z) == epoch && ci.y > ci.x) {
+                rs_l[32 * nr] = static_cast<uint32_t>(ci.x);
+                re_l[32 * nr] = static_cast<uint32_t>(ci.y);
+                rk_l[32 * nr] = static_cast<uint8_t>(k);
+                ++nr;
+              }
+            }
+          }
+        }
+      }
+      sm.km[wib][lane] = kmask;
+      }
+      // walk the ranges as one flattened list, four neighbours per iteration whose loads
+      // are in flight together; lanes of one cell stay in step (broadcast loads)
+      int ri = 0;
+      uint32_t j = 0, je = 0;
+      float cx = 0.f, cy = 0.f, cz = 0.f;
       auto open = [&](int r) {
         j = rs_l[32 * r];
         je = re_l[32 * r];
-        int ox, oy, oz;
-        fwd_offset(rk_l[32 * r], ox, oy, oz);
-        cx = ox * tr.hf; cy = oy * tr.hf; cz = oz * tr.hf;
+        const int k = rk_l[32 * r];
+        cx = c_fwd.x[k] * tr.hf; cy = c_fwd.y[k] * tr.hf; cz = c_fwd.z[k] * tr.hf;
       };
       if (nr > 0) open(0);
       while (__any_sync(0xffffffffu, ri < nr)) {
-        const uint32_t idle = __ballot_sync(0xffffffffu, ri >= nr);
+        // a lane with cells still to collect keeps its own home
+        const uint32_t idle = __ballot_sync(0xffffffffu, ri >= nr && sm.km[wib][lane] == 0ull);
         if (idle != 0u) {
           const uint32_t rem = (ri < nr) ? je - j : 0u;
           const uint32_t donors = __ballot_sync(0xffffffffu, rem >= 4u);
@@ -1427,6 +1495,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           }
         }
       }
+      }  // batches of ranges
     }
     c_next = __shfl_sync(0xffffffffu, c_next, 0);
   }
@@ -2054,9 +2123,11 @@ __device__ void phase_products(const Dev& d, ProductsSmem& sm) {
       cell_decode(ca - tr.cell_base, tr.cb, ax_, ay_, az_);
       cell_decode(cc - tr.cell_base, tr.cb, cx_, cy_, cz_);
       int dx = cx_ - ax_, dy = cy_ - ay_, dz = cz_ - az_;
-      dx = dx > 1 ? dx - n : (dx < -1 ? dx + n : dx);
-      dy = dy > 1 ? dy - n : (dy < -1 ? dy + n : dy);
-      dz = dz > 1 ? dz - n : (dz < -1 ? dz + n : dz);
+      // cells of a reacting pair are at most tr.reach apart (with n >= 5 when 2)
+      const int rr = tr.reach;
+      dx = dx > rr ? dx - n : (dx < -rr ? dx + n : dx);
+      dy = dy > rr ? dy - n : (dy < -rr ? dy + n : dy);
+      dz = dz > rr ? dz - n : (dz < -rr ? dz + n : dz);
       const float w = tb.Df[tlo] / (tb.Df[tlo] + tb.Df[thi]);
       const float px = a.x + w * (dx * tr.hf + (c.x - a.x));
       const float py = a.y + w * (dy * tr.hf + (c.y - a.y));
