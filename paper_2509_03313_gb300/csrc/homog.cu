@@ -4,13 +4,14 @@
 //
 // For every train the host selected (Train::hx_sel):
 //  1. k_hx_remove marks every particle of the train removed (the next sort drops it);
-//  2. k_hx_integrate, one thread per train, takes the train's species counts n0 as
+//  2. k_hx_integrate, one warp per train, takes the train's species counts n0 as
 //     molecule numbers in the box volume V and integrates the reaction extents e_r
 //     (events): n(e) = n0 + nu e, de_r/dt = kappa_r n_a n_b, kappa_r = k_r / (N_A V), and
 //     (k_tab / 2) / (N_A V) for a self reaction whose tabulated value is 2k. This is Eq. 3
 //     multiplied through by N_A V. The integrator is the extrapolated linearly implicit
 //     Euler method (Deuflhard 1985; Hairer and Wanner, Solving ODEs II, Sec. IV.9) with
-//     the harmonic substep sequence 1..6 and an analytic Jacobian: stiff rate equations
+//     the harmonic substep sequence 1..6 (one lane per column) and an analytic
+//     Jacobian: stiff rate equations
 //     (R9 at 1.1e11 L/mol/s) over 10 s take a few hundred steps;
 //  3. the extents are rounded to whole events without bias, E_r = floor(e_r) +
 //     [u_r < frac(e_r)], u_r from Philox4x32-10 at counter (stage, r, 0, 4); while a
@@ -109,55 +110,81 @@ __device__ void hx_solve(const double (*M)[MAXR], const int* piv, int nr, double
   }
 }
 
-// One extrapolated step of length H from y0: y1 and the scaled error estimate.
-// Column j integrates H with j linearly implicit Euler substeps, (I - hJ) d = h f(y),
-// y += d, with the Jacobian J of y0; the Aitken-Neville table then removes the error
-// terms in h, h^2, ... (the method's expansion is in powers of h).
-__device__ bool hx_step(const Kin& k, const double* y0, double H, double* y1, double* err) {
+// Per-warp shared memory of the integrator: the columns' end values and the step's result.
+struct HxWarpSmem {
+  double col[HX_K][MAXR];
+  double y1[MAXR];
+};
+
+// One extrapolated step of length H from y0, taken by one warp (every lane calls it with
+// the same y0 and H): lane j - 1 integrates H with j linearly implicit Euler substeps,
+// (I - hJ) d = h f(y), y += d, with the Jacobian J of y0 (columns are independent, so the
+// six run side by side); lane 0 then applies the Aitken-Neville table, which removes the
+// error terms in h, h^2, ... (the method's expansion is in powers of h). Returns false
+// (on every lane) when a column is singular or the result is not finite; else y1 and
+// the scaled error estimate on every lane.
+__device__ bool hx_step(const Kin& k, const double* y0, double H, double* y1, double* err, HxWarpSmem& sm,
+                        int lane) {
   const int nr = k.nr;
-  double J[MAXR][MAXR], M[MAXR][MAXR];
-  double f0[MAXR], y[MAXR], f[MAXR];
-  double prev[HX_K][MAXR], cur[HX_K][MAXR];
-  int piv[MAXR];
-  hx_jacobian(k, y0, J);
-  hx_rates(k, y0, f0);
-  for (int j = 1; j <= HX_K; ++j) {
+  bool ok = true;
+  if (lane < HX_K) {
+    const int j = lane + 1;
+    double J[MAXR][MAXR], M[MAXR][MAXR];
+    double y[MAXR], f[MAXR];
+    int piv[MAXR];
+    hx_jacobian(k, y0, J);
     const double h = H / j;
     for (int r = 0; r < nr; ++r)
       for (int s = 0; s < nr; ++s) M[r][s] = (r == s ? 1.0 : 0.0) - h * J[r][s];
-    if (!hx_lu(M, piv, nr)) return false;
-    for (int r = 0; r < nr; ++r) y[r] = y0[r];
-    for (int i = 0; i < j; ++i) {
-      if (i == 0) {
-        for (int r = 0; r < nr; ++r) f[r] = h * f0[r];
-      } else {
+    ok = hx_lu(M, piv, nr);
+    if (ok) {
+      for (int r = 0; r < nr; ++r) y[r] = y0[r];
+      for (int i = 0; i < j; ++i) {
         hx_rates(k, y, f);
         for (int r = 0; r < nr; ++r) f[r] *= h;
+        hx_solve(M, piv, nr, f);
+        for (int r = 0; r < nr; ++r) y[r] += f[r];
       }
-      hx_solve(M, piv, nr, f);
-      for (int r = 0; r < nr; ++r) y[r] += f[r];
+      for (int r = 0; r < nr; ++r) sm.col[lane][r] = y[r];
     }
-    for (int r = 0; r < nr; ++r) cur[0][r] = y[r];
-    for (int l = 0; l + 1 < j; ++l) {
-      const double den = static_cast<double>(j) / static_cast<double>(j - l - 1) - 1.0;
-      for (int r = 0; r < nr; ++r) cur[l + 1][r] = cur[l][r] + (cur[l][r] - prev[l][r]) / den;
-    }
-    for (int l = 0; l < j; ++l)
-      for (int r = 0; r < nr; ++r) prev[l][r] = cur[l][r];
   }
+  ok = __all_sync(0xffffffffu, ok);
+  __syncwarp();
+  if (!ok) return false;
   double e = 0.0;
-  for (int r = 0; r < nr; ++r) {
-    y1[r] = cur[HX_K - 1][r];
-    if (!isfinite(y1[r])) return false;
-    const double sc = HX_ATOL + HX_RTOL * fmax(fabs(y0[r]), fabs(y1[r]));
-    e = fmax(e, fabs(cur[HX_K - 1][r] - cur[HX_K - 2][r]) / sc);
+  bool fin = true;
+  if (lane == 0) {
+    double prev[HX_K][MAXR], cur[HX_K][MAXR];
+    for (int jj = 1; jj <= HX_K; ++jj) {
+      for (int r = 0; r < nr; ++r) cur[0][r] = sm.col[jj - 1][r];
+      for (int l = 0; l + 1 < jj; ++l) {
+        const double den = static_cast<double>(jj) / static_cast<double>(jj - l - 1) - 1.0;
+        for (int r = 0; r < nr; ++r) cur[l + 1][r] = cur[l][r] + (cur[l][r] - prev[l][r]) / den;
+      }
+      for (int l = 0; l < jj; ++l)
+        for (int r = 0; r < nr; ++r) prev[l][r] = cur[l][r];
+    }
+    for (int r = 0; r < nr; ++r) {
+      const double v = cur[HX_K - 1][r];
+      fin = fin && isfinite(v);
+      sm.y1[r] = v;
+      const double sc = HX_ATOL + HX_RTOL * fmax(fabs(y0[r]), fabs(v));
+      e = fmax(e, fabs(v - cur[HX_K - 2][r]) / sc);
+    }
   }
+  fin = __shfl_sync(0xffffffffu, fin, 0);
+  e = __shfl_sync(0xffffffffu, e, 0);
+  __syncwarp();
+  if (!fin) return false;
+  for (int r = 0; r < nr; ++r) y1[r] = sm.y1[r];
+  __syncwarp();
   *err = e;
   return true;
 }
 
-// Extents after T seconds from e = 0. Returns the accepted steps, or -1 on failure.
-__device__ long long hx_integrate(const Kin& k, double T, double* e) {
+// Extents after T seconds from e = 0, by one warp (identical control flow on every lane).
+// Returns the accepted steps, or -1 on failure.
+__device__ long long hx_integrate(const Kin& k, double T, double* e, HxWarpSmem& sm, int lane) {
   for (int r = 0; r < k.nr; ++r) e[r] = 0.0;
   if (k.nr == 0 || !(T > 0.0)) return 0;
   double t = 0.0, H = fmin(T, 1e-9);
@@ -168,7 +195,7 @@ __device__ long long hx_integrate(const Kin& k, double T, double* e) {
     const bool last = H >= T - t;
     const double Hs = last ? T - t : H;
     double err = 0.0;
-    const bool ok = hx_step(k, e, Hs, y1, &err);
+    const bool ok = hx_step(k, e, Hs, y1, &err, sm, lane);
     if (ok && err <= 1.0) {
       for (int r = 0; r < k.nr; ++r) e[r] = y1[r];
       t = last ? T : t + Hs;
@@ -193,9 +220,13 @@ __global__ void k_hx_remove(Dev d) {
   }
 }
 
-__global__ void k_hx_integrate(Dev d) {
-  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= d.n_trains || status_of_hx(d)) return;
+constexpr int HX_WARPS = 2;  // trains per CTA, one warp each
+
+__global__ void __launch_bounds__(32 * HX_WARPS) k_hx_integrate(Dev d) {
+  __shared__ HxWarpSmem smem[HX_WARPS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t b = blockIdx.x * HX_WARPS + static_cast<uint32_t>(w);
+  if (b >= d.n_trains || status_of_hx(d)) return;  // warp-uniform
   Train& tr = d.trains[b];
   if (!tr.hx_sel) return;
   const Tables& tb = *d.tables;
@@ -217,7 +248,8 @@ __global__ void k_hx_integrate(Dev d) {
     for (int q = 0; q < tb.n_prod[r]; ++q) k.nu[tb.prod[r][q]][r] += 1.0;
   }
   double e[MAXR];
-  const long long steps = hx_integrate(k, tr.hx_t_end - tr.t, e);
+  const long long steps = hx_integrate(k, tr.hx_t_end - tr.t, e, smem[w], lane);
+  if (lane != 0) return;  // the rounding and the train's record: one lane
   if (steps < 0) {
     raise_status(d.g, CHEM_ECAPACITY);
     d.g->err_where = 0x4858u;  // integrator step limit of the homogeneous stage
@@ -284,8 +316,7 @@ cudaError_t enqueue_homogeneous(const Dev& d, int blocks, cudaStream_t s) {
   k_hx_remove<<<blocks, 256, 0, s>>>(d);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nt = 64;
-  k_hx_integrate<<<(static_cast<int>(d.n_trains) + nt - 1) / nt, nt, 0, s>>>(d);
+  k_hx_integrate<<<(static_cast<int>(d.n_trains) + HX_WARPS - 1) / HX_WARPS, 32 * HX_WARPS, 0, s>>>(d);
   return cudaGetLastError();
 }
 
