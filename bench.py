@@ -367,6 +367,7 @@ def run_gpu_arm(args):
     hres = None if args.no_hybrid else run_hybrid(args, chem, W, torch, stream, alloc, rank, world, dev,
                                                   tuned=bres.get("autotuned") if bres else None)
     vres = None if args.no_volume else run_volume_scaling(args, chem, W, torch, stream, alloc, rank, world, dev)
+    lres = run_large(args, chem, W, torch, stream, alloc) if not args.no_large and rank == 0 else None
     if rank != 0:
         return 0
     value = ss_all / t_max
@@ -454,6 +455,8 @@ def run_gpu_arm(args):
         line["hybrid"] = hres
     if vres is not None:
         line["volume_scaling"] = vres
+    if lres is not None:
+        line["large"] = lres
     line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     return 0
@@ -723,6 +726,49 @@ def run_volume_scaling(args, chem, W, torch, stream, alloc, rank=0, world=1, dev
                         "0.2/0.5/1.0 um, log dt from 1 ps to 1 ms, FP32-local"}
 
 
+def run_large(args, chem, W, torch, stream, alloc):
+    """Large build-up (10 um, 20 pulses, 20 Gy, ~7.5e6 species created), step by step
+    throughout, FP32-local and FP64: G(H2O2) at the end of every pulse and before the
+    next, wall time and species-steps/s of each, and the FP32-local / FP64 G(H2O2) ratio
+    at the end (one seed each)."""
+    wl = W.large_build_up(seed=1)
+    n = wl.n_species
+    period = 10e-6
+    stops = sorted({round(k * period + d, 12) for k in range(20) for d in (1e-6, period)})
+    out = {"workload": "10 um cube, 20 pulses of ~1 Gy (648 tracks, 375,000 species, 4 bunches each) every "
+                       "10 us at 1e6 Gy/s pulse dose rate, step by step throughout, to 200 us",
+           "species_created": int(n), "t_s": stops}
+    precisions = [("fp32l", chem.CHEM_FP32_LOCAL)] + ([] if args.no_large_fp64 else [("fp64", chem.CHEM_FP64)])
+    for name, prec in precisions:
+        cfg, keep = chem.make_config(wl.L, wl.D, wl.reactions, seed=3, precision=prec,
+                                     dt_min=wl.schedule.dt_min, dt_max=wl.schedule.dt_max,
+                                     dt_growth=wl.schedule.dt_growth, capacity_species=int(1.2 * n) + 4096,
+                                     capacity_pending=n, capacity_candidates=max(4096, n // 4),
+                                     stream=stream.cuda_stream, allocator=alloc)
+        ctx = chem.chem_init(cfg)
+        try:
+            if name == "fp32l" and args.tuned:
+                chem.chem_set_tuning(ctx, *[int(v) for v in args.tuned.split(",")])
+            for p in wl.pulses:
+                chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
+            g = []
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for t in stops:
+                chem.chem_run_until(ctx, t)
+                g.append(float(chem.chem_tally(ctx, 7, 9)["G"][6]))
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            tal = chem.chem_tally(ctx, 7, 9)
+        finally:
+            chem.chem_destroy(ctx)
+        out[name] = {"wall_s": wall, "value": tal["species_steps"] / wall, "unit": UNIT,
+                     "G_H2O2": [round(v, 4) for v in g], "live_at_end": int(tal["counts"][:7].sum())}
+    if "fp64" in out:
+        out["G_H2O2_end_fp32l_over_fp64"] = out["fp32l"]["G_H2O2"][-1] / out["fp64"]["G_H2O2"][-1]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -751,6 +797,8 @@ def main():
     ap.add_argument("--hybrid-scale", type=float, default=1.0)
     ap.add_argument("--no-dose-series", action="store_true")
     ap.add_argument("--no-volume", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 10 um, 20-pulse build-up")
+    ap.add_argument("--no-large-fp64", action="store_true", help="run it in FP32-local mode only")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference_arm(args)

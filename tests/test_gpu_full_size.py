@@ -121,3 +121,44 @@ def test_batched_sweep_full_size():
             assert np.unique(ids).size == ids.size
     finally:
         chem.chem_destroy(ctx)
+
+
+def test_large_box_build_up_first_pulses_conserve():
+    """The 10 um, 20-pulse build-up at full size for its first two pulses (750,000 species
+    created, FP32-local): charge and atoms conserved exactly, counts equal to the injected
+    species plus events times stoichiometry, and species carried into the second pulse."""
+    import torch
+    wl = W.large_build_up(seed=1, n_pulses=2)
+    n = wl.n_species
+    cfg, keep = chem.make_config(wl.L, wl.D, wl.reactions, seed=3, precision=chem.CHEM_FP32_LOCAL,
+                                 dt_min=wl.schedule.dt_min, dt_max=wl.schedule.dt_max,
+                                 dt_growth=wl.schedule.dt_growth, capacity_species=int(1.2 * n) + 4096,
+                                 capacity_pending=n, capacity_candidates=max(4096, n // 4),
+                                 stream=torch.cuda.current_stream().cuda_stream,
+                                 allocator=chem.torch_allocator(0))
+    ctx = chem.chem_init(cfg)
+    try:
+        for p in wl.pulses:
+            chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        chem.chem_run_until(ctx, 10e-6)
+        first = chem.chem_tally(ctx, 7, 9)
+        chem.chem_run_until(ctx, wl.t_end)
+        tal = chem.chem_tally(ctx, 7, 9)
+    finally:
+        chem.chem_destroy(ctx)
+    injected = np.bincount(np.concatenate([p.types for p in wl.pulses]), minlength=7)
+    nu = np.zeros((7, 9), np.int64)
+    water = 0
+    for r, rx in enumerate(W.WATER_REACTIONS):
+        nu[rx.a, r] -= 1
+        nu[rx.b, r] -= 1
+        for q in rx.products:
+            nu[q, r] += 1
+        water += int(tal["events"][r]) * rx.water_delta
+    counts = tal["counts"][:7]
+    np.testing.assert_array_equal(counts, injected + nu @ tal["events"][:9])
+    assert int(counts @ W.CHARGE) == int(injected @ W.CHARGE)
+    assert int(counts @ W.N_H) + 2 * water == int(injected @ W.N_H)
+    assert int(counts @ W.N_O) + water == int(injected @ W.N_O)
+    assert first["counts"][:7].sum() > 50_000 and first["t"] == 10e-6
+    assert tal["t"] == wl.t_end
