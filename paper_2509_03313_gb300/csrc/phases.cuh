@@ -791,7 +791,8 @@ __device__ __forceinline__ void emit_candidate(const Dev& d, uint32_t s_lo, uint
 // estimate of p decides whenever those bounds clear it by twice its error bound (FP32
 // rounding of d0, d1, R and of the products, cancellation in d - R, the documented
 // __expf error, and a few ulp for the two expm1f and their quotient, whose arguments
-// suffer no cancellation since d0 + d1 - R > R); otherwise u and p are formed in FP64,
+// suffer no cancellation since d0 + d1 - R > R); since p <= exp(-a), a uniform above the
+// bound of exp(-a) alone rejects before the expm1f. Otherwise u and p are formed in FP64,
 // so the outcome is always that of the FP64 test. The fast path uses no FP64
 // arithmetic (a slow pipe on this part).
 __device__ __forceinline__ bool accept_f32(float d0sq, float d1sq, int r, const Tables& tb, const Train& tr,
@@ -806,11 +807,14 @@ __device__ __forceinline__ bool accept_f32(float d0sq, float d1sq, int r, const 
     if (x > 60.f) {
       if ((w.x | (w.y >> 11)) != 0u) return false;  // p <= exp(-a) < 1e-26 < 2^-53 <= u
     } else {
-      const float cb = d0f * d1f * inv, cc = Rf * (d0f + d1f - Rf) * inv;
-      const float p = __expf(-x) * (expm1f(-cc) / expm1f(-cb));
-      const float err = 1.2e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x) + 3e-6f;
-      const float band = 2.f * err * p;
+      const float ea = __expf(-x);
       const float ulo = static_cast<float>(w.x >> 8) * 5.9604645e-8f;  // k 2^-24 <= u
+      const float err = 1.2e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x) + 3e-6f;
+      // p <= exp(-a): most pairs are rejected on that bound alone
+      if (ulo >= ea * (1.f + 2.f * err)) return false;
+      const float cb = d0f * d1f * inv, cc = Rf * (d0f + d1f - Rf) * inv;
+      const float p = ea * (expm1f(-cc) / expm1f(-cb));
+      const float band = 2.f * err * p;
       if (ulo >= p + band) return false;
       if (ulo + 5.9604645e-8f <= p - band) return true;               // u < (k + 1) 2^-24
     }
@@ -835,11 +839,13 @@ __device__ __forceinline__ bool accept_f64(double d0sq, double d1sq, int r, cons
     if (x > 60.f) {
       if ((w.x | (w.y >> 11)) != 0u) return false;
     } else {
-      const float cb = d0f * d1f * inv, cc = Rf * (d0f + d1f - Rf) * inv;
-      const float p = __expf(-x) * (expm1f(-cc) / expm1f(-cb));
-      const float err = 2.4e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x) + 4e-6f;
-      const float band = 2.f * err * p;
+      const float ea = __expf(-x);
       const float ulo = static_cast<float>(w.x >> 8) * 5.9604645e-8f;
+      const float err = 2.4e-7f * inv * (b * (d0f + Rf) + a * (d1f + Rf)) + 1e-6f * (1.f + x) + 4e-6f;
+      if (ulo >= ea * (1.f + 2.f * err)) return false;  // p <= exp(-a)
+      const float cb = d0f * d1f * inv, cc = Rf * (d0f + d1f - Rf) * inv;
+      const float p = ea * (expm1f(-cc) / expm1f(-cb));
+      const float band = 2.f * err * p;
       if (ulo >= p + band) return false;
       if (ulo + 5.9604645e-8f <= p - band) return true;
     }
