@@ -106,3 +106,38 @@ def test_two_gloo_ranks_gather_the_sharded_sweep():
     for rank, ss, t, c in got:
         assert ss == 300.0 and t == 3.0
         assert c == [[b + 1] * 7 for b in range(4)]
+
+
+def _rows_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import numpy as np
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # the hybrid and volume legs: each train's float row filled on its own rank only
+        rows = np.zeros((5, 3))
+        for b in bench.shard_trains([50, 10, 40, 20, 30], world)[rank]:
+            rows[b] = [b + 0.25, 1.0 / (b + 1), -b]
+        q.put((rank, bench.sum_over_ranks(rows).tolist()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_sum_per_train_rows():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rows_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    want = [[b + 0.25, 1.0 / (b + 1), -b] for b in range(5)]
+    for rank, rows in got:
+        assert rows == want
