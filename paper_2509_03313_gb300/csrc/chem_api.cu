@@ -2,6 +2,7 @@
 // the pending-species queue, CUDA-graph capture of the step kernels and the run loop.
 // The host never computes a step: it only queues kernels and copies data.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -9,6 +10,7 @@
 #include <cstring>
 #include <limits>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "launch.h"
@@ -363,6 +365,26 @@ chem_status run_loop(chem_ctx* ctx) {
   return CHEM_OK;
 }
 
+// fn(lo, hi) over [0, n), split between up to 16 host threads when n is large.
+template <class F>
+void parallel_ranges(size_t n, F fn) {
+  const size_t min_chunk = size_t(1) << 16;
+  const size_t hw = std::max<size_t>(1, std::thread::hardware_concurrency());
+  const size_t nt = std::min<size_t>({hw, 16, (n + min_chunk - 1) / min_chunk});
+  if (nt <= 1) {
+    fn(size_t(0), n);
+    return;
+  }
+  const size_t step = (n + nt - 1) / nt;
+  std::vector<std::thread> th;
+  for (size_t k = 1; k < nt; ++k) {
+    const size_t lo = k * step, hi = std::min(n, lo + step);
+    if (lo < hi) th.emplace_back(fn, lo, hi);
+  }
+  fn(size_t(0), std::min(n, step));
+  for (auto& x : th) x.join();
+}
+
 // Homogeneous stage (Sec. 2.2) of every train b with t_end[b] > its clock. Pending
 // species already due join the stage; one arriving inside it is an error (EINVAL, nothing
 // changed).
@@ -443,16 +465,20 @@ chem_status inject_one(chem_ctx* ctx, int b, int64_t n, const int32_t* type, con
   if (s) return s;
   Train& t = tr[b];
   TrainHost& h = ctx->th[b];
-  const double L = t.L, halfL = t.halfL;
-  for (int64_t i = 0; i < n; ++i) {
-    if (type[i] < 0 || type[i] >= ctx->tables.n_types) return CHEM_EINVAL;
-    if (!(t_arr[i] >= t.t) || !std::isfinite(t_arr[i])) return CHEM_EINVAL;
-    for (int a = 0; a < 3; ++a) {
-      const double v = xyz[3 * i + a];
-      if (!(v >= -halfL && v < halfL)) return CHEM_EINVAL;
+  const double halfL = t.halfL, t_now = t.t;
+  const int n_types = ctx->tables.n_types;
+  std::atomic<bool> bad(false);
+  parallel_ranges(static_cast<size_t>(n), [&](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi && !bad.load(std::memory_order_relaxed); ++i) {
+      bool ok = type[i] >= 0 && type[i] < n_types && t_arr[i] >= t_now && std::isfinite(t_arr[i]);
+      for (int a = 0; a < 3; ++a) {
+        const double v = xyz[3 * i + a];
+        ok = ok && v >= -halfL && v < halfL;
+      }
+      if (!ok) bad.store(true, std::memory_order_relaxed);
     }
-  }
-  (void)L;
+  });
+  if (bad.load()) return CHEM_EINVAL;
   // drop what the device already released, merge the new species stably by arrival
   // (still-pending species first on equal arrival, new ones in call order)
   PendingHost& p = h.pend;
@@ -476,19 +502,39 @@ chem_status inject_one(chem_ctx* ctx, int b, int64_t n, const int32_t* type, con
                        return a.first < c.first;
                      });
   }
-  size_t i = 0, j = 0;
-  for (size_t k = 0; k < tot; ++k) {
-    const size_t jn = j < static_cast<size_t>(n) ? (sorted_new ? j : by_t[j].second) : 0;
-    const bool take_old = i < keep && (j >= static_cast<size_t>(n) || src.t[head + i] <= t_arr[jn]);
-    if (take_old) {
-      const size_t q = head + i++;
-      dst.t[k] = src.t[q]; dst.x[k] = src.x[q]; dst.y[k] = src.y[q]; dst.z[k] = src.z[q];
-      dst.type[k] = src.type[q];
-    } else {
-      dst.t[k] = t_arr[jn];
-      dst.x[k] = xyz[3 * jn]; dst.y[k] = xyz[3 * jn + 1]; dst.z[k] = xyz[3 * jn + 2];
-      dst.type[k] = type[jn];
-      ++j;
+  const size_t nn = static_cast<size_t>(n);
+  if (sorted_new && (keep == 0 || nn == 0 || src.t[head + keep - 1] <= t_arr[0])) {
+    // every kept species arrives no later than the first new one: an append
+    parallel_ranges(keep, [&](size_t lo, size_t hi) {
+      std::memcpy(dst.t + lo, src.t + head + lo, (hi - lo) * sizeof(double));
+      std::memcpy(dst.x + lo, src.x + head + lo, (hi - lo) * sizeof(double));
+      std::memcpy(dst.y + lo, src.y + head + lo, (hi - lo) * sizeof(double));
+      std::memcpy(dst.z + lo, src.z + head + lo, (hi - lo) * sizeof(double));
+      std::memcpy(dst.type + lo, src.type + head + lo, (hi - lo) * sizeof(int32_t));
+    });
+    parallel_ranges(nn, [&](size_t lo, size_t hi) {
+      for (size_t q = lo; q < hi; ++q) {
+        const size_t k = keep + q;
+        dst.t[k] = t_arr[q];
+        dst.x[k] = xyz[3 * q]; dst.y[k] = xyz[3 * q + 1]; dst.z[k] = xyz[3 * q + 2];
+        dst.type[k] = type[q];
+      }
+    });
+  } else {
+    size_t i = 0, j = 0;
+    for (size_t k = 0; k < tot; ++k) {
+      const size_t jn = j < static_cast<size_t>(n) ? (sorted_new ? j : by_t[j].second) : 0;
+      const bool take_old = i < keep && (j >= static_cast<size_t>(n) || src.t[head + i] <= t_arr[jn]);
+      if (take_old) {
+        const size_t q = head + i++;
+        dst.t[k] = src.t[q]; dst.x[k] = src.x[q]; dst.y[k] = src.y[q]; dst.z[k] = src.z[q];
+        dst.type[k] = src.type[q];
+      } else {
+        dst.t[k] = t_arr[jn];
+        dst.x[k] = xyz[3 * jn]; dst.y[k] = xyz[3 * jn + 1]; dst.z[k] = xyz[3 * jn + 2];
+        dst.type[k] = type[jn];
+        ++j;
+      }
     }
   }
   p.cur = 1 - p.cur;
