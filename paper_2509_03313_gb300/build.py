@@ -2,7 +2,7 @@
 
 The translation units compile in parallel; FP64-mode kernels are built with
 --fmad=false and all host code with -ffp-contract=off so that no multiply-add is
-contracted on either side (the GPU machine is aarch64, where GCC would otherwise fuse).
+contracted on either side (on aarch64 hosts GCC would otherwise fuse).
 """
 from __future__ import annotations
 
