@@ -315,6 +315,14 @@ chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, double t_s,
                               double* xyz_out, int32_t* n_out, uint32_t* next_id_out,
                               chem_event* events_out, int32_t* n_events_out);
 
+/* Diagnostic with no counterpart in the paper: one device thread waits for a word that
+ * nothing writes, bounded by limit_s seconds (0 < limit_s <= 10), the way every device-side
+ * wait of the library is bounded (sort look-back, grid barrier). Returns CHEM_ETIMEOUT,
+ * sticky on ctx like any device error, with the CUDA context left usable: the error
+ * path a caller sees when a bounded wait runs out, produced without a GPU fault.
+ * CHEM_EINVAL (nothing launched) for a limit outside that range. */
+chem_status chem_check_bounded_wait(chem_ctx* ctx, double limit_s);
+
 /* Library version string. */
 const char* chem_version(void);
 

@@ -85,7 +85,8 @@ EXPORTS = ["chem_init", "chem_inject_pulse", "chem_run_until", "chem_tally", "ch
            "chem_batch_init", "chem_batch_inject", "chem_batch_run_until", "chem_batch_tally",
            "chem_batch_get_state", "chem_batch_reset", "chem_batch_size", "chem_autotune", "chem_set_tuning",
            "chem_version", "chem_get_stats", "chem_set_profiling", "chem_step_noalloc",
-           "chem_run_homogeneous", "chem_batch_run_homogeneous", "chem_batch_homogeneous_report"]
+           "chem_run_homogeneous", "chem_batch_run_homogeneous", "chem_batch_homogeneous_report",
+           "chem_check_bounded_wait"]
 
 
 class ChemError(RuntimeError):
@@ -128,6 +129,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "chem_run_homogeneous": (i32, [vp, dbl]),
         "chem_batch_run_homogeneous": (i32, [vp, vp]),
         "chem_batch_homogeneous_report": (i32, [vp, i32, vp, vp, vp]),
+        "chem_check_bounded_wait": (i32, [vp, dbl]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -298,6 +300,12 @@ def chem_batch_homogeneous_report(ctx, train: int = 0, n_rxn: int = 16):
     st = np.zeros(1, np.int64)
     _check(ctx, lib().chem_batch_homogeneous_report(ctx, int(train), _ptr(e), _ptr(E), _ptr(st)))
     return e, E, int(st[0])
+
+
+def chem_check_bounded_wait(ctx, limit_s: float):
+    """Diagnostic: a device wait on a word nothing writes, bounded by limit_s; raises
+    ChemError(CHEM_ETIMEOUT) (sticky on ctx)."""
+    _check(ctx, lib().chem_check_bounded_wait(ctx, float(limit_s)))
 
 
 def chem_batch_size(ctx) -> int:

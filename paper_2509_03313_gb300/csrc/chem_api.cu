@@ -948,6 +948,21 @@ chem_status chem_run_until(chem_ctx* ctx, double t_end_s) {
   return chem_batch_run_until(ctx, t.data());
 }
 
+chem_status chem_check_bounded_wait(chem_ctx* ctx, double limit_s) {
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  if (!(limit_s > 0.0) || !(limit_s <= 10.0)) return CHEM_EINVAL;
+  CK(enqueue_bounded_wait(ctx->d, limit_s, ctx->stream));
+  ctx->stats.kernel_launches += 1;
+  s = download_global(ctx);
+  if (s) return s;
+  const int st = ctx->g_pinned->status;
+  if (st != 0)
+    return fail(ctx, static_cast<chem_status>(st), "a bounded device wait ran out after %.3g s (status %d)",
+                limit_s, st);
+  return CHEM_OK;
+}
+
 chem_status chem_batch_run_homogeneous(chem_ctx* ctx, const double* t_end_s) {
   return homogeneous_run(ctx, t_end_s);
 }

@@ -81,6 +81,30 @@ cudaError_t sort_pass_occupancy(int* blocks_per_sm) {
                                                        sizeof(SortSmem));
 }
 
+// One thread waits for a word that nothing writes (Global::never_set), polling it until
+// limit_ns of the global timer have passed, then raises CHEM_ETIMEOUT: the error path of
+// every bounded device wait of the library, without a fault.
+__global__ void k_bounded_wait(const __grid_constant__ Dev d, unsigned long long limit_ns) {
+  if (threadIdx.x != 0) return;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  const volatile uint32_t* flag = &d.g->never_set;
+  for (;;) {
+    if (*flag != 0u) return;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > limit_ns) {
+      raise_status(d.g, CHEM_ETIMEOUT);
+      return;
+    }
+    __nanosleep(1000);
+  }
+}
+
+cudaError_t enqueue_bounded_wait(const Dev& d, double limit_s, cudaStream_t s) {
+  k_bounded_wait<<<1, 32, 0, s>>>(d, static_cast<unsigned long long>(limit_s * 1e9));
+  return cudaGetLastError();
+}
+
 cudaError_t enqueue_set_t_end(const Dev& d, const double* t_end_dev, cudaStream_t s) {
   k_set_t_end<<<1, 256, 0, s>>>(d, t_end_dev);
   return cudaGetLastError();

@@ -35,6 +35,8 @@ cudaError_t enqueue_step_f64(const Dev& d, const LaunchCfg& lc, cudaStream_t s, 
 cudaError_t enqueue_persistent_f64(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s);
 cudaError_t persistent_occupancy_f64(int* blocks_per_sm);
 cudaError_t enqueue_set_t_end(const Dev& d, const double* t_end_dev, cudaStream_t s);
+// one device thread waits, up to limit_s, for a word nothing writes (then CHEM_ETIMEOUT)
+cudaError_t enqueue_bounded_wait(const Dev& d, double limit_s, cudaStream_t s);
 
 // homog.cu: homogeneous (beam-off) stage of the trains with Train::hx_sel set
 cudaError_t enqueue_homogeneous(const Dev& d, int blocks, cudaStream_t s);

@@ -141,7 +141,7 @@ struct Global {
   uint32_t sort_parity;   // number of non-trivial passes of this step's cell sort, mod 2
   uint32_t sort_any;      // at least one pass executed (else the order is unchanged)
   uint32_t ev_parity;     // event order in ev_v1 (1) or ev_v0 (0), prefix in the other key buffer
-  uint32_t pad_[1];
+  uint32_t never_set;     // stays 0: the word chem_check_bounded_wait waits for
 };
 
 // Accepted reactive pair.
