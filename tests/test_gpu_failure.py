@@ -52,3 +52,43 @@ def test_bounded_wait_limit_is_checked():
         chem.chem_run_until(ctx, 0.0)  # not sticky: the context is still fine
     finally:
         chem.chem_destroy(ctx)
+
+
+def test_bad_inputs_are_refused_and_leave_the_context_usable():
+    ctx, keep, wl = _ctx()
+    try:
+        p = wl.pulses[0]
+        good_t = p.t_arrival.copy()
+        for types, xyz, t in (
+                (p.types, p.xyz, np.where(np.arange(p.n) == 5, np.nan, good_t)),      # NaN arrival
+                (p.types, p.xyz, good_t - 1e-9),                                      # before the clock
+                (p.types, np.where(np.arange(3 * p.n).reshape(-1, 3) == 7, wl.L, p.xyz), good_t),  # outside
+                (np.where(np.arange(p.n) == 3, 7, p.types).astype(np.int32), p.xyz, good_t)):     # bad type
+            with pytest.raises(chem.ChemError) as err:
+                chem.chem_inject_pulse(ctx, types, xyz, t, p.energy_eV)
+            assert err.value.status == chem.CHEM_EINVAL
+        chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)  # still fine
+        chem.chem_run_until(ctx, 2e-9)
+        assert chem.chem_tally(ctx, 7, 9)["counts"][:7].sum() > 0
+    finally:
+        chem.chem_destroy(ctx)
+
+
+def test_species_capacity_overflow_is_a_sticky_status():
+    import torch
+    wl = W.uniform_2000(seed=3, L=400.0, n_steps=20)
+    cfg, keep = chem.make_config(wl.L, wl.D, wl.reactions, seed=3, capacity_species=1000,
+                                 capacity_pending=4096, stream=torch.cuda.current_stream().cuda_stream,
+                                 allocator=chem.torch_allocator(0))
+    ctx = chem.chem_init(cfg)
+    try:
+        p = wl.pulses[0]
+        chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)  # 2,000 > 1,000 slots
+        with pytest.raises(chem.ChemError) as err:
+            chem.chem_run_until(ctx, 1e-8)
+        assert err.value.status == chem.CHEM_ECAPACITY
+        with pytest.raises(chem.ChemError) as err:
+            chem.chem_run_until(ctx, 2e-8)
+        assert err.value.status == chem.CHEM_ECAPACITY
+    finally:
+        chem.chem_destroy(ctx)
