@@ -141,3 +141,22 @@ def test_two_gloo_ranks_sum_per_train_rows():
     want = [[b + 0.25, 1.0 / (b + 1), -b] for b in range(5)]
     for rank, rows in got:
         assert rows == want
+
+
+def test_recorded_traffic_only_while_the_sources_match(tmp_path, monkeypatch):
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = {"dram_bytes_per_launch": {"k_search_tps": 123, "k_diffuse": 45},
+           "sources_sha256": bench.sources_digest(), "tuning": [8, 384, 0, 1]}
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(path))
+    assert bench.recorded_traffic("k_search_tps") == 123
+    assert bench.recorded_traffic("k_sort_pass") is None
+    rec["sources_sha256"] = "0" * 64  # the kernels changed since the capture
+    path.write_text(json.dumps(rec))
+    assert bench.recorded_traffic("k_search_tps") is None
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.json"))
+    assert bench.recorded_traffic("k_search_tps") is None
+
