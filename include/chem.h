@@ -156,10 +156,11 @@ chem_status chem_inject_pulse(chem_ctx* ctx, int64_t n, const int32_t* type, con
  * Blocks until the device has finished. */
 chem_status chem_run_until(chem_ctx* ctx, double t_end_s);
 
-/* Tallies of train 0 after the last completed step. Any output pointer may be NULL.
- * counts[n_types]: live species; G_per_100eV[n_types]: counts * 100 / E_dep;
- * events[n_rxn]: reactions so far; t_now: clock; species_steps: sum over steps of the
- * species that took the step. */
+/* Tallies of train 0 after the last completed step (or homogeneous stage). Any output
+ * pointer may be NULL. counts[n_types]: live species, including survivors of a
+ * homogeneous stage not yet re-created; G_per_100eV[n_types]: counts * 100 / E_dep;
+ * events[n_rxn]: reactions so far, the whole events of homogeneous stages included;
+ * t_now: clock; species_steps: sum over steps of the species that took the step. */
 chem_status chem_tally(chem_ctx* ctx, int64_t* counts, double* G_per_100eV, int64_t* events,
                        double* t_now, int64_t* species_steps);
 
@@ -168,8 +169,9 @@ chem_status chem_tally(chem_ctx* ctx, int64_t* counts, double* G_per_100eV, int6
 chem_status chem_get_state(chem_ctx* ctx, int64_t cap, int32_t* type, uint32_t* id, double* xyz,
                            int64_t* n);
 
-/* Recorded events (all trains, in step order, within a step in (train, id_lo) order)
- * and per-step records. *n receives the number copied; ECAPACITY (sticky) if the log
+/* Recorded events of the step-by-step stage (all trains, in step order, within a step in
+ * (train, id_lo) order) and per-step records; homogeneous stages add to the event tallies
+ * but not to these logs. *n receives the number copied; ECAPACITY (sticky) if the log
  * overflowed on the device. */
 chem_status chem_get_events(chem_ctx* ctx, int64_t cap, chem_event* ev, int64_t* n);
 chem_status chem_get_step_log(chem_ctx* ctx, int64_t cap, chem_step_record* rec, int64_t* n);
