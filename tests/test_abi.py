@@ -57,3 +57,9 @@ def test_invalid_configs_are_rejected_before_touching_a_gpu(lib):
         with pytest.raises(chem.ChemError) as e:
             chem.chem_init(cfg)
         assert e.value.status == chem.CHEM_EINVAL, kw
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    from paper_2509_03313_gb300 import chem
+    with pytest.raises(ImportError):
+        chem.load(str(tmp_path / "libchem.so"))
