@@ -69,3 +69,20 @@ def test_water_table_conserves_charge_and_atoms():
     assert int(last @ W.N_H) + 2 * water == int(n0 @ W.N_H)
     assert int(last @ W.N_O) + water == int(n0 @ W.N_O)
     assert events.sum() > 100
+
+
+def test_rate_equations_and_stochastic_simulation_agree_within_one_percent():
+    """The paper's check of its rate equations against Kinetiscope (Sec. 2.3: below 1 %
+    for every species): the reference rate equations (extents, scipy Radau) against the
+    mean of independent Gillespie runs, the volume-scaling mixture in a 0.5 um box."""
+    from oracle import homogeneous as H
+    wl = W.volume_scaling(500.0, seed=100)
+    n0 = np.bincount(wl.pulses[0].types, minlength=7)
+    T = [1e-6, 1e-4, 1e-3]
+    runs = np.array([G.ssa(n0, 500.0, W.WATER_REACTIONS, T, seed=s)[0] for s in range(4)], float)
+    mean, sem = runs.mean(axis=0), runs.std(axis=0, ddof=1) / 2.0
+    nu = H.stoichiometry(7, W.WATER_REACTIONS)
+    for i, t in enumerate(T):
+        ode = n0 + nu @ H.extents(n0.astype(float), 500.0, t, W.WATER_REACTIONS)
+        big = mean[i] > 200
+        assert np.all(np.abs(ode - mean[i])[big] <= (0.01 * mean[i] + 4 * sem[i] + 2.0)[big]), (t, ode, mean[i])
