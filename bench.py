@@ -595,11 +595,11 @@ def run_trains(chem, hybrid, wls_all, plans_all, stream, alloc, rank, world, dev
 
 
 def run_hybrid(args, chem, W, torch, stream, alloc, rank=0, world=1, device=None, tuned=None):
-    """Sec. 2.2 alternation on the GPU: step-by-step chemistry while the beam is on, the
+    """Sec. 2.1 alternation on the GPU: step-by-step chemistry while the beam is on, the
     rate equations for the rest of each interval and for 10 s after the last pulse.
     (1) The 64 trains of the dose-rate sweep with all 10 pulses: post-irradiation
     G(H2O2) per train and the radical build-up before the last pulse, whose onset gives
-    the SDR/UHDR threshold of Sec. 3. (2) Separate irradiations of 1-20 pulses at 1 and
+    the SDR/UHDR threshold of Sec. 3.3. (2) Separate irradiations of 1-20 pulses at 1 and
     1e4 Gy/s: the H2O2 yield as the slope of post-irradiation concentration against dose
     (Fig. Concentration-Dose). Timed end to end on the host clock (every call syncs);
     trains are split between the ranks."""
@@ -650,7 +650,7 @@ def run_hybrid(args, chem, W, torch, stream, alloc, rank=0, world=1, device=None
 
 
 def run_volume_scaling(args, chem, W, torch, stream, alloc, rank=0, world=1, device=None):
-    """Volume-scaling study of Sec. 2.3 on the GPU: one mixture concentration in boxes of
+    """Volume-scaling study of Sec. 2.2 / Sec. 3.1 on the GPU: one mixture concentration in boxes of
     0.2, 0.5 and 1.0 um (8, 4 and 2 seeds) followed to 1 ms by the FP32-local SBS in one
     batched context per rank; mean concentrations per box at 1 ms, their largest
     relative spread across the boxes, and the ratio of the SBS to the GPU rate equations

@@ -158,7 +158,9 @@ chem_status chem_run_until(chem_ctx* ctx, double t_end_s);
 
 /* Tallies of train 0 after the last completed step (or homogeneous stage). Any output
  * pointer may be NULL. counts[n_types]: live species, including survivors of a
- * homogeneous stage not yet re-created; G_per_100eV[n_types]: counts * 100 / E_dep;
+ * homogeneous stage not yet re-created; G_per_100eV[n_types]: the G-values of Sec. 1
+ * (species per 100 eV of deposited energy), counts * 100 / E_dep with E_dep in eV the
+ * sum of the energies passed to chem_inject_pulse (multiply by 1.0364e-7 for mol/J);
  * events[n_rxn]: reactions so far, the whole events of homogeneous stages included;
  * t_now: clock; species_steps: sum over steps of the species that took the step. */
 chem_status chem_tally(chem_ctx* ctx, int64_t* counts, double* G_per_100eV, int64_t* events,
@@ -207,9 +209,9 @@ chem_status chem_batch_reset(chem_ctx* ctx, const uint64_t* seeds);
 int32_t chem_batch_size(const chem_ctx* ctx);
 
 /* ---- homogeneous (beam-off) stage ------------------------------------------------
- * Sec. 2.2: during the beam-off time between pulses, and for 10 s after the last pulse,
- * the paper follows the species as a well-mixed system with the rate equations of
- * Table 1 (Eq. 3, Eq. 4) instead of step by step. For every train whose clock is below
+ * Sec. 2.3 (and the workflow of Sec. 2.1): during the beam-off time between pulses, and
+ * for 10 s after the last pulse, the paper follows the species as a well-mixed system
+ * with the rate equations of Table 1 (Eq. 3, Eq. 4) instead of step by step. For every train whose clock is below
  * t_end_s[b] (trains at or past it are left alone):
  *  - its species counts, plus pending species already due (arrival <= clock), become
  *    molecule numbers in the box volume L^3; its particles are removed;
@@ -275,6 +277,25 @@ typedef struct chem_stats {
   int64_t bytes_d2h;        /* bytes copied device -> host                             */
   double phase_ms[8];       /* summed device time per phase                            */
   int64_t phase_launches[8];/* kernel launches per phase behind phase_ms               */
+  /* Which branches reaction resolution took (device counters, summed over resets). The
+   * conflict rounds run in shared memory for up to 1,536 conflicting accepted pairs and
+   * in global memory beyond (always in the persistent kernel); the events of a step are
+   * ordered in shared memory for up to 8,192 events (bucket sort, or a block radix sort
+   * when the keys cluster) and in global memory beyond. The results do not depend on the
+   * branch; these counters let tests show that each branch ran. */
+  int64_t react_rounds_global;  /* steps whose conflict rounds ran in global memory     */
+  int64_t react_order_global;   /* steps whose event order ran in global memory         */
+  int64_t react_order_radix;    /* steps whose shared-memory event order used the radix
+                                   sort because a bucket held more than 64 keys          */
+  int64_t max_conflict_pairs;   /* most conflicting accepted pairs in one step          */
+  int64_t max_step_events;      /* most events in one step                              */
+  /* Pair-search work (device counters, summed over resets): neighbour pairs whose
+   * separation the search tested, those of reacting types inside their cutoff (each
+   * costs one acceptance test: a Philox block and the touch probability), and the
+   * accepted ones. */
+  int64_t pairs_tested;
+  int64_t pairs_in_cutoff;
+  int64_t pairs_accepted;
 } chem_stats;
 chem_status chem_get_stats(const chem_ctx* ctx, chem_stats* out);
 /* on != 0: re-capture the step graph with CUDA events around every phase kernel (adds
@@ -309,7 +330,10 @@ chem_status chem_set_profiling(chem_ctx* ctx, int32_t on);
  * and *n_events_out. Blocks until the step has finished on the stream.
  * Returns CHEM_ECAPACITY when n exceeds CHEM_NOALLOC_MAX_SPECIES or the step would need
  * more room than the fixed array has (candidates, products), CHEM_EINVAL for bad
- * arguments, CHEM_ECUDA when a CUDA call fails. */
+ * arguments, CHEM_ECUDA when a CUDA call fails. The device inputs are checked on the
+ * device: a type outside [0, n_types), an id >= 2^29 - 1, or a position that is not
+ * finite and inside [-L/2, L/2)^3 gives CHEM_EINVAL with *n_out = *n_events_out = 0,
+ * *next_id_out = next_id and no species or event written. */
 enum { CHEM_NOALLOC_MAX_SPECIES = 16384 };
 chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, double t_s, double dt_s,
                               uint32_t next_id, int32_t n, const uint32_t* id, const int32_t* type,
@@ -324,6 +348,24 @@ chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, double t_s,
  * path a caller sees when a bounded wait runs out, produced without a GPU fault.
  * CHEM_EINVAL (nothing launched) for a limit outside that range. */
 chem_status chem_check_bounded_wait(chem_ctx* ctx, double limit_s);
+
+/* Diagnostic with no counterpart in the paper: the pair search's acceptance test alone.
+ * For each i, the pair (id_lo[i], id_hi[i]) of reaction rxn[i] with squared start and end
+ * separations d0sq[i], d1sq[i] (nm^2) in a step `step` of length dt_s (s) of train 0 is
+ * accepted when its uniform u (Philox4x32-10 of train 0's key at counter (id_lo, step,
+ * id_hi, 2), 53 bits) is below the touch probability p of chem_run_until. The search
+ * decides most pairs on an FP32 estimate of p with a rigorous error band and forms p in
+ * FP64 only when u falls inside the band; this call lets a test check, with u placed
+ * within a few ulp of p, that the tiered decision always equals the FP64 one.
+ * precision: CHEM_FP64 runs the FP64 mode's test on the squared separations as given;
+ * CHEM_FP32_LOCAL runs the FP32-local mode's test on their FP32 roundings. Output
+ * (host, n bytes): accept[i] bit 0 = the tiered decision, bit 1 = u < p evaluated in
+ * FP64 on the same inputs. All array arguments are host arrays of n elements. Returns
+ * CHEM_EINVAL for a reaction index out of range, a negative or non-finite input, or
+ * n > 2^24; uses a temporary device block (through the allocator callbacks when given). */
+chem_status chem_check_acceptance(chem_ctx* ctx, int32_t precision, uint32_t step, double dt_s, int64_t n,
+                                  const double* d0sq, const double* d1sq, const int32_t* rxn,
+                                  const uint32_t* id_lo, const uint32_t* id_hi, uint8_t* accept);
 
 /* Library version string. */
 const char* chem_version(void);

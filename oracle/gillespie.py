@@ -1,5 +1,5 @@
-"""Well-mixed stochastic reference for the volume-scaling study (Sec. 2.3 verification of
-the periodic boundary conditions): the paper compares the SBS in boxes of 0.2, 0.5 and
+"""Well-mixed stochastic reference for the volume-scaling study (Sec. 2.2 setup and
+Sec. 3.1 results of the verification of the periodic boundary conditions): the paper compares the SBS in boxes of 0.2, 0.5 and
 1.0 um with Kinetiscope, which runs Gillespie's stochastic simulation algorithm. This is
 an independent implementation of that algorithm (the direct method of Gillespie, J.
 Phys. Chem. 81, 2340, 1977) for the reaction table of Table 1.

@@ -1,4 +1,4 @@
-"""Homogeneous stage of a pulse train (Sec. 2.2 workflow, Sec. 2.4 rate equations
+"""Homogeneous stage of a pulse train (Sec. 2.1 workflow, Sec. 2.3 rate equations
 Eq. 3 / Eq. 4) in plain FP64 numpy/scipy.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/sbs.py``).

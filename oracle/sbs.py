@@ -16,7 +16,8 @@ against the paper:
 * Table 1 + Table S2 + Eq. kdiff1/kdiff2 (supplement): every reaction is diffusion
   controlled and its radius follows from k = 4 pi R D_AB N_A, where for the self
   reactions R1, R6 and R8 the tabulated value is already 2k.
-* Sec. 2.3 and the supplement: two reactants react when they come within R.
+* Sec. 2.2 (Fig. PBClattice), Sec. 2.4 and the supplement: two reactants react when
+  they come within R.
 
 Where the paper is silent the following readings are used, identically in the library:
 
@@ -43,7 +44,7 @@ Where the paper is silent the following readings are used, identically in the li
   order and table order; products diffuse from the next step;
 * optional free-diffusion jump (no reactions) once sbs_horizon has passed since the
   last release, up to the next arrival or the end time;
-* the beam-off (homogeneous) stage of Sec. 2.2 with its own readings in
+* the beam-off (homogeneous) stage of Sec. 2.3 with its own readings in
   ``oracle/homogeneous.py``; its survivors are re-created ahead of the pending species
   at the next release.
 """
@@ -315,7 +316,7 @@ class SBSOracle:
         return dt, self.t + dt, False
 
     def candidates(self, delta, dt):
-        """Accepted reactive pairs of this step (Sec. 2.3 criterion with the bridge
+        """Accepted reactive pairs of this step (Sec. 2.4 criterion with the bridge
         reading). Returns arrays (lo, hi, rxn, d1sq, r1) with lo/hi indices into the live
         arrays ordered so that ids[lo] < ids[hi]."""
         N = self.ids.shape[0]
@@ -409,7 +410,7 @@ class SBSOracle:
             n += 1
         return n
 
-    # -- homogeneous stage (Sec. 2.2) ------------------------------------------------
+    # -- homogeneous stage (Sec. 2.3) ------------------------------------------------
     def run_homogeneous(self, t_end: float):
         """Beam-off stage: the species (and pending ones already due) become molecule
         numbers, the rate equations of Table 1 (Eq. 3, Eq. 4) run for t_end - t, and the

@@ -67,7 +67,11 @@ class chem_stats(ctypes.Structure):
     _fields_ = [("graph_replays", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("steps_launched", ctypes.c_int64), ("bytes_h2d", ctypes.c_int64),
                 ("bytes_d2h", ctypes.c_int64), ("phase_ms", ctypes.c_double * 8),
-                ("phase_launches", ctypes.c_int64 * 8)]
+                ("phase_launches", ctypes.c_int64 * 8), ("react_rounds_global", ctypes.c_int64),
+                ("react_order_global", ctypes.c_int64), ("react_order_radix", ctypes.c_int64),
+                ("max_conflict_pairs", ctypes.c_int64), ("max_step_events", ctypes.c_int64),
+                ("pairs_tested", ctypes.c_int64), ("pairs_in_cutoff", ctypes.c_int64),
+                ("pairs_accepted", ctypes.c_int64)]
 
 
 PHASES = ("begin", "release", "diffuse", "sort", "gather", "search", "react", "persistent")
@@ -86,7 +90,7 @@ EXPORTS = ["chem_init", "chem_inject_pulse", "chem_run_until", "chem_tally", "ch
            "chem_batch_get_state", "chem_batch_reset", "chem_batch_size", "chem_autotune", "chem_set_tuning",
            "chem_version", "chem_get_stats", "chem_set_profiling", "chem_step_noalloc",
            "chem_run_homogeneous", "chem_batch_run_homogeneous", "chem_batch_homogeneous_report",
-           "chem_check_bounded_wait"]
+           "chem_check_bounded_wait", "chem_check_acceptance"]
 
 
 class ChemError(RuntimeError):
@@ -130,6 +134,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "chem_batch_run_homogeneous": (i32, [vp, vp]),
         "chem_batch_homogeneous_report": (i32, [vp, i32, vp, vp, vp]),
         "chem_check_bounded_wait": (i32, [vp, dbl]),
+        "chem_check_acceptance": (i32, [vp, i32, ctypes.c_uint32, dbl, i64, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -284,7 +289,7 @@ def chem_batch_run_until(ctx, t_end):
 
 
 def chem_run_homogeneous(ctx, t_end: float):
-    """Homogeneous (beam-off) stage of every train up to t_end (rate equations, Sec. 2.2)."""
+    """Homogeneous (beam-off) stage of every train up to t_end (rate equations, Sec. 2.3)."""
     _check(ctx, lib().chem_run_homogeneous(ctx, float(t_end)))
 
 
@@ -306,6 +311,20 @@ def chem_check_bounded_wait(ctx, limit_s: float):
     """Diagnostic: a device wait on a word nothing writes, bounded by limit_s; raises
     ChemError(CHEM_ETIMEOUT) (sticky on ctx)."""
     _check(ctx, lib().chem_check_bounded_wait(ctx, float(limit_s)))
+
+
+def chem_check_acceptance(ctx, precision: int, step: int, dt_s: float, d0sq, d1sq, rxn, id_lo, id_hi):
+    """The search's acceptance test on given squared separations: returns (tiered, exact)
+    boolean arrays (the tiered FP32/FP64 decision and u < p in FP64)."""
+    d0 = np.ascontiguousarray(d0sq, np.float64)
+    d1 = np.ascontiguousarray(d1sq, np.float64)
+    r = np.ascontiguousarray(rxn, np.int32)
+    lo = np.ascontiguousarray(id_lo, np.uint32)
+    hi = np.ascontiguousarray(id_hi, np.uint32)
+    out = np.zeros(d0.shape[0], np.uint8)
+    _check(ctx, lib().chem_check_acceptance(ctx, int(precision), int(step), float(dt_s), d0.shape[0], _ptr(d0),
+                                            _ptr(d1), _ptr(r), _ptr(lo), _ptr(hi), _ptr(out)))
+    return (out & 1) != 0, (out & 2) != 0
 
 
 def chem_batch_size(ctx) -> int:
@@ -413,7 +432,11 @@ def chem_get_stats(ctx) -> dict:
     return dict(graph_replays=st.graph_replays, kernel_launches=st.kernel_launches,
                 steps_launched=st.steps_launched, bytes_h2d=st.bytes_h2d, bytes_d2h=st.bytes_d2h,
                 phase_ms={PHASES[i]: st.phase_ms[i] for i in range(8)},
-                phase_launches={PHASES[i]: st.phase_launches[i] for i in range(8)})
+                phase_launches={PHASES[i]: st.phase_launches[i] for i in range(8)},
+                react_rounds_global=st.react_rounds_global, react_order_global=st.react_order_global,
+                react_order_radix=st.react_order_radix, max_conflict_pairs=st.max_conflict_pairs,
+                max_step_events=st.max_step_events, pairs_tested=st.pairs_tested,
+                pairs_in_cutoff=st.pairs_in_cutoff, pairs_accepted=st.pairs_accepted)
 
 
 def chem_set_profiling(ctx, on: bool):

@@ -98,6 +98,8 @@ struct chem_ctx {
   bool profiling = false;
   std::vector<cudaEvent_t> events;  // 2 * N_PHASES per captured step when profiling
   chem_stats stats{};
+  uint32_t seen_rounds_global = 0, seen_order_global = 0, seen_order_radix = 0;  // device counters seen
+  unsigned long long seen_tested = 0, seen_in_cut = 0, seen_accepted = 0;
   std::string err;
   chem_status status = CHEM_OK;
 };
@@ -221,6 +223,8 @@ chem_status download_trains(chem_ctx* ctx, std::vector<Train>& h) {
 }
 
 chem_status init_global(chem_ctx* ctx) {
+  ctx->seen_rounds_global = ctx->seen_order_global = ctx->seen_order_radix = 0;
+  ctx->seen_tested = ctx->seen_in_cut = ctx->seen_accepted = 0;
   CK(cudaMemsetAsync(ctx->d.g, 0, sizeof(Global), ctx->stream));
   const uint32_t ih = static_cast<uint32_t>(ctx->item_home);
   CK(cudaMemcpyAsync(&ctx->d.g->item_home, &ih, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
@@ -228,10 +232,31 @@ chem_status init_global(chem_ctx* ctx) {
   return CHEM_OK;
 }
 
+// Fold the device's reaction-branch counters (cumulative since the last reset) into the
+// context's statistics.
+void note_react_branches(chem_ctx* ctx, const Global& g) {
+  chem_stats& st = ctx->stats;
+  st.react_rounds_global += g.react_rounds_global - ctx->seen_rounds_global;
+  st.react_order_global += g.react_order_global - ctx->seen_order_global;
+  st.react_order_radix += g.react_order_radix - ctx->seen_order_radix;
+  ctx->seen_rounds_global = g.react_rounds_global;
+  ctx->seen_order_global = g.react_order_global;
+  ctx->seen_order_radix = g.react_order_radix;
+  st.max_conflict_pairs = std::max<int64_t>(st.max_conflict_pairs, g.max_conflict);
+  st.max_step_events = std::max<int64_t>(st.max_step_events, g.max_events);
+  st.pairs_tested += static_cast<int64_t>(g.pairs_tested - ctx->seen_tested);
+  st.pairs_in_cutoff += static_cast<int64_t>(g.pairs_in_cutoff - ctx->seen_in_cut);
+  st.pairs_accepted += static_cast<int64_t>(g.pairs_accepted - ctx->seen_accepted);
+  ctx->seen_tested = g.pairs_tested;
+  ctx->seen_in_cut = g.pairs_in_cutoff;
+  ctx->seen_accepted = g.pairs_accepted;
+}
+
 chem_status download_global(chem_ctx* ctx) {
   ctx->stats.bytes_d2h += sizeof(Global);
   CK(cudaMemcpyAsync(ctx->g_pinned, ctx->d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  note_react_branches(ctx, *ctx->g_pinned);
   return CHEM_OK;
 }
 
@@ -331,6 +356,7 @@ chem_status run_loop(chem_ctx* ctx) {
     CK(cudaMemcpyAsync(ctx->g_pinned, ctx->d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const Global& g = *ctx->g_pinned;
+    note_react_branches(ctx, g);
     ctx->stats.graph_replays += 1;
     ctx->stats.steps_launched += ctx->graph_steps;
     // per replay: one begin kernel, then every step's kernels (the end kernel of each step
@@ -385,7 +411,7 @@ void parallel_ranges(size_t n, F fn) {
   for (auto& x : th) x.join();
 }
 
-// Homogeneous stage (Sec. 2.2) of every train b with t_end[b] > its clock. Pending
+// Homogeneous stage (Sec. 2.3) of every train b with t_end[b] > its clock. Pending
 // species already due join the stage; one arriving inside it is an error (EINVAL, nothing
 // changed).
 chem_status homogeneous_run(chem_ctx* ctx, const double* t_end) {
@@ -960,6 +986,53 @@ chem_status chem_check_bounded_wait(chem_ctx* ctx, double limit_s) {
   if (st != 0)
     return fail(ctx, static_cast<chem_status>(st), "a bounded device wait ran out after %.3g s (status %d)",
                 limit_s, st);
+  return CHEM_OK;
+}
+
+chem_status chem_check_acceptance(chem_ctx* ctx, int32_t precision, uint32_t step, double dt_s, int64_t n,
+                                  const double* d0sq, const double* d1sq, const int32_t* rxn,
+                                  const uint32_t* id_lo, const uint32_t* id_hi, uint8_t* accept) {
+  chem_status s = check_ctx(ctx);
+  if (s) return s;
+  if (precision != CHEM_FP64 && precision != CHEM_FP32_LOCAL) return CHEM_EINVAL;
+  if (!(dt_s > 0.0) || !std::isfinite(dt_s) || n < 0 || n > (1ll << 24)) return CHEM_EINVAL;
+  if (n == 0) return CHEM_OK;
+  if (!d0sq || !d1sq || !rxn || !id_lo || !id_hi || !accept) return CHEM_EINVAL;
+  for (int64_t i = 0; i < n; ++i) {
+    if (rxn[i] < 0 || rxn[i] >= ctx->tables.n_rxn) return CHEM_EINVAL;
+    if (!(d0sq[i] >= 0.0) || !(d1sq[i] >= 0.0) || !std::isfinite(d0sq[i]) || !std::isfinite(d1sq[i]))
+      return CHEM_EINVAL;
+  }
+  const size_t un = static_cast<size_t>(n);
+  const size_t bytes = un * (8 + 8 + 4 + 4 + 4 + 1);
+  void* buf = nullptr;  // one temporary block, released before returning
+  if (ctx->alloc) buf = ctx->alloc((bytes + 255) & ~static_cast<size_t>(255), ctx->alloc_user);
+  else if (cudaMalloc(&buf, bytes) != cudaSuccess) { cudaGetLastError(); buf = nullptr; }
+  if (!buf) return CHEM_ENOMEM;
+  char* b = static_cast<char*>(buf);
+  double* dd0 = reinterpret_cast<double*>(b);
+  double* dd1 = dd0 + un;
+  int32_t* dr = reinterpret_cast<int32_t*>(dd1 + un);
+  uint32_t* dlo = reinterpret_cast<uint32_t*>(dr + un);
+  uint32_t* dhi = dlo + un;
+  uint8_t* dout = reinterpret_cast<uint8_t*>(dhi + un);
+  cudaError_t e = cudaMemcpyAsync(dd0, d0sq, un * 8, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dd1, d1sq, un * 8, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dr, rxn, un * 4, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dlo, id_lo, un * 4, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dhi, id_hi, un * 4, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = precision == CHEM_FP64
+            ? enqueue_check_accept_f64(ctx->d, static_cast<uint32_t>(n), step, dt_s, dd0, dd1, dr, dlo, dhi, dout,
+                                       ctx->stream)
+            : enqueue_check_accept_f32l(ctx->d, static_cast<uint32_t>(n), step, dt_s, dd0, dd1, dr, dlo, dhi,
+                                        dout, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(accept, dout, un, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (ctx->dfree) ctx->dfree(buf, (bytes + 255) & ~static_cast<size_t>(255), ctx->alloc_user);
+  else cudaFree(buf);
+  if (e != cudaSuccess) return fail(ctx, CHEM_ECUDA, "acceptance check: %s", cudaGetErrorString(e));
+  ctx->stats.kernel_launches += 1;
   return CHEM_OK;
 }
 

@@ -1,4 +1,4 @@
-// Homogeneous (beam-off) stage of a pulse train, Sec. 2.2 of arxiv 2509.03313: between
+// Homogeneous (beam-off) stage of a pulse train, Sec. 2.3 of arxiv 2509.03313: between
 // pulses, and after the last one, the species are followed as a well-mixed system by
 // the rate equations of Table 1 (Eq. 3, Eq. 4) instead of particle by particle.
 //

@@ -161,6 +161,51 @@ cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cu
   return cudaGetLastError();
 }
 
+// Diagnostic: the pair search's acceptance test on given squared separations d0^2 and
+// d1^2 of reaction rxn[i] for the pair (id_lo[i], id_hi[i]) at `step`, with the constants
+// the begin phase derives from dt. out[i] bit 0: the tiered test of the search (FP32
+// estimate, FP64 where undecided); bit 1: the FP64 test u < p itself on the same inputs
+// (in FP32-local mode, on the FP32 roundings of the squared separations).
+template <bool F32L>
+__global__ void __launch_bounds__(256) k_check_accept(const __grid_constant__ Dev d, uint32_t n, uint32_t step,
+                                                      double dt, const double* d0sq, const double* d1sq,
+                                                      const int32_t* rxn, const uint32_t* id_lo,
+                                                      const uint32_t* id_hi, uint8_t* out) {
+  __shared__ Train tr;
+  const Tables& tb = *d.tables;
+  if (threadIdx.x == 0) {
+    tr = d.trains[0];
+    tr.step = step;
+    for (int r = 0; r < tb.n_rxn; ++r) set_pair_constants(tr, tb, r, dt);
+  }
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int r = rxn[i];
+    const uint32_t lo = id_lo[i], hi = id_hi[i];
+    const double u = pair_uniform(lo, hi, step, tr.key0, tr.key1);
+    bool tiered, exact;
+    if constexpr (F32L) {
+      const float a = static_cast<float>(d0sq[i]), b = static_cast<float>(d1sq[i]);
+      tiered = accept_f32(a, b, r, tb, tr, lo, hi);
+      exact = u < bridge_p(sqrt(static_cast<double>(a)), sqrt(static_cast<double>(b)), tb.R[r], tr.ddt[r]);
+    } else {
+      tiered = accept_f64(d0sq[i], d1sq[i], r, tb, tr, lo, hi);
+      exact = u < bridge_p(sqrt(d0sq[i]), sqrt(d1sq[i]), tb.R[r], tr.ddt[r]);
+    }
+    out[i] = static_cast<uint8_t>((tiered ? 1 : 0) | (exact ? 2 : 0));
+  }
+}
+
+template <bool F32L>
+cudaError_t enqueue_check_accept(const Dev& d, uint32_t n, uint32_t step, double dt, const double* d0sq,
+                                 const double* d1sq, const int32_t* rxn, const uint32_t* id_lo,
+                                 const uint32_t* id_hi, uint8_t* out, cudaStream_t s) {
+  const uint32_t blocks = n ? (n + 255u) / 256u : 1u;
+  k_check_accept<F32L><<<blocks < 1024u ? blocks : 1024u, 256, 0, s>>>(d, n, step, dt, d0sq, d1sq, rxn, id_lo,
+                                                                       id_hi, out);
+  return cudaGetLastError();
+}
+
 template <bool F32L>
 cudaError_t enqueue_persistent(const Dev& d, const LaunchCfg& lc, int n_steps, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};

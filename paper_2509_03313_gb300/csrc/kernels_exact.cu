@@ -121,4 +121,10 @@ cudaError_t enqueue_persistent_f64(const Dev& d, const LaunchCfg& lc, int n_step
 
 cudaError_t persistent_occupancy_f64(int* blocks_per_sm) { return persistent_occupancy<false>(blocks_per_sm); }
 
+cudaError_t enqueue_check_accept_f64(const Dev& d, uint32_t n, uint32_t step, double dt, const double* d0sq,
+                                     const double* d1sq, const int32_t* rxn, const uint32_t* id_lo,
+                                     const uint32_t* id_hi, uint8_t* out, cudaStream_t s) {
+  return enqueue_check_accept<false>(d, n, step, dt, d0sq, d1sq, rxn, id_lo, id_hi, out, s);
+}
+
 }  // namespace chem

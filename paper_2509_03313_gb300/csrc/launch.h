@@ -1,5 +1,6 @@
 // Host-side entry points of the kernel translation units.
 #pragma once
+#include <cstdint>
 #include <cuda_runtime.h>
 
 namespace chem {
@@ -37,6 +38,14 @@ cudaError_t persistent_occupancy_f64(int* blocks_per_sm);
 cudaError_t enqueue_set_t_end(const Dev& d, const double* t_end_dev, cudaStream_t s);
 // one device thread waits, up to limit_s, for a word nothing writes (then CHEM_ETIMEOUT)
 cudaError_t enqueue_bounded_wait(const Dev& d, double limit_s, cudaStream_t s);
+
+// the pair acceptance test on given squared separations (diagnostic; one per precision)
+cudaError_t enqueue_check_accept_f64(const Dev& d, uint32_t n, uint32_t step, double dt, const double* d0sq,
+                                     const double* d1sq, const int32_t* rxn, const uint32_t* id_lo,
+                                     const uint32_t* id_hi, uint8_t* out, cudaStream_t s);
+cudaError_t enqueue_check_accept_f32l(const Dev& d, uint32_t n, uint32_t step, double dt, const double* d0sq,
+                                      const double* d1sq, const int32_t* rxn, const uint32_t* id_lo,
+                                      const uint32_t* id_hi, uint8_t* out, cudaStream_t s);
 
 // homog.cu: homogeneous (beam-off) stage of the trains with Train::hx_sel set
 cudaError_t enqueue_homogeneous(const Dev& d, int blocks, cudaStream_t s);

@@ -90,14 +90,30 @@ __global__ void k_noalloc_setup(Dev d, Tables tb, Train tr) {
   }
 }
 
+// Copy the caller's species into the scratch state. The inputs live on the device, so
+// they are checked here: a type outside [0, n_types), an id at or above the id limit (it
+// would overlap the type bits) or a position that is not finite and inside [-L/2, L/2)^3
+// raises CHEM_EINVAL and is not written; every later phase then does nothing and the
+// store kernel reports no species and no events.
 __global__ void k_noalloc_load(Dev d, int32_t n, const uint32_t* id, const int32_t* type,
                                const double* xyz) {
+  const Train& tr = d.trains[0];
+  const int n_types = d.tables->n_types;
   for (int32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const uint32_t ty = static_cast<uint32_t>(type[s]);
-    d.sx[s] = xyz[3 * s];
-    d.sy[s] = xyz[3 * s + 1];
-    d.sz[s] = xyz[3 * s + 2];
-    d.stid[s] = (id[s] << 3) | ty;
+    const int32_t ty = type[s];
+    const uint32_t ids = id[s];
+    const double x = xyz[3 * s], y = xyz[3 * s + 1], z = xyz[3 * s + 2];
+    // written so that NaN fails every comparison
+    const bool in_box = x >= -tr.halfL && x < tr.halfL && y >= -tr.halfL && y < tr.halfL &&
+                        z >= -tr.halfL && z < tr.halfL;
+    if (ty < 0 || ty >= n_types || ids >= tr.id_limit || !in_box) {
+      raise_status(d.g, CHEM_EINVAL);
+      continue;
+    }
+    d.sx[s] = x;
+    d.sy[s] = y;
+    d.sz[s] = z;
+    d.stid[s] = (ids << 3) | static_cast<uint32_t>(ty);
     d.cell_sorted[s] = 0;
     d.dead[s] = 0;
     atomicAdd(reinterpret_cast<unsigned long long*>(&d.trains[0].counts[ty]), 1ull);

@@ -133,6 +133,13 @@ __device__ __forceinline__ int wrap_cell(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// Per-reaction constants of the acceptance test for a step of length dt: D_AB dt (the
+// exponents' denominator) in FP64 and its reciprocal in FP32 (the first tier).
+__device__ __forceinline__ void set_pair_constants(Train& tr, const Tables& tb, int r, double dt) {
+  tr.ddt[r] = __dmul_rn(tb.D_AB[r], dt);
+  tr.inv_ddt_f[r] = 1.0f / static_cast<float>(tr.ddt[r]);
+}
+
 // ======================================================================== begin
 // One CTA. Per train: release count, clock step, free-jump decision, hash grid and
 // cutoffs of this step; then the slot offsets of the releases and the step counters.
@@ -238,8 +245,7 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
       const double rc = __dadd_rn(tb.R[q], __dmul_rn(tr.c, sqrt(__dmul_rn(__dmul_rn(2.0, tb.D_AB[q]), dt))));
       tr.rc2[q] = __dmul_rn(rc, rc);
       tr.rc2f[q] = static_cast<float>(tr.rc2[q]);
-      tr.ddt[q] = __dmul_rn(tb.D_AB[q], dt);
-      tr.inv_ddt_f[q] = 1.0f / static_cast<float>(tr.ddt[q]);
+      set_pair_constants(tr, tb, q, dt);
       atomicMax(&sb.rcmax_bits[b], static_cast<unsigned long long>(__double_as_longlong(rc)));
     } else {
       const int ty = q - MAXR;
@@ -771,6 +777,20 @@ struct SearchSmem {
   int ct_train[8];
 };
 
+// Warp-reduced pair-search counters, added once per warp to the context's totals.
+__device__ __forceinline__ void add_pair_counts(const Dev& d, uint32_t tested, uint32_t in_cut) {
+  unsigned long long t = tested, c = in_cut;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (t) atomicAdd(&d.g->pairs_tested, t);
+    if (c) atomicAdd(&d.g->pairs_in_cutoff, c);
+  }
+}
+
 __device__ __forceinline__ void emit_candidate(const Dev& d, uint32_t s_lo, uint32_t s_hi, uint32_t id_lo,
                                                uint32_t id_hi, int r, int b, double d1sq) {
   const uint32_t c = atomicAdd(&d.g->n_cand, 1u);
@@ -945,6 +965,7 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
   it_next = __shfl_sync(0xffffffffu, it_next, 0);
   uint2 rec_next = make_uint2(0u, 0u);
   if (it_next < n_items) rec_next = d.items[it_next];
+  uint32_t n_tested = 0, n_in_cut = 0;  // pair-search counters of this lane
   for (;;) {
     if (it_next >= n_items) break;
     const uint2 rec = rec_next;
@@ -1077,6 +1098,8 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
             }
           }
         }
+        n_tested += (h < hmax) ? 1u : 0u;
+        n_in_cut += pass ? 1u : 0u;
         const uint32_t bal = __ballot_sync(0xffffffffu, pass);
         if (bal) {
           const uint32_t base = q.n;
@@ -1098,6 +1121,7 @@ __device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
     flush_pairs<F32L>(d, tb, tr, b, hs, q, s0, vf, lane);
     __syncwarp();
   }
+  add_pair_counts(d, n_tested, n_in_cut);
 }
 
 // ---- one thread per home species
@@ -1209,6 +1233,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
   __syncwarp();
   const uint32_t lanemask_lt = (1u << lane) - 1u;
   const uint32_t n_chunks = (n_live + 31u) / 32u;
+  uint32_t n_tested = 0, n_in_cut = 0;  // pair-search counters of this lane
   uint32_t c_next = 0;
   if (lane == 0) c_next = atomicAdd(&d.g->item_ctr, 1u);
   c_next = __shfl_sync(0xffffffffu, c_next, 0);
@@ -1462,6 +1487,8 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             float fx, fy, fz;
             pass[u] = vu[u] && sep(u, fx, fy, fz) < hrow[__float_as_uint(vj[u].w) & 7u];
             any = any || pass[u];
+            n_tested += vu[u] ? 1u : 0u;
+            n_in_cut += pass[u] ? 1u : 0u;
           }
           if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
@@ -1497,6 +1524,8 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
                 pass = d1sq < c2;
               }
             }
+            n_tested += vu[u] ? 1u : 0u;
+            n_in_cut += pass ? 1u : 0u;
             push(pass, jj, 0.f, 0.f, 0.f, 0.f, rx1, ry1, rz1, d1sq);
           }
         }
@@ -1506,10 +1535,12 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
     c_next = __shfl_sync(0xffffffffu, c_next, 0);
   }
   tps_flush<F32L>(d, tb, q, vf, lane);
+  add_pair_counts(d, n_tested, n_in_cut);
 }
 
 // ======================================================================== react
-// One reaction per species (Sec. 2.3: reactants react on encounter):
+// One reaction per species (Sec. 2.4: diffusion-controlled reactions, reactants react
+// on encounter):
 //  1. phase_match_fast (all CTAs): an accepted pair whose two species are in no other
 //     accepted pair is committed at once; the others go to a conflict list.
 //  2. phase_match_rounds (one CTA): rounds of locally-dominant selection over the
@@ -2062,13 +2093,23 @@ struct SerialSmem {
 // the sort runs in shared memory; otherwise in the global event buffers.
 static __device__ void phase_react_serial(const Dev& d, SerialSmem& sm, uint32_t* sbuf) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (sbuf == nullptr || !phase_match_rounds_smem(d, sm.match, sbuf)) phase_match_rounds(d, sm.match);
+  const uint32_t n_conflict = d.g->n_conflict;  // read before the rounds (all threads, uniform)
+  const bool rounds_smem = sbuf != nullptr && phase_match_rounds_smem(d, sm.match, sbuf);
+  if (!rounds_smem) phase_match_rounds(d, sm.match);
   const bool ok = block_status_ok(d);
   const uint32_t E = ok ? min(d.g->n_events, d.cap_cand) : 0u;
   const uint32_t* okeys;
   const uint32_t* order;
   uint32_t* order_out = nullptr;
   uint32_t* pref;
+  if (tid == 0 && ok) {  // branch record (read by chem_get_stats)
+    Global* g = d.g;
+    if (!rounds_smem && n_conflict > 0) g->react_rounds_global += 1;
+    if (n_conflict > g->max_conflict) g->max_conflict = n_conflict;
+    g->pairs_accepted += min(g->n_cand, d.cap_cand);
+    if (E > g->max_events) g->max_events = E;
+    if (E > 0 && (sbuf == nullptr || E > static_cast<uint32_t>(EV_SMEM_CAP))) g->react_order_global += 1;
+  }
   if (sbuf != nullptr && E <= static_cast<uint32_t>(EV_SMEM_CAP)) {
     uint32_t* k0 = sbuf;
     uint32_t* v0 = sbuf + EV_SMEM_CAP;
@@ -2076,8 +2117,9 @@ static __device__ void phase_react_serial(const Dev& d, SerialSmem& sm, uint32_t
     uint32_t* v1 = sbuf + 3 * EV_SMEM_CAP;
     for (uint32_t i = tid; i < E; i += nt) { k0[i] = d.ev_k0[i]; v0[i] = d.ev_v0[i]; }
     __syncthreads();
-    const int p = block_bucket_sort(k0, v0, k1, v1, E, sm.sort, sm.scan) ? 0
-                                                                           : block_sort_pairs(k0, v0, k1, v1, E, sm.sort);
+    const bool bucketed = block_bucket_sort(k0, v0, k1, v1, E, sm.sort, sm.scan);
+    if (!bucketed && tid == 0 && E > 0) d.g->react_order_radix += 1;
+    const int p = bucketed ? 0 : block_sort_pairs(k0, v0, k1, v1, E, sm.sort);
     okeys = p ? k1 : k0;
     order = p ? v1 : v0;
     order_out = d.ev_v0;

@@ -142,6 +142,16 @@ struct Global {
   uint32_t sort_any;      // at least one pass executed (else the order is unchanged)
   uint32_t ev_parity;     // event order in ev_v1 (1) or ev_v0 (0), prefix in the other key buffer
   uint32_t never_set;     // stays 0: the word chem_check_bounded_wait waits for
+  // which branches reaction resolution took (cumulative since the last reset)
+  uint32_t react_rounds_global;  // steps whose conflict rounds ran in global memory
+  uint32_t react_order_global;   // steps whose event order ran in global memory
+  uint32_t react_order_radix;    // steps whose shared-memory event order needed the radix sort
+  uint32_t max_conflict;         // most conflicting accepted pairs in one step
+  uint32_t max_events;           // most events in one step
+  // pair-search work (cumulative since the last reset)
+  unsigned long long pairs_tested;     // neighbour pairs whose separation was tested
+  unsigned long long pairs_in_cutoff;  // of them, reacting type pairs inside the cutoff
+  unsigned long long pairs_accepted;   // of them, accepted (the steps' reactive pairs)
 };
 
 // Accepted reactive pair.

@@ -1,10 +1,11 @@
-"""Pulse trains that alternate the step-by-step stage and the rate equations (Sec. 2.2):
+"""Pulse trains that alternate the step-by-step stage and the rate equations (Sec. 2.1
+workflow, Sec. 2.3 rate equations):
 the step-by-step (SBS) chemistry runs while the beam is on, the rate equations of Table 1
 (Eq. 3, Eq. 4) for the rest of the beam-off time up to the next pulse, and after the last
 pulse for 10 s. Every step of both stages runs in the CUDA library; this module only
 sequences the calls for the trains of a batched context and reads their tallies.
 
-The post-irradiation analysis of Sec. 3 (the H2O2 yield as the slope of its
+The post-irradiation analysis of Sec. 3.3 (the H2O2 yield as the slope of its
 post-irradiation concentration against dose, Fig. Concentration-Dose and Fig.
 G-yield_Dav, and the average dose rate above which radicals build up from pulse to pulse)
 works on those tallies on the host.
@@ -85,7 +86,7 @@ def concentration(count, L_nm: float):
 
 def dose_slope_yield(dose_Gy, conc_mol_per_L):
     """Yield as the least-squares slope of post-irradiation concentration against dose,
-    the way Sec. 3 derives the H2O2 yield from Fig. Concentration-Dose. With water at
+    the way Sec. 3.3 derives the H2O2 yield from Fig. Concentration-Dose. With water at
     1 kg/L the slope in (mol/L)/Gy is mol/J; returned in mol/J and in molecules/100 eV."""
     d = np.asarray(dose_Gy, dtype=np.float64)
     c = np.asarray(conc_mol_per_L, dtype=np.float64)
@@ -98,7 +99,7 @@ def buildup_fraction(run, radicals: Sequence[int] = (0, 1, 2), nu=None):
     """Per train, the radicals (e_aq, OH, H by default) left when the next pulse starts,
     as a fraction of those present when the previous beam-on stage ended, for the last
     inter-pulse interval of its plan. Near 0: steady state reached between pulses;
-    large: the radicals build up (Sec. 3). With the stoichiometry ``nu`` the numbers left
+    large: the radicals build up (Sec. 3.3). With the stoichiometry ``nu`` the numbers left
     are the rate equations' real ones (before the rounding to whole events, whose +-1
     noise would dominate in small boxes), else the whole counts."""
     kinds, counts = run["kinds"], run["counts"]
@@ -123,7 +124,7 @@ def buildup_fraction(run, radicals: Sequence[int] = (0, 1, 2), nu=None):
 
 def threshold_dose_rate(avg_dose_rates, fractions, level: float = 0.01):
     """Lowest average dose rate whose build-up fraction exceeds ``level`` (the SDR/UHDR
-    threshold of Sec. 3, read as: radicals no longer fall below ``level`` of their
+    threshold of Sec. 3.3, read as: radicals no longer fall below ``level`` of their
     end-of-pulse number before the next pulse), or None."""
     dav = np.asarray(avg_dose_rates, dtype=np.float64)
     f = np.asarray(fractions, dtype=np.float64)

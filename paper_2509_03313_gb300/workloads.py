@@ -62,7 +62,7 @@ WATER_REACTIONS: List[Reaction] = [
 # Species mix of the 2,000-species uniform workload: e 600, OH 600, H 120, H3O+ 600,
 # OH- 80. Used as the type ratio of the synthetic tracks too.
 MIX_COUNTS = np.array([600, 600, 120, 600, 80, 0, 0], dtype=np.int64)
-LET_EV_PER_NM = 0.96  # 70 MeV protons, 0.96 keV/um (Sec. 2.4)
+LET_EV_PER_NM = 0.96  # 70 MeV protons, 0.96 keV/um (Sec. 2.5)
 
 
 def _rng(seed: int, stream: int = 0) -> np.random.Generator:
@@ -220,7 +220,7 @@ def multi_pulse(seed: int, n_pulses: int = 10, period_s: float = 1e-4, fwhm_s: f
 
 def hybrid_stages(n_pulses: int, period_s: float, fwhm_s: float, tail_s: float = 10.0,
                   sbs_after_s: float = 0.0) -> List[tuple]:
-    """The alternation of Sec. 2.2: step-by-step chemistry while the beam is on (each
+    """The alternation of Sec. 2.1: step-by-step chemistry while the beam is on (each
     pulse [T_k, T_k + fwhm_s), extended by sbs_after_s), the rate equations for the rest
     of the beam-off time up to the next pulse, and for tail_s after the last pulse.
     Returns the calls in order as (kind, t_end) with kind "sbs" or "ode"."""
@@ -319,7 +319,8 @@ def dose_series(avg_dose_rates=(1.0, 1e4), pulse_dose_rate: float = 1e6,
 
 def volume_scaling(L: float, seed: int, counts_at_200nm: Sequence[int] = MIX_COUNTS,
                    t_end: float = 1e-3, dt_min: float = 1e-12, dt_max: float = 1.5e-8) -> Workload:
-    """Volume-scaling study (Sec. 2.3, verification of the periodic boundaries): one
+    """Volume-scaling study (Sec. 2.2 setup, Sec. 3.1 results: verification of the
+    periodic boundaries): one
     homogeneous mixture concentration in cubes of side L (0.2, 0.5 and 1.0 um), i.e.
     counts_at_200nm scaled by (L / 200 nm)^3 (2,000 species at 0.2 um, 250,000 at 1 um),
     followed to t_end = 1 ms with log-growing dt from 1 ps up to dt_max. The default

@@ -49,6 +49,7 @@ def gpu_run(wl, seed, precision=chem.CHEM_FP64, t_end=None, capacity=None, recor
         if record:
             out["events"] = chem.chem_get_events(ctx)
             out["steps"] = chem.chem_get_step_log(ctx)
+        out["stats"] = chem.chem_get_stats(ctx)
     finally:
         chem.chem_destroy(ctx)
     return out
@@ -111,8 +112,9 @@ def assert_fp64_parity(g, o, L, pos_tol_rel=1e-12):
 
 
 def gpu_batch_run(wls, seeds, train_ids=None, precision=chem.CHEM_FP64, record=True,
-                  launch_mode=chem.CHEM_LAUNCH_AUTO, steps_per_launch=0, t_end=None):
-    """Run several trains in one batched context; returns one result dict per train."""
+                  launch_mode=chem.CHEM_LAUNCH_AUTO, steps_per_launch=0, t_end=None, stats=None):
+    """Run several trains in one batched context; returns one result dict per train
+    (and fills the dict ``stats`` with the context's counters when given)."""
     import torch
     train_ids = train_ids or list(range(len(wls)))
     cfgs, keep = [], []
@@ -150,6 +152,8 @@ def gpu_batch_run(wls, seeds, train_ids=None, precision=chem.CHEM_FP64, record=T
                 o["events"] = ev[ev["train"] == b]
                 o["steps"] = st[st["train"] == b]
             outs.append(o)
+        if stats is not None:
+            stats.update(chem.chem_get_stats(ctx))
     finally:
         chem.chem_destroy(ctx)
     return outs

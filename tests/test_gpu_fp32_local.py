@@ -81,7 +81,7 @@ def test_free_diffusion_msd_with_regridding():
 
 @pytest.mark.parametrize("wl_name", ["dense_uniform", "tracks"])
 def test_g_values_match_fp64_reference_over_seeds(wl_name):
-    seeds = list(range(32)) if wl_name == "dense_uniform" else list(range(16))
+    seeds = list(range(32))
     g32 = {k: [] for k in SPECIES_G}
     g64 = {k: [] for k in SPECIES_G}
     for s in seeds:

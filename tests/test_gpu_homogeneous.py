@@ -1,4 +1,4 @@
-"""GPU homogeneous (beam-off) stage against the reference (Sec. 2.2, Eq. 3 / Eq. 4).
+"""GPU homogeneous (beam-off) stage against the reference (Sec. 2.3, Eq. 3 / Eq. 4).
 
 The library integrates the rate equations with its own scheme, so real extents agree
 within the integrators' tolerances; whole events, counts, the re-created particles and

@@ -1,4 +1,4 @@
-"""Volume-scaling study (Sec. 2.3): the SBS with periodic boundaries must give the same
+"""Volume-scaling study (Sec. 2.2, Sec. 3.1): the SBS with periodic boundaries must give the same
 concentrations in boxes of 0.2, 0.5 and 1.0 um (no finite-size effect, pin P7), stay
 close to a well-mixed stochastic simulation (the paper's Kinetiscope comparison, here an
 independent Gillespie implementation; the paper saw up to 20 % for H2 and 12 % for H2O2 at

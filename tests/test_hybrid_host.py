@@ -1,5 +1,5 @@
-"""Host logic of the pulse-train alternation (Sec. 2.2) and of the post-irradiation
-analysis (Sec. 3), on the CPU: the call sequencing against a recording stand-in for the
+"""Host logic of the pulse-train alternation (Sec. 2.1) and of the post-irradiation
+analysis (Sec. 3.3), on the CPU: the call sequencing against a recording stand-in for the
 library, and the analysis against closed forms and numpy's least squares."""
 import numpy as np
 import pytest

@@ -71,16 +71,20 @@ def test_water_table_conserves_charge_and_atoms():
     assert events.sum() > 100
 
 
-def test_rate_equations_and_stochastic_simulation_agree_within_one_percent():
-    """The paper's check of its rate equations against Kinetiscope (Sec. 2.3: below 1 %
+def test_rate_equations_and_stochastic_simulation_agree():
+    """The paper's check of its rate equations against Kinetiscope (Sec. 2.3 setup,
+    Sec. 3.1: below 1 %
     for every species): the reference rate equations (extents, scipy Radau) against the
-    mean of independent Gillespie runs, the volume-scaling mixture in a 0.5 um box."""
+    mean of 16 independent Gillespie runs, the volume-scaling mixture in a 0.5 um box.
+    Bound per species with a mean above 200 molecules: 1 % of the mean plus 4 standard
+    errors of the 16-run mean (0.2-1.6 % here) plus 2 molecules; the differences seen
+    are below 0.8 %."""
     from oracle import homogeneous as H
     wl = W.volume_scaling(500.0, seed=100)
     n0 = np.bincount(wl.pulses[0].types, minlength=7)
     T = [1e-6, 1e-4, 1e-3]
-    runs = np.array([G.ssa(n0, 500.0, W.WATER_REACTIONS, T, seed=s)[0] for s in range(4)], float)
-    mean, sem = runs.mean(axis=0), runs.std(axis=0, ddof=1) / 2.0
+    runs = np.array([G.ssa(n0, 500.0, W.WATER_REACTIONS, T, seed=s)[0] for s in range(16)], float)
+    mean, sem = runs.mean(axis=0), runs.std(axis=0, ddof=1) / 4.0
     nu = H.stoichiometry(7, W.WATER_REACTIONS)
     for i, t in enumerate(T):
         ode = n0 + nu @ H.extents(n0.astype(float), 500.0, t, W.WATER_REACTIONS)

@@ -1,4 +1,4 @@
-"""Pins of the reference homogeneous (beam-off) stage, Sec. 2.2 with the rate equations
+"""Pins of the reference homogeneous (beam-off) stage, Sec. 2.3 with the rate equations
 Eq. 3 / Eq. 4: closed-form solutions of single reactions, the concentration form of the
 same equations integrated by another scheme, exact conservation of charge and atoms
 after rounding to whole events, unbiased rounding, uniform re-created positions, and the
