@@ -40,6 +40,16 @@ WORKLOAD = ("single pulse of 200 synthetic proton tracks (Gaussian spurs, sigma 
 # the state where the phase rewrites it, one read where it only reads it; sort passes
 # read and write one (key, value) pair.
 STATE_BYTES = {"fp32l": 16, "fp64": 28}
+# Minimum lane instructions of the pair search's two kinds of work (FP32-local mode): a
+# tested neighbour pair is one 16-byte load, three subtractions, a squared norm (one
+# multiply, two fused multiply-adds), the type pair's cutoff and a compare; a pair
+# inside its cutoff adds one acceptance test: the Philox4x32-10 block (ten rounds of two
+# wide multiplies and two three-input XORs), the start separation from the two stored
+# displacements (two loads, six adds, a squared norm), the two square roots and the
+# exp(-a) bound, and the compare with the uniform.
+ALU_OPS_TESTED = 9
+ALU_OPS_IN_CUTOFF = 66
+ISSUE_LANE_OPS_PER_S = 152 * 4 * 32 * 2.07e9
 PHASE_BYTES = {"diffuse": lambda s: 2 * s, "gather": lambda s: 2 * s, "search": lambda s: s,
                "sort": lambda s: 16, "release": lambda s: 0, "begin": lambda s: 0, "react": lambda s: 0}
 
@@ -122,28 +132,49 @@ def aggregate_over_ranks(species_steps, seconds, device=None):
 
 
 # ------------------------------------------------------------------- CPU reference arm
+# The reference is timed on whole trajectories (every SBS step from 1 ps to 1 us) of the
+# benchmark workload in a smaller box with the same track density, species density and
+# time-step schedule (workloads.tracks_same_density): its species-steps cost what the
+# 1e6-species trajectory's cost, early and late steps alike, in seconds of CPU time.
+ORACLE_L_NM = 1600.0
+ORACLE_KIND = "oracle (numpy/scipy FP64, the repository's reference)"
+
+
 def _oracle_worker(args):
-    seed, n_species, n_steps = args
+    seed, L, n_warm, n_timed = args
     from oracle import sbs
     from paper_2509_03313_gb300 import workloads as W
-    wl = W.single_pulse_tracks(seed, n_species=n_species)
-    o = sbs.from_workload(wl, seed=seed, record=False)
-    t0 = time.perf_counter()
-    for _ in range(n_steps):
-        o.step_once(wl.t_end)
-    return o.species_steps, time.perf_counter() - t0
+    ss, busy = 0, 0.0
+    for k in range(n_warm + n_timed):
+        wl = W.tracks_same_density(seed + 7919 * k, L)
+        o = sbs.from_workload(wl, seed=seed + 7919 * k, record=False)
+        t0 = time.perf_counter()
+        o.run_until(wl.t_end)
+        if k >= n_warm:
+            busy += time.perf_counter() - t0
+            ss += o.species_steps
+    return ss, busy
 
 
-def oracle_rate(n_proc: int, n_species: int, n_steps: int):
-    """Aggregate species-steps/s of n_proc independent reference runs (one per core)."""
+def oracle_rate(n_proc: int, L: float, n_warm: int, n_timed: int):
+    """Aggregate species-steps/s of n_proc reference processes (one per core), each timing
+    n_timed whole trajectories after n_warm untimed ones."""
     ctx = mp.get_context("spawn")
     with ctx.Pool(n_proc) as pool:
         t0 = time.perf_counter()
-        res = pool.map(_oracle_worker, [(1000 + i, n_species, n_steps) for i in range(n_proc)])
+        res = pool.map(_oracle_worker, [(1000 + i, L, n_warm, n_timed) for i in range(n_proc)])
         wall = time.perf_counter() - t0
     ss = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
     return ss / busy, ss, busy, wall
+
+
+def oracle_sample_text(n_proc, n_traj, L):
+    from paper_2509_03313_gb300 import workloads as W
+    n = W.tracks_same_density(1, L).n_species
+    return (f"{n_proc} processes x {n_traj} whole trajectories (1 ps -> 1 us, all SBS steps) of the track "
+            f"workload at the benchmark's density in a {L / 1000:g} um box ({n} species, "
+            f"{max(1, int(round(200 * (L / 5000) ** 2)))} tracks)")
 
 
 def run_reference_arm(args):
@@ -152,18 +183,16 @@ def run_reference_arm(args):
         return 0
     cores = os.cpu_count() or 1
     n_proc = max(1, min(cores, args.ref_procs or cores))
-    # warm-up and timed steps: each step = n_proc workers x 1 SBS step of the trajectory
-    rate, ss, busy, wall = oracle_rate(n_proc, args.species, args.warmup + args.steps)
+    # each benchmark step: every process runs one whole trajectory
+    rate, ss, busy, wall = oracle_rate(n_proc, ORACLE_L_NM, args.warmup, args.steps)
+    sample = oracle_sample_text(n_proc, args.steps, ORACLE_L_NM)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * busy / max(1, args.warmup + args.steps),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * busy / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "species": args.species, "L_nm": 5000.0,
-                       "sample": f"first {args.warmup + args.steps} SBS steps (1 ps onwards) of "
-                                 f"{n_proc} independent trajectories, one per process"},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": n_proc, "kind": "oracle",
-                             "sample": f"{n_proc} processes x {args.warmup + args.steps} SBS steps of "
-                                       f"the {args.species}-species trajectory"},
+            "config": {"workload": WORKLOAD, "species": args.species, "L_nm": 5000.0, "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": n_proc, "kind": ORACLE_KIND,
+                             "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -286,10 +315,9 @@ def run_gpu_arm(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_proc = max(1, min(cores, args.ref_procs or cores))
-        rate, ss, busy, wall = oracle_rate(n_proc, args.species, args.cpu_steps)
-        cpu = {"value": rate, "unit": UNIT, "cores": n_proc, "kind": "oracle",
-               "sample": f"{n_proc} processes x first {args.cpu_steps} SBS steps (1 ps onwards) of "
-                         f"independent {args.species}-species trajectories; {busy:.1f} s"}
+        rate, ss, busy, wall = oracle_rate(n_proc, ORACLE_L_NM, 0, args.cpu_trajectories)
+        cpu = {"value": rate, "unit": UNIT, "cores": n_proc, "kind": ORACLE_KIND,
+               "sample": oracle_sample_text(n_proc, args.cpu_trajectories, ORACLE_L_NM) + f"; {busy:.1f} s"}
     seed0 = 10_000 * (rank + 1)
     wl = W.single_pulse_tracks(seed0, n_species=args.species, n_tracks=args.tracks)
     pulse = wl.pulses[0]
@@ -300,7 +328,7 @@ def run_gpu_arm(args):
     results = {}
     modes = [("fp32l", chem.CHEM_FP32_LOCAL, args.steps)]
     if not args.no_fp64:
-        modes.append(("fp64", chem.CHEM_FP64, max(1, args.fp64_steps)))
+        modes.append(("fp64", chem.CHEM_FP64, args.fp64_steps if args.fp64_steps > 0 else args.steps))
     for name, prec, k_steps in modes:
         ctx, keep = make_ctx(chem, wl, prec, seed0, cap, stream.cuda_stream, alloc,
                              profiling=not args.no_phase_events)
@@ -353,7 +381,9 @@ def run_gpu_arm(args):
             ms = st1["phase_ms"][ph]
             nl = st1["phase_launches"][ph]
             per_phase[ph] = {"ms_total": ms, "launches": nl}
-        results[name] = dict(times=times, ss=ss, tot=tot, G_H2O2=g_h2o2, G_OH=g_oh, G_e=g_e,
+        work = {k: st1[k] - st0[k] for k in ("pairs_tested", "pairs_in_cutoff", "pairs_accepted",
+                                             "steps_advanced")}
+        results[name] = dict(times=times, ss=ss, tot=tot, G_H2O2=g_h2o2, G_OH=g_oh, G_e=g_e, work=work,
                              launches=st1["kernel_launches"] - st0["kernel_launches"],
                              phases=per_phase, clocks=clk.summary(), e2e_t=e2e_t, e2e_ss=e2e_ss,
                              tuned=tuned,
@@ -368,6 +398,9 @@ def run_gpu_arm(args):
                                                   tuned=bres.get("autotuned") if bres else None)
     vres = None if args.no_volume else run_volume_scaling(args, chem, W, torch, stream, alloc, rank, world, dev)
     lres = run_large(args, chem, W, torch, stream, alloc) if not args.no_large and rank == 0 else None
+    mres = run_multi_pulse(args, chem, W, torch, stream, alloc) if not args.no_multi_pulse and rank == 0 else None
+    xres = (run_beyond_l2(args, chem, W, torch, stream, alloc, flush)
+            if not args.no_beyond_l2 and rank == 0 else None)
     if rank != 0:
         return 0
     value = ss_all / t_max
@@ -397,6 +430,31 @@ def run_gpu_arm(args):
         same = rec_tuning is not None and tuned is not None and rec_tuning[2:] == tuned[2:]
         return recorded_traffic(kern) if kern and same else None
 
+    def search_alu_roofline(res):
+        # The search is bound by instruction issue, not by memory: its algorithmic work is
+        # counted in lane instructions, ALU_OPS_TESTED per neighbour pair whose separation
+        # is tested and ALU_OPS_IN_CUTOFF per pair inside its cutoff (one acceptance test),
+        # against the issue ceiling of the part (one warp instruction per cycle and
+        # scheduler: 152 SMs x 4 x 32 lanes x the maximum SM clock).
+        ph = res["phases"]["search"]
+        w = res["work"]
+        if ph["ms_total"] <= 0.0 or w["pairs_tested"] <= 0:
+            return None
+        ops = ALU_OPS_TESTED * w["pairs_tested"] + ALU_OPS_IN_CUTOFF * w["pairs_in_cutoff"]
+        ach = ops / (ph["ms_total"] * 1e-3)
+        peak_alu = ISSUE_LANE_OPS_PER_S
+        return {"bound": "alu", "kernel": "search", "achieved": ach, "peak": peak_alu,
+                "unit": "lane-instr/s (algorithmic)", "frac": ach / peak_alu, "traffic": traffic_of("search"),
+                "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (one warp instruction per cycle "
+                               "per scheduler)",
+                "algorithmic_ops": f"{ALU_OPS_TESTED} lane-instr per tested pair + {ALU_OPS_IN_CUTOFF} per pair "
+                                   "inside the cutoff",
+                "pairs_tested_per_launch": w["pairs_tested"] / max(1, ph["launches"]),
+                "pairs_in_cutoff_per_launch": w["pairs_in_cutoff"] / max(1, ph["launches"]),
+                "pairs_tested_per_s": w["pairs_tested"] / (ph["ms_total"] * 1e-3),
+                "pairs_in_cutoff_per_s": w["pairs_in_cutoff"] / (ph["ms_total"] * 1e-3),
+                "avg_launch_ms": ph["ms_total"] / max(1, ph["launches"])}
+
     def roofline_of(phase):
         ph = phases[phase]
         if ph["ms_total"] <= 0.0:
@@ -415,7 +473,7 @@ def run_gpu_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "species": int(pulse.n), "L_nm": wl.L,
-                   "t_end_s": wl.t_end, "sbs_steps_per_trajectory": int(round(r["ss"] / len(r["times"]) / pulse.n)) if pulse.n else 0,
+                   "t_end_s": wl.t_end, "sbs_steps_per_trajectory": r["work"]["steps_advanced"] / len(r["times"]),
                    "mode": "FP32-local positions, FP64 clock/probabilities/tallies",
                    "l2": "flushed (256 MiB write) before every timed trajectory",
                    "phase_events": not args.no_phase_events,
@@ -426,8 +484,10 @@ def run_gpu_arm(args):
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
                 "includes": "chem_reset + chem_inject_pulse (host arrays) + chem_run_until + chem_tally"},
         "gpu_launches": int(r["launches"]),
-        "roofline": roofline_of(dom) if have_phases else None,
+        "roofline": (search_alu_roofline(r) if dom == "search" else roofline_of(dom)) if have_phases else None,
+        "roofline_hbm_search": roofline_of("search") if have_phases else None,
         "roofline_diffuse": roofline_of("diffuse") if have_phases else None,
+        "search_work_per_trajectory": {k: v / len(r["times"]) for k, v in r["work"].items()},
         "phases_ms": {p: round(v["ms_total"], 3) for p, v in phases.items()},
         "clocks": r["clocks"],
         "G_per_100eV_fp32l": {"H2O2": float(np.mean(r["G_H2O2"])), "OH": float(np.mean(r["G_OH"])),
@@ -457,6 +517,10 @@ def run_gpu_arm(args):
         line["volume_scaling"] = vres
     if lres is not None:
         line["large"] = lres
+    if mres is not None:
+        line["multi_pulse"] = mres
+    if xres is not None:
+        line["beyond_l2"] = xres
     line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     return 0
@@ -726,6 +790,133 @@ def run_volume_scaling(args, chem, W, torch, stream, alloc, rank=0, world=1, dev
                         "0.2/0.5/1.0 um, log dt from 1 ps to 1 ms, FP32-local"}
 
 
+def phase_rooflines(phases, ss, state_bytes, work, peak, peak_src):
+    """HBM roofline of every phase kernel over a run (algorithmic bytes of the phase per
+    species-step, summed, over the phase's summed device time), and the search's issue
+    roofline from the pair counters."""
+    out = {}
+    diff_launches = max(1, phases["diffuse"]["launches"])
+    for ph in ("diffuse", "sort", "gather", "search"):
+        ms = phases[ph]["ms_total"]
+        if ms <= 0.0:
+            continue
+        nb = PHASE_BYTES[ph](state_bytes) * ss
+        if ph == "sort":
+            nb *= phases["sort"]["launches"] / diff_launches
+        ach = nb / (ms * 1e-3) / 1e9
+        out[ph] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                   "peak_source": peak_src, "ms_total": ms, "launches": phases[ph]["launches"],
+                   "algorithmic_bytes": f"{PHASE_BYTES[ph](state_bytes)} B per species per launch"}
+    ms = phases["search"]["ms_total"]
+    if ms > 0.0 and work["pairs_tested"] > 0:
+        ops = ALU_OPS_TESTED * work["pairs_tested"] + ALU_OPS_IN_CUTOFF * work["pairs_in_cutoff"]
+        out["search_alu"] = {"bound": "alu", "achieved": ops / (ms * 1e-3), "peak": ISSUE_LANE_OPS_PER_S,
+                             "unit": "lane-instr/s (algorithmic)",
+                             "frac": ops / (ms * 1e-3) / ISSUE_LANE_OPS_PER_S,
+                             "pairs_tested_per_s": work["pairs_tested"] / (ms * 1e-3),
+                             "pairs_in_cutoff_per_s": work["pairs_in_cutoff"] / (ms * 1e-3)}
+    return out
+
+
+def timed_trajectories(chem, torch, wl, precision, seeds, n_warm, stream, alloc, flush, tuning=None):
+    """Whole trajectories of a single-pulse workload in one context with per-phase device
+    timers: n_warm untimed, then one per seed timed with CUDA events (L2 flushed before
+    each). Returns species-steps, seconds, per-phase times, counters and G(H2O2)."""
+    pulse = wl.pulses[0]
+    cap = int(pulse.n * 1.3) + 4096
+    ctx, keep = make_ctx(chem, wl, precision, seeds[0], cap, stream.cuda_stream, alloc, profiling=True)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    try:
+        if tuning is not None:
+            chem.chem_set_tuning(ctx, *tuning)
+        for w in range(n_warm):
+            trajectory(chem, ctx, pulse, seeds[0] + 31 + w, wl.t_end, torch, stream, flush, ev)
+        chem.chem_set_profiling(ctx, True)
+        st0 = chem.chem_get_stats(ctx)
+        ss, tot, g = 0, 0.0, []
+        for sd in seeds:
+            tot += trajectory(chem, ctx, pulse, sd, wl.t_end, torch, stream, flush, ev)
+            tal = chem.chem_tally(ctx, 7, 9)
+            ss += tal["species_steps"]
+            g.append(float(tal["G"][6]))
+        st1 = chem.chem_get_stats(ctx)
+    finally:
+        chem.chem_destroy(ctx)
+    phases = {ph: {"ms_total": st1["phase_ms"][ph], "launches": st1["phase_launches"][ph]}
+              for ph in ("diffuse", "sort", "gather", "search", "react", "begin", "release")}
+    work = {k: st1[k] - st0[k] for k in ("pairs_tested", "pairs_in_cutoff", "pairs_accepted", "steps_advanced")}
+    return ss, tot, phases, work, g
+
+
+def run_beyond_l2(args, chem, W, torch, stream, alloc, flush):
+    """The benchmark workload at 20x the volume (13.6 um box, same track and species
+    density, 2e7 species): state arrays of 320 MB (FP32-local) and 560 MB (FP64), beyond
+    the 126 MB L2, so every phase's traffic reaches HBM. Per-phase HBM rooflines and the
+    search's issue roofline in both precisions."""
+    wl = W.tracks_same_density(seed=4242, L=13572.0)
+    peak, peak_src = measured_peaks()
+    out = {"workload": f"single pulse of tracks at the benchmark's density, 13.6 um box, "
+                       f"{wl.n_species} species, log dt 1 ps -> 1 us", "species": int(wl.n_species)}
+    tuning = tuple(int(v) for v in args.tuned.split(",")) if args.tuned else None
+    for name, prec, n_timed in (("fp32l", chem.CHEM_FP32_LOCAL, 2), ("fp64", chem.CHEM_FP64, 1)):
+        if name == "fp64" and args.no_fp64:
+            continue
+        seeds = [4300 + k for k in range(n_timed)]
+        ss, tot, phases, work, g = timed_trajectories(chem, torch, wl, prec, seeds, 1, stream, alloc, flush,
+                                                      tuning if name == "fp32l" else None)
+        out[name] = {"value": ss / tot, "unit": UNIT, "ms_per_trajectory": 1e3 * tot / n_timed,
+                     "trajectories": n_timed, "G_H2O2": g,
+                     "sbs_steps_per_trajectory": work["steps_advanced"] / n_timed,
+                     "phases_ms": {p: round(v["ms_total"], 3) for p, v in phases.items()},
+                     "rooflines": phase_rooflines(phases, ss, STATE_BYTES[name], work, peak, peak_src)}
+    return out
+
+
+def run_multi_pulse(args, chem, W, torch, stream, alloc):
+    """Multi-pulse build-up (10 pulses of 1 us at 1e6 Gy/s pulse dose rate, 0.1 ms apart,
+    163 tracks x 1,800 species each, step by step throughout, species carried across the
+    intervals), FP32-local: wall time, species-steps/s, live species and G(H2O2) at the
+    end of every pulse and before the next."""
+    wl = W.multi_pulse(seed=11)
+    n = wl.n_species
+    period = 1e-4
+    stops = sorted({round(k * period + d, 12) for k in range(len(wl.pulses)) for d in (1e-6, period)})
+    stops = [t for t in stops if t <= wl.t_end] + ([wl.t_end] if wl.t_end not in stops else [])
+    cfg, keep = chem.make_config(wl.L, wl.D, wl.reactions, seed=11, precision=chem.CHEM_FP32_LOCAL,
+                                 dt_min=wl.schedule.dt_min, dt_max=wl.schedule.dt_max,
+                                 dt_growth=wl.schedule.dt_growth, capacity_species=n + 200_000,
+                                 capacity_pending=n, capacity_candidates=max(4096, n // 4),
+                                 stream=stream.cuda_stream, allocator=alloc)
+    ctx = chem.chem_init(cfg)
+    try:
+        if args.tuned:
+            chem.chem_set_tuning(ctx, *[int(v) for v in args.tuned.split(",")])
+        for p in wl.pulses:
+            chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        st0 = chem.chem_get_stats(ctx)
+        g, live = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in stops:
+            chem.chem_run_until(ctx, t)
+            tal = chem.chem_tally(ctx, 7, 9)
+            g.append(round(float(tal["G"][6]), 4))
+            live.append(int(tal["counts"][:7].sum()))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st1 = chem.chem_get_stats(ctx)
+        tal = chem.chem_tally(ctx, 7, 9)
+    finally:
+        chem.chem_destroy(ctx)
+    return {"workload": "10 pulses of 1 us (163 tracks x 1,800 species each, arrivals uniform over the "
+                        "pulse) every 0.1 ms, 5 um box, step by step throughout (dt reset at every "
+                        "arrival, 10 ps -> 1 us)",
+            "species_created": int(n), "wall_s": wall, "value": tal["species_steps"] / wall, "unit": UNIT,
+            "sbs_steps": st1["steps_advanced"] - st0["steps_advanced"],
+            "timing": "host clock around the run_until calls (each syncs)",
+            "t_s": stops, "live": live, "G_H2O2": g, "peak_live": max(live)}
+
+
 def run_large(args, chem, W, torch, stream, alloc):
     """Large build-up (10 um, 20 pulses, 20 Gy, ~7.5e6 species created), step by step
     throughout, FP32-local and FP64: G(H2O2) at the end of every pulse and before the
@@ -778,8 +969,10 @@ def main():
     ap.add_argument("--species", type=int, default=1_000_000)
     ap.add_argument("--tracks", type=int, default=200,
                     help="number of tracks (species per track = species / tracks)")
-    ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--cpu-steps", type=int, default=4)
+    ap.add_argument("--fp64-steps", type=int, default=0,
+                    help="FP64 trajectories (default: as many as --steps, same seeds)")
+    ap.add_argument("--cpu-trajectories", type=int, default=1,
+                    help="whole reference trajectories per process in the cpu_baseline sample")
     ap.add_argument("--ref-procs", type=int, default=0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -799,6 +992,8 @@ def main():
     ap.add_argument("--no-volume", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 10 um, 20-pulse build-up")
     ap.add_argument("--no-large-fp64", action="store_true", help="run it in FP32-local mode only")
+    ap.add_argument("--no-multi-pulse", action="store_true", help="skip the 10-pulse build-up (0.1 ms apart)")
+    ap.add_argument("--no-beyond-l2", action="store_true", help="skip the 2e7-species workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference_arm(args)

@@ -243,11 +243,13 @@ chem_status chem_batch_homogeneous_report(chem_ctx* ctx, int32_t train, double* 
                                           int64_t* integrator_steps);
 
 /* Choose, by timing short runs from the current state, the launch form (one kernel per
- * phase in a graph, or the persistent cooperative kernel), the steps per graph replay,
- * the hash resolution limit (cells per axis at small cutoffs, i.e. the cell size) and
- * the pair-search mapping (threads per cell): 0 = one thread per home species, else the
- * number of home species one warp takes per work item of a cell. The device state is saved before and restored after every trial; trials run
- * past the end time. FP64 results do not depend on the choice; FP32-local results
+ * phase in a graph, or the persistent cooperative kernel), the steps per graph replay
+ * and the hash resolution limit (cells per axis at small cutoffs, i.e. the cell size).
+ * The pair-search mapping is kept (set it with chem_set_tuning): 0 = one thread per
+ * home species; 1..32 = cell tiles, the number of home species one warp takes per work
+ * item of a cell; -1 = chosen per step (cell tiles when the last step found more than 3
+ * pairs inside the cutoffs per live species; the default). The device state is saved
+ * before and restored after every trial; trials run past the end time. FP64 results do not depend on the choice; FP32-local results
  * depend on the hash resolution only through rounding. budget_ms bounds the time spent
  * (at least one trial runs). chosen[4] = {steps_per_launch, cells_per_axis_limit,
  * species_per_item, launch_mode} when chosen is not NULL. */
@@ -255,7 +257,7 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen);
 
 /* Apply tuning parameters directly, in the layout chem_autotune reports: tuning[4] =
  * {steps_per_launch (1..1024), cells_per_axis_limit (>= 3; clamped to the allocated hash),
- * species_per_item (0..64, 0 = one thread per home species), launch_mode
+ * species_per_item (-1..32: -1 per step, 0 one thread per home species), launch_mode
  * (CHEM_LAUNCH_PHASES or CHEM_LAUNCH_PERSISTENT)}.
  * Allowed between runs; the device state is kept. Results depend on the parameters as
  * described for chem_autotune. Out-of-range values: CHEM_EINVAL, nothing changed. No
@@ -296,6 +298,8 @@ typedef struct chem_stats {
   int64_t pairs_tested;
   int64_t pairs_in_cutoff;
   int64_t pairs_accepted;
+  int64_t steps_advanced;       /* SBS steps in which at least one train advanced       */
+  int64_t steps_cell_tiles;     /* of them, steps whose pair search ran the cell tiles  */
 } chem_stats;
 chem_status chem_get_stats(const chem_ctx* ctx, chem_stats* out);
 /* on != 0: re-capture the step graph with CUDA events around every phase kernel (adds
@@ -312,7 +316,7 @@ chem_status chem_set_profiling(chem_ctx* ctx, int32_t on);
  * created by chem_init with dt_min = dt_max = dt_s would take that step.
  *
  * Memory: it calls no cudaMalloc, cudaFree or allocator callback. All working memory is
- * one file-scope __device__ array of about 3.7 MB sized for CHEM_NOALLOC_MAX_SPECIES
+ * one file-scope __device__ array of about 4.2 MB sized for CHEM_NOALLOC_MAX_SPECIES
  * species; every GPU that loads this library holds that array until the process exits.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any

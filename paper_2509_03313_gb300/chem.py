@@ -71,7 +71,8 @@ class chem_stats(ctypes.Structure):
                 ("react_order_global", ctypes.c_int64), ("react_order_radix", ctypes.c_int64),
                 ("max_conflict_pairs", ctypes.c_int64), ("max_step_events", ctypes.c_int64),
                 ("pairs_tested", ctypes.c_int64), ("pairs_in_cutoff", ctypes.c_int64),
-                ("pairs_accepted", ctypes.c_int64)]
+                ("pairs_accepted", ctypes.c_int64), ("steps_advanced", ctypes.c_int64),
+                ("steps_cell_tiles", ctypes.c_int64)]
 
 
 PHASES = ("begin", "release", "diffuse", "sort", "gather", "search", "react", "persistent")
@@ -436,7 +437,8 @@ def chem_get_stats(ctx) -> dict:
                 react_rounds_global=st.react_rounds_global, react_order_global=st.react_order_global,
                 react_order_radix=st.react_order_radix, max_conflict_pairs=st.max_conflict_pairs,
                 max_step_events=st.max_step_events, pairs_tested=st.pairs_tested,
-                pairs_in_cutoff=st.pairs_in_cutoff, pairs_accepted=st.pairs_accepted)
+                pairs_in_cutoff=st.pairs_in_cutoff, pairs_accepted=st.pairs_accepted,
+                steps_advanced=st.steps_advanced, steps_cell_tiles=st.steps_cell_tiles)
 
 
 def chem_set_profiling(ctx, on: bool):

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <limits>
 #include <string>
@@ -90,8 +91,8 @@ struct chem_ctx {
   int steps_per_launch = 16;
   bool persistent = false;
   int cell_factor_x100 = 1600;  // hash cells per species (x100) of the runtime grid limit
-  int item_home = 0;             // pair search: 0 = one thread per home species, else
-                                 // home species per warp work item
+  int item_home = -1;            // pair search: 0 = one thread per home species, 1..32 =
+                                 // cell tiles of that many homes, -1 = chosen per step
   Global* g_pinned = nullptr;  // host copy of the global counters
   double* t_end_pinned = nullptr;
   double* t_end_dev = nullptr;
@@ -100,6 +101,7 @@ struct chem_ctx {
   chem_stats stats{};
   uint32_t seen_rounds_global = 0, seen_order_global = 0, seen_order_radix = 0;  // device counters seen
   unsigned long long seen_tested = 0, seen_in_cut = 0, seen_accepted = 0;
+  uint32_t seen_steps = 0, seen_cells_steps = 0;
   std::string err;
   chem_status status = CHEM_OK;
 };
@@ -222,19 +224,35 @@ chem_status download_trains(chem_ctx* ctx, std::vector<Train>& h) {
   return CHEM_OK;
 }
 
-chem_status init_global(chem_ctx* ctx) {
-  ctx->seen_rounds_global = ctx->seen_order_global = ctx->seen_order_radix = 0;
-  ctx->seen_tested = ctx->seen_in_cut = ctx->seen_accepted = 0;
-  CK(cudaMemsetAsync(ctx->d.g, 0, sizeof(Global), ctx->stream));
-  const uint32_t ih = static_cast<uint32_t>(ctx->item_home);
-  CK(cudaMemcpyAsync(&ctx->d.g->item_home, &ih, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+// The Global fields that select the pair-search mapping for a tuning value ih (-1
+// adaptive, 0 one thread per species, 1..32 cell tiles of that many homes).
+void set_mapping(Global& g, int ih) {
+  g.item_home = ih < 0 ? static_cast<uint32_t>(ITEM_HOME) : static_cast<uint32_t>(ih);
+  g.search_adaptive = ih < 0 ? 1u : 0u;
+}
+
+chem_status upload_mapping(chem_ctx* ctx, int ih) {
+  Global g{};
+  set_mapping(g, ih);
+  static_assert(offsetof(Global, search_adaptive) == offsetof(Global, item_home) + 4, "adjacent fields");
+  CK(cudaMemcpyAsync(&ctx->d.g->item_home, &g.item_home, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                     ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return CHEM_OK;
 }
 
-// Fold the device's reaction-branch counters (cumulative since the last reset) into the
-// context's statistics.
-void note_react_branches(chem_ctx* ctx, const Global& g) {
+chem_status init_global(chem_ctx* ctx) {
+  ctx->seen_rounds_global = ctx->seen_order_global = ctx->seen_order_radix = 0;
+  ctx->seen_tested = ctx->seen_in_cut = ctx->seen_accepted = 0;
+  ctx->seen_steps = 0;
+  ctx->seen_cells_steps = 0;
+  CK(cudaMemsetAsync(ctx->d.g, 0, sizeof(Global), ctx->stream));
+  return upload_mapping(ctx, ctx->item_home);
+}
+
+// Fold the device's counters (reaction-resolution branches, pair-search work, steps;
+// cumulative since the last reset) into the context's statistics.
+void note_device_counters(chem_ctx* ctx, const Global& g) {
   chem_stats& st = ctx->stats;
   st.react_rounds_global += g.react_rounds_global - ctx->seen_rounds_global;
   st.react_order_global += g.react_order_global - ctx->seen_order_global;
@@ -247,6 +265,10 @@ void note_react_branches(chem_ctx* ctx, const Global& g) {
   st.pairs_tested += static_cast<int64_t>(g.pairs_tested - ctx->seen_tested);
   st.pairs_in_cutoff += static_cast<int64_t>(g.pairs_in_cutoff - ctx->seen_in_cut);
   st.pairs_accepted += static_cast<int64_t>(g.pairs_accepted - ctx->seen_accepted);
+  st.steps_advanced += g.steps_active - ctx->seen_steps;
+  ctx->seen_steps = g.steps_active;
+  st.steps_cell_tiles += g.cells_steps - ctx->seen_cells_steps;
+  ctx->seen_cells_steps = g.cells_steps;
   ctx->seen_tested = g.pairs_tested;
   ctx->seen_in_cut = g.pairs_in_cutoff;
   ctx->seen_accepted = g.pairs_accepted;
@@ -256,7 +278,7 @@ chem_status download_global(chem_ctx* ctx) {
   ctx->stats.bytes_d2h += sizeof(Global);
   CK(cudaMemcpyAsync(ctx->g_pinned, ctx->d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  note_react_branches(ctx, *ctx->g_pinned);
+  note_device_counters(ctx, *ctx->g_pinned);
   return CHEM_OK;
 }
 
@@ -296,7 +318,7 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
 int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 7 + ctx->d.passes; }
 
 chem_status capture_graph(chem_ctx* ctx) {
-  ctx->lc.search_tps = ctx->item_home == 0 ? 1 : 0;
+  ctx->lc.search_tps = ctx->item_home == 0 ? 1 : (ctx->item_home > 0 ? 0 : 2);
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
@@ -356,7 +378,7 @@ chem_status run_loop(chem_ctx* ctx) {
     CK(cudaMemcpyAsync(ctx->g_pinned, ctx->d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const Global& g = *ctx->g_pinned;
-    note_react_branches(ctx, g);
+    note_device_counters(ctx, g);
     ctx->stats.graph_replays += 1;
     ctx->stats.steps_launched += ctx->graph_steps;
     // per replay: one begin kernel, then every step's kernels (the end kernel of each step
@@ -883,6 +905,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     d.s4 = static_cast<float4*>(A(cap * 16));
     d.t4 = static_cast<float4*>(A(cap * 16));
     d.td4 = static_cast<float4*>(A(cap * 16));
+    d.sd4 = static_cast<float4*>(A(cap * 16));
   }
   d.cap_items = static_cast<uint32_t>(cap + cap / ITEM_HOME + 64);
   d.items = static_cast<uint2*>(A(static_cast<size_t>(d.cap_items) * 8));
@@ -1191,11 +1214,14 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   std::vector<Train> tr0;
   s = download_trains(ctx, tr0);
   if (s) return s;
-  // ---- candidates: runtime hash limit, species per work item, steps per replay
+  // ---- candidates: runtime hash limit, steps per replay, launch form. The search
+  // mapping is not a candidate: trials time the next few steps only, while the mapping's
+  // payoff changes along a trajectory; it stays the context's (by default chosen per
+  // step from the pairs inside the cutoffs, see phase_begin).
   const int n_alloc = tr0[0].n_alloc;
   std::vector<int> n_cands;
   for (double f : {1.0, 0.75, 0.55, 0.4}) n_cands.push_back(std::max(3, static_cast<int>(n_alloc * f)));
-  const int ih_cands[3] = {0, 32, 64};  // 0: one thread per home species
+  const int ih_cands[1] = {ctx->item_home};
   const int spl_cands[2] = {8, 32};
   const bool mode_cands[2] = {false, true};  // per-phase graph, persistent launch
   const bool saved_persistent = ctx->persistent;
@@ -1209,10 +1235,10 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   const int saved_spl = ctx->steps_per_launch;
   const bool saved_prof = ctx->profiling;
   ctx->profiling = false;
-  for (int combo = 0; combo < 4 * 3; ++combo) {
-    const bool pers = mode_cands[combo / 6];
-    const int spl = spl_cands[(combo / 3) % 2];
-    const int ih = ih_cands[combo % 3];
+  for (int combo = 0; combo < 4; ++combo) {
+    const bool pers = mode_cands[combo / 2];
+    const int spl = spl_cands[combo % 2];
+    const int ih = ih_cands[0];
     ctx->persistent = pers;
     ctx->steps_per_launch = spl;
     ctx->item_home = ih;  // selects the search kernel of the captured graph
@@ -1235,7 +1261,7 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
         CK(cudaMemcpyAsync(&gfix, d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         gfix.epoch = std::max(gfix.epoch, epoch_now) + 1;  // stale hash stamps never match
-        gfix.item_home = static_cast<uint32_t>(ih);
+        set_mapping(gfix, ih);
         CK(cudaMemcpyAsync(d.g, &gfix, sizeof(Global), cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         const int reps = std::max(1, 24 / spl);
@@ -1278,7 +1304,7 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
     CK(cudaMemcpyAsync(&gfix, snap + global_off, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     gfix.epoch = std::max(gfix.epoch, epoch_now) + 1;
-    gfix.item_home = static_cast<uint32_t>(best_ih);
+    set_mapping(gfix, best_ih);
     CK(cudaMemcpyAsync(d.g, &gfix, sizeof(Global), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
   }
@@ -1315,7 +1341,7 @@ chem_status chem_set_tuning(chem_ctx* ctx, const int32_t* tuning) {
   if (s) return s;
   if (!tuning) return CHEM_EINVAL;
   const int spl = tuning[0], n_lim = tuning[1], ih = tuning[2], mode = tuning[3];
-  if (spl < 1 || spl > 1024 || n_lim < 3 || ih < 0 || ih > ITEM_HOME ||
+  if (spl < 1 || spl > 1024 || n_lim < 3 || ih < -1 || ih > ITEM_HOME ||
       (mode != CHEM_LAUNCH_PHASES && mode != CHEM_LAUNCH_PERSISTENT))
     return CHEM_EINVAL;
   std::vector<Train> tr;
@@ -1324,9 +1350,8 @@ chem_status chem_set_tuning(chem_ctx* ctx, const int32_t* tuning) {
   for (auto& t : tr) t.n_max = std::min(n_lim, t.n_alloc);
   s = upload_trains(ctx, tr);
   if (s) return s;
-  const uint32_t ih32 = static_cast<uint32_t>(ih);
-  CK(cudaMemcpyAsync(&ctx->d.g->item_home, &ih32, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
+  s = upload_mapping(ctx, ih);
+  if (s) return s;
   ctx->item_home = ih;
   ctx->steps_per_launch = spl;
   ctx->persistent = mode == CHEM_LAUNCH_PERSISTENT;

@@ -4,6 +4,7 @@
 #pragma once
 #include "launch.h"
 #include "phases.cuh"
+#include "search_cells.cuh"
 
 namespace chem {
 
@@ -12,8 +13,7 @@ union PhaseSmem {
   SerialSmem serial;
   ProductsSmem products;
   EndSmem end;
-  SearchSmem<true> search32;
-  SearchSmem<false> search64;
+  ScSmem<8> cells;
   TpsSmem<true, 8> tps32;
   TpsSmem<false, 8> tps64;
   uint32_t hist[MAX_PASSES][RADIX];
@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(256) k_gather(const __grid_constant__ Dev d) {
 
 template <bool F32L>
 __global__ void __launch_bounds__(256, 4) k_search(const __grid_constant__ Dev d) {
-  __shared__ SearchSmem<F32L> sm;
-  phase_search<F32L>(d, sm);
+  __shared__ ScSmem<8> sm;
+  phase_search_cells<F32L, 8>(d, sm);
 }
 
 constexpr int TPS_WARPS = 4;  // warps per CTA of the one-thread-per-species search
@@ -96,12 +96,11 @@ __global__ void __launch_bounds__(PERSIST_THREADS) k_persistent(const __grid_con
     }
     phase_gather<F32L>(d);
     grid_sync(d);
-    if (d.g->item_home == 0) {
+    if (d.g->search_cells_now) {
+      phase_search_cells<F32L, 8>(d, sm.cells);
+    } else {
       if constexpr (F32L) phase_search_tps<true, 8>(d, sm.tps32);
       else phase_search_tps<false, 8>(d, sm.tps64);
-    } else {
-      if constexpr (F32L) phase_search<true>(d, sm.search32);
-      else phase_search<false>(d, sm.search64);
     }
     grid_sync(d);
     phase_match_fast(d);
@@ -148,8 +147,9 @@ cudaError_t enqueue_phases(const Dev& d, const LaunchCfg& lc, cudaStream_t s, cu
   k_gather<F32L><<<lc.stream_blocks, 256, 0, s>>>(d);
   mark(2 * PH_GATHER + 1);
   mark(2 * PH_SEARCH);
-  if (lc.search_tps) k_search_tps<F32L><<<2 * lc.search_blocks, 32 * TPS_WARPS, 0, s>>>(d);
-  else k_search<F32L><<<lc.search_blocks, 256, 0, s>>>(d);
+  // one mapping, or both with the one not chosen for the step returning at once
+  if (lc.search_tps != 0) k_search_tps<F32L><<<2 * lc.search_blocks, 32 * TPS_WARPS, 0, s>>>(d);
+  if (lc.search_tps != 1) k_search<F32L><<<lc.search_blocks, 256, 0, s>>>(d);
   mark(2 * PH_SEARCH + 1);
   mark(2 * PH_REACT);
   e = enqueue_react_head(d, lc, s);

@@ -16,7 +16,8 @@ struct LaunchCfg {
   int search_blocks;      // grid of the pair search
   int sort_blocks;        // resident CTAs of a sort pass
   int persistent_blocks;  // resident CTAs of the persistent step kernel
-  int search_tps;         // pair search with one thread per home species (else warp per item)
+  int search_tps;         // pair search: 1 one thread per home species, 0 cell tiles,
+                          // 2 both launched, the step's choice runs (adaptive)
 };
 
 // kernels_exact.cu (FP64 arithmetic without contraction)

@@ -31,7 +31,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(25
 
 // Byte layout of the scratch array.
 struct Layout {
-  size_t sx, sy, sz, stid, tx, ty, tz, ttid, tdx, tdy, tdz, items, touch, cell_sorted, sortbuf, dead, cell_info, occ, lookback, cand,
+  size_t sx, sy, sz, stid, tx, ty, tz, ttid, tdx, tdy, tdz, s4, t4, items, touch, cell_sorted, sortbuf, dead, cell_info, occ, lookback, cand,
       ev_list, alive0, alive1, ev_k0, ev_k1, ev_v0, ev_v1, ev_log, step_log, pend, trains, tables,
       global, total;
 };
@@ -44,6 +44,7 @@ constexpr Layout make_layout() {
   L.sx = take(M * 8); L.sy = take(M * 8); L.sz = take(M * 8); L.stid = take(M * 4);
   L.tx = take(M * 8); L.ty = take(M * 8); L.tz = take(M * 8); L.ttid = take(M * 4);
   L.tdx = take(M * 8); L.tdy = take(M * 8); L.tdz = take(M * 8);
+  L.s4 = take(M * 16); L.t4 = take(M * 16);  // FP32 cell offsets (the search's prefilter)
   L.items = take((M + M / ITEM_HOME + 64) * 8);
   L.touch = take(M * 4);
   L.cell_sorted = take(M * 4);
@@ -70,7 +71,7 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = LAYOUT.total;
 
 }  // namespace
 
-// The shared working memory of chem_step_noalloc (about 3.7 MB).
+// The shared working memory of chem_step_noalloc (about 4.2 MB).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 namespace {
@@ -293,6 +294,8 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   d.tdx = reinterpret_cast<double*>(b + LAYOUT.tdx);
   d.tdy = reinterpret_cast<double*>(b + LAYOUT.tdy);
   d.tdz = reinterpret_cast<double*>(b + LAYOUT.tdz);
+  d.s4 = reinterpret_cast<float4*>(b + LAYOUT.s4);
+  d.t4 = reinterpret_cast<float4*>(b + LAYOUT.t4);
   d.items = reinterpret_cast<uint2*>(b + LAYOUT.items);
   d.touch = reinterpret_cast<uint32_t*>(b + LAYOUT.touch);
   d.cap_items = NA_MAX_SPECIES + NA_MAX_SPECIES / ITEM_HOME + 64;

@@ -358,6 +358,19 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     g->n_dead = 0;
     g->epoch += 1;
     g->any_active = sb.any;
+    // Search mapping of this step. Cell tiles amortise the neighbour-cell lookups over
+    // the homes of a cell and test a pair only when the types react; one thread per
+    // species has the shorter per-item latency chain. Adaptive: cell tiles when the last
+    // step found more than 3 pairs inside the cutoffs per live species (the measured
+    // crossover on track workloads); results do not depend on the mapping.
+    if (g->search_adaptive) {
+      const unsigned long long inc = g->pairs_in_cutoff - g->incut_mark;
+      g->search_cells_now = inc > 3ull * static_cast<unsigned long long>(g->n_live) ? 1u : 0u;
+    } else {
+      g->search_cells_now = g->item_home != 0u ? 1u : 0u;
+    }
+    g->incut_mark = g->pairs_in_cutoff;
+    if (g->search_cells_now && sb.any) g->cells_steps += 1;
   }
   for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&d.g->hist[0][0])[i] = 0u;
   __syncthreads();
@@ -642,6 +655,7 @@ __device__ void phase_gather(const Dev& d) {
     }
     if (F32L) {
       d.s4[s] = d.t4[i];
+      if (d.sd4) d.sd4[s] = d.td4[i];
     } else {
       d.sx[s] = d.tx[i]; d.sy[s] = d.ty[i]; d.sz[s] = d.tz[i]; d.stid[s] = d.ttid[i];
       if (d.s4) d.s4[s] = d.t4[i];
@@ -657,7 +671,7 @@ __device__ void phase_gather(const Dev& d) {
     if (s + 1 == n_live || kf[s + 1] != key) ci[1] = static_cast<int>(s + 1);
     // pair-search work item: a cell's first slot and every item_home-th slot (none when
     // the search runs one thread per species)
-    if (item_home != 0 && (first || (s % item_home) == 0)) {
+    if (item_home != 0 && d.g->search_cells_now && (first || (s % item_home) == 0)) {
       const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, key);
       if (d.trains[b].active && !d.trains[b].free_jump) {
         const uint32_t it = atomicAdd(&d.g->n_items, 1u);
@@ -672,13 +686,10 @@ __device__ void phase_gather(const Dev& d) {
 // ======================================================================== search
 // For every unordered pair of live species whose types react (Table 1), separated by
 // less than the reaction's cutoff under the minimum image (Eq. 2), evaluate the
-// encounter probability and keep the pair if its uniform falls below it.
-//
-// One warp per work item: up to ITEM_HOME home species of one cell, staged in shared
-// memory. The own cell (slots after the item's first slot) and the 13 forward cells of
-// the half shell are flattened into one neighbour list; lanes stride over it (coalesced
-// loads) and each lane tests its neighbour against every home species (shared-memory
-// broadcast). With at least 3 cells per axis each unordered pair is visited once.
+// encounter probability and keep the pair if its uniform falls below it. Two mappings
+// visit the same pairs: one thread per home species (below) and cell tiles
+// (search_cells.cuh). With at least 3 cells per axis each unordered pair is visited
+// once: the own cell's later slots and the forward half of the surrounding cells.
 
 // Half-shell offsets within two cells: entry 0 is the own cell, 1..13 the cells one away
 // in fwd_offset's order, 14..62 the cells two away; each keeps the offsets (dz, dy, dx)
@@ -719,63 +730,17 @@ __device__ __forceinline__ void fwd_offset(int k, int& dx, int& dy, int& dz) {
   dz = 0; dy = 0; dx = 1;
 }
 
-template <bool F32L>
-struct SearchWarpSmem;
-
-template <>
-struct SearchWarpSmem<true> {
-  float4 pos[ITEM_HOME];   // offsets + tid bits
-};
-
-template <>
-struct SearchWarpSmem<false> {
-  double x[ITEM_HOME], y[ITEM_HOME], z[ITEM_HOME];
-  uint32_t tid[ITEM_HOME];
-};
-
-struct SearchRanges {
-  uint32_t start[N_FWD];   // first slot of each neighbour range
-  uint32_t off[N_FWD];     // its offset in the flattened neighbour list
-};
-
-// Squared cutoff of every type pair for the warp's current train (negative when the
-// pair does not react): FP32 in FP32-local mode, FP64 (exact) in FP64 mode.
-template <bool F32L>
-struct CutoffTable {
-  using T = typename std::conditional<F32L, float, double>::type;
-  T rc2[MAXT * MAXT];
-};
-
-// Pairs inside the cutoff, queued per warp and resolved with one pair per lane.
-template <bool F32L>
-struct PairQueue;
-
-template <>
-struct PairQueue<true> {
-  static constexpr int CAP = 96;
-  uint32_t hj[CAP];                  // home index in the item
-  uint32_t j[CAP];                   // neighbour slot
-  float fx[CAP], fy[CAP], fz[CAP], f2[CAP];
-  uint32_t n;
-};
-
-template <>
-struct PairQueue<false> {
-  static constexpr int CAP = 64;
-  uint32_t hj[CAP];
-  uint32_t j[CAP];
-  double rx[CAP], ry[CAP], rz[CAP], d2[CAP];
-  uint32_t n;
-};
-
-template <bool F32L>
-struct SearchSmem {
-  SearchWarpSmem<F32L> w[8];
-  SearchRanges rg[8];
-  CutoffTable<F32L> ct[8];
-  PairQueue<F32L> q[8];
-  int ct_train[8];
-};
+// FP32 separation x_j - x_i of two species held as offsets from their cells' corners,
+// the neighbour's cell lying (cfx, cfy, cfz) cells away (cell side hf), and its square.
+// Written with explicit roundings (no contraction left to the compiler) so that every
+// kernel that forms it, both search mappings and the acceptance, gets the same bits.
+__device__ __forceinline__ float sep_f32(float cfx, float cfy, float cfz, float hf, const float4& vj,
+                                         const float4& vi, float& fx, float& fy, float& fz) {
+  fx = __fsub_rn(__fmaf_rn(cfx, hf, vj.x), vi.x);
+  fy = __fsub_rn(__fmaf_rn(cfy, hf, vj.y), vi.y);
+  fz = __fsub_rn(__fmaf_rn(cfz, hf, vj.z), vi.z);
+  return __fmaf_rn(fz, fz, __fmaf_rn(fy, fy, __fmul_rn(fx, fx)));
+}
 
 // Warp-reduced pair-search counters, added once per warp to the context's totals.
 __device__ __forceinline__ void add_pair_counts(const Dev& d, uint32_t tested, uint32_t in_cut) {
@@ -874,258 +839,8 @@ __device__ __forceinline__ bool accept_f64(double d0sq, double d1sq, int r, cons
   return u < bridge_p(sqrt(d0sq), sqrt(d1sq), tb.R[r], tr.ddt[r]);
 }
 
-// Slow path of one pair that passed the cutoff: orientation, this step's
-// displacements (stored by the diffusion), acceptance, candidate.
-template <bool F32L>
-__device__ __forceinline__ void pair_accept(const Dev& d, const Tables& tb, const Train& tr, int b,
-                                            const SearchWarpSmem<F32L>& hs, uint32_t h, uint32_t s0,
-                                            uint32_t j, uint32_t tid_j, float fx, float fy, float fz,
-                                            float f2, double d1sq, double rx1, double ry1, double rz1,
-                                            const uint32_t* vf) {
-  uint32_t tid_i;
-  if constexpr (F32L) tid_i = __float_as_uint(hs.pos[h].w);
-  else tid_i = hs.tid[h];
-  const uint32_t ti = tid_type(tid_i), tj = tid_type(tid_j);
-  const int r = tb.pair_rxn[ti][tj];
-  const uint32_t id_i = tid_id(tid_i), id_j = tid_id(tid_j);
-  const bool i_lo = id_i < id_j;
-  const uint32_t id_lo = i_lo ? id_i : id_j, id_hi = i_lo ? id_j : id_i;
-  const uint32_t si = s0 + h;
-  if constexpr (F32L) {
-    if (!i_lo) { fx = -fx; fy = -fy; fz = -fz; }
-    // this step's displacements, stored by the diffusion in pre-sort order
-    const float4 di = d.td4[vf ? vf[si] : si];
-    const float4 dj = d.td4[vf ? vf[j] : j];
-    const float4 dlo = i_lo ? di : dj, dhi = i_lo ? dj : di;
-    const float r0x = fx - (dhi.x - dlo.x), r0y = fy - (dhi.y - dlo.y), r0z = fz - (dhi.z - dlo.z);
-    const float d0sq = r0x * r0x + r0y * r0y + r0z * r0z;
-    if (!accept_f32(d0sq, f2, r, tb, tr, id_lo, id_hi)) return;
-    emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, static_cast<double>(f2));
-  } else {
-    // r1 = minimum image of x_hi - x_lo, recomputed in that orientation as the reference does
-    if (!i_lo) { rx1 = -rx1; ry1 = -ry1; rz1 = -rz1; }
-    // this step's displacements, stored by the diffusion in pre-sort order
-    const uint32_t tj_idx = vf ? vf[j] : j, ti_idx = vf ? vf[si] : si;
-    const double ejx = d.tdx[tj_idx], ejy = d.tdy[tj_idx], ejz = d.tdz[tj_idx];
-    const double eix = d.tdx[ti_idx], eiy = d.tdy[ti_idx], eiz = d.tdz[ti_idx];
-    const double elx = i_lo ? eix : ejx, ely = i_lo ? eiy : ejy, elz = i_lo ? eiz : ejz;
-    const double ehx = i_lo ? ejx : eix, ehy = i_lo ? ejy : eiy, ehz = i_lo ? ejz : eiz;
-    const double r0x = __dsub_rn(rx1, __dsub_rn(ehx, elx));
-    const double r0y = __dsub_rn(ry1, __dsub_rn(ehy, ely));
-    const double r0z = __dsub_rn(rz1, __dsub_rn(ehz, elz));
-    if (!accept_f64(sq3(r0x, r0y, r0z), d1sq, r, tb, tr, id_lo, id_hi)) return;
-    emit_candidate(d, i_lo ? si : j, i_lo ? j : si, id_lo, id_hi, r, b, d1sq);
-  }
-}
-
-// Resolve the queued pairs, one per lane (the warp is converged here).
-template <bool F32L>
-__device__ __forceinline__ void flush_pairs(const Dev& d, const Tables& tb, const Train& tr, int b,
-                                            const SearchWarpSmem<F32L>& hs, PairQueue<F32L>& q,
-                                            uint32_t s0, const uint32_t* vf, int lane) {
-  const uint32_t nq = q.n;
-  for (uint32_t e = lane; e < nq; e += 32) {
-    const uint32_t h = q.hj[e], j = q.j[e];
-    uint32_t tid_j;
-    if constexpr (F32L) tid_j = __float_as_uint(d.s4[j].w);
-    else tid_j = d.stid[j];
-    if constexpr (F32L)
-      pair_accept<true>(d, tb, tr, b, hs, h, s0, j, tid_j, q.fx[e], q.fy[e], q.fz[e], q.f2[e], 0.0, 0.0,
-                        0.0, 0.0, vf);
-    else
-      pair_accept<false>(d, tb, tr, b, hs, h, s0, j, tid_j, 0.f, 0.f, 0.f, 0.f, q.d2[e], q.rx[e], q.ry[e],
-                         q.rz[e], vf);
-  }
-  __syncwarp();
-  if (lane == 0) q.n = 0;
-  __syncwarp();
-}
-
-template <bool F32L>
-__device__ void phase_search(const Dev& d, SearchSmem<F32L>& sm) {
-  if (status_of(d)) return;
-  const uint32_t n_items = min(d.g->n_items, d.cap_items);
-  const uint32_t n_live = d.g->n_total - d.g->n_dead;
-  const uint32_t epoch = d.g->epoch;
-  // pre-sort slot of each sorted slot; nullptr when no radix pass moved anything
-  const uint32_t* vf = d.g->sort_any ? (d.g->sort_parity ? d.vals1 : d.vals0) : nullptr;
-  const Tables& tb = *d.tables;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  SearchWarpSmem<F32L>& hs = sm.w[wib];
-  SearchRanges& rg = sm.rg[wib];
-  auto& ct = sm.ct[wib];
-  PairQueue<F32L>& q = sm.q[wib];
-  if (lane == 0) { sm.ct_train[wib] = -1; q.n = 0; }
-  __syncwarp();
-  const uint32_t item_home = d.g->item_home;
-  // work stealing, one item ahead: the next item's index and record are fetched while
-  // the current item computes
-  uint32_t it_next = 0;
-  if (lane == 0) it_next = atomicAdd(&d.g->item_ctr, 1u);
-  it_next = __shfl_sync(0xffffffffu, it_next, 0);
-  uint2 rec_next = make_uint2(0u, 0u);
-  if (it_next < n_items) rec_next = d.items[it_next];
-  uint32_t n_tested = 0, n_in_cut = 0;  // pair-search counters of this lane
-  for (;;) {
-    if (it_next >= n_items) break;
-    const uint2 rec = rec_next;
-    uint32_t it_ahead = 0;
-    if (lane == 0) it_ahead = atomicAdd(&d.g->item_ctr, 1u);
-    const uint32_t s0 = rec.x, cell = rec.y;
-    const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
-    const Train& tr = d.trains[b];
-    if (sm.ct_train[wib] != b) {  // cutoff table of this train (warp-uniform)
-      for (int q = lane; q < MAXT * MAXT; q += 32) {
-        const int r = tb.pair_rxn[q >> 3][q & 7];
-        if constexpr (F32L) ct.rc2[q] = r >= 0 ? tr.rc2f[r] : -1.f;
-        else ct.rc2[q] = r >= 0 ? tr.rc2[r] : -1.0;
-      }
-      __syncwarp();
-      if (lane == 0) sm.ct_train[wib] = b;
-    }
-    // in parallel: own cell range (lane 0), the 13 forward cells (lanes 1-13) and the
-    // home species, staged speculatively up to the item size
-    const int n = tr.n;
-    int ix, iy, iz;
-    cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
-    uint32_t rs = 0, rl = 0, own_end = 0;
-    if (lane == 0) {
-      own_end = static_cast<uint32_t>(d.cell_info[cell].y);
-    } else if (lane < N_FWD) {
-      int ox, oy, oz;
-      fwd_offset(lane, ox, oy, oz);
-      const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, ox, n), step_cell(iy, oy, n),
-                                                     step_cell(iz, oz, n), tr.cb);
-      // one bit per cell (L2-resident) filters the empty cells; the 16-byte entry with
-      // its epoch confirms
-      if ((d.occ[nc >> 5] >> (nc & 31u)) & 1u) {
-        const int4 nci = d.cell_info[nc];
-        if (static_cast<uint32_t>(nci.z) == epoch) {
-          rs = static_cast<uint32_t>(nci.x);
-          rl = static_cast<uint32_t>(nci.y - nci.x);
-        }
-      }
-    }
-    const uint32_t stage_end = min(n_live, (s0 / item_home + 1) * item_home);
-    for (uint32_t h = lane; s0 + h < stage_end; h += 32) {
-      const uint32_t s = s0 + h;
-      if constexpr (F32L) {
-        hs.pos[h] = d.s4[s];
-      } else {
-        hs.x[h] = d.sx[s]; hs.y[h] = d.sy[s]; hs.z[h] = d.sz[s];
-        hs.tid[h] = d.stid[s];
-      }
-    }
-    own_end = __shfl_sync(0xffffffffu, own_end, 0);
-    const uint32_t s_end = min(own_end, stage_end);
-    const uint32_t nh = s_end - s0;
-    if (lane == 0) { rs = s0 + 1; rl = own_end - rs; }
-    __syncwarp();
-    uint32_t want = 0;
-    for (uint32_t h = lane; h < nh; h += 32) {
-      uint32_t t;
-      if constexpr (F32L) t = __float_as_uint(hs.pos[h].w);
-      else t = hs.tid[h];
-      want |= tb.reactive_mask[tid_type(t)];
-    }
-    want = __reduce_or_sync(0xffffffffu, want);
-    uint32_t incl = rl;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const uint32_t excl = incl - rl;
-    const uint32_t total = want ? __shfl_sync(0xffffffffu, incl, N_FWD - 1) : 0u;
-    if (lane < N_FWD) { rg.start[lane] = rs; rg.off[lane] = excl; }
-    // the stolen index is needed only now; fetch the record of the item after this one
-    it_next = __shfl_sync(0xffffffffu, it_ahead, 0);
-    if (it_next < n_items) rec_next = d.items[it_next];
-    __syncwarp();
-    // lanes -> (neighbour, home group): with fewer than 32 neighbours several home rows
-    // are processed at once so that no lane idles. Both loops have warp-uniform trip
-    // counts; pairs inside the cutoff go to the warp's queue, which is resolved one
-    // pair per lane whenever it could overflow and at the end of the item.
-    uint32_t T2 = 32;
-    if (total < 32) { T2 = 1; while (T2 < total) T2 <<= 1; }
-    const uint32_t G = 32 / T2, hg = lane / T2;
-    const uint32_t lanemask_lt = (1u << lane) - 1u;
-    for (uint32_t f0 = 0; f0 < total; f0 += T2) {
-      const uint32_t f = f0 + (lane & (T2 - 1));
-      bool lane_on = f < total;
-      int k = 0;
-      uint32_t j = 0, tid_j = 0;
-      float4 vj = make_float4(0.f, 0.f, 0.f, 0.f);
-      double xj = 0, yj = 0, zj = 0;
-      if (lane_on) {
-#pragma unroll
-        for (int q = 1; q < N_FWD; ++q) k += (rg.off[q] <= f) ? 1 : 0;
-        j = rg.start[k] + (f - rg.off[k]);
-        if constexpr (F32L) { vj = d.s4[j]; tid_j = __float_as_uint(vj.w); }
-        else { tid_j = d.stid[j]; }
-        lane_on = (want >> tid_type(tid_j)) & 1u;
-        if constexpr (!F32L) { if (lane_on) { xj = d.sx[j]; yj = d.sy[j]; zj = d.sz[j]; } }
-      }
-      const auto* row = &ct.rc2[tid_type(tid_j) * MAXT];
-      // own cell: only home slots below j
-      const uint32_t hmax = lane_on ? ((k == 0) ? min(nh, j - s0) : nh) : 0u;
-      int odx, ody, odz;
-      fwd_offset(k, odx, ody, odz);
-      const float cx = odx * tr.hf, cy = ody * tr.hf, cz = odz * tr.hf;
-      for (uint32_t h0 = 0; h0 < nh; h0 += G) {
-        const uint32_t h = h0 + hg;
-        bool pass = false;
-        float fx = 0.f, fy = 0.f, fz = 0.f, f2 = 0.f;
-        double rx1 = 0, ry1 = 0, rz1 = 0, d1sq = 0;
-        if (h < hmax) {
-          if constexpr (F32L) {
-            const float4 vi = hs.pos[h];
-            const float rc2 = row[__float_as_uint(vi.w) & 7u];
-            fx = cx + (vj.x - vi.x); fy = cy + (vj.y - vi.y); fz = cz + (vj.z - vi.z);
-            f2 = fx * fx + fy * fy + fz * fz;
-            pass = f2 < rc2;
-          } else {
-            const double rc2 = row[hs.tid[h] & 7u];
-            if (rc2 >= 0.0) {
-              // minimum image of x_j - x_i (Eq. 2). The reference orients it x_hi - x_lo;
-              // for any pair inside the cutoff (|dx| < L/2) negating this exactly
-              // computed separation gives that orientation bit for bit
-              rx1 = min_image(__dsub_rn(xj, hs.x[h]), tr.L, tr.halfL);
-              ry1 = min_image(__dsub_rn(yj, hs.y[h]), tr.L, tr.halfL);
-              rz1 = min_image(__dsub_rn(zj, hs.z[h]), tr.L, tr.halfL);
-              d1sq = sq3(rx1, ry1, rz1);
-              pass = d1sq < rc2;
-            }
-          }
-        }
-        n_tested += (h < hmax) ? 1u : 0u;
-        n_in_cut += pass ? 1u : 0u;
-        const uint32_t bal = __ballot_sync(0xffffffffu, pass);
-        if (bal) {
-          const uint32_t base = q.n;
-          if (pass) {
-            const uint32_t pos = base + __popc(bal & lanemask_lt);
-            q.hj[pos] = h;
-            q.j[pos] = j;
-            if constexpr (F32L) { q.fx[pos] = fx; q.fy[pos] = fy; q.fz[pos] = fz; q.f2[pos] = f2; }
-            else { q.rx[pos] = rx1; q.ry[pos] = ry1; q.rz[pos] = rz1; q.d2[pos] = d1sq; }
-          }
-          __syncwarp();
-          if (lane == 0) q.n = base + __popc(bal);
-          __syncwarp();
-          if (q.n > static_cast<uint32_t>(PairQueue<F32L>::CAP) - 32u)
-            flush_pairs<F32L>(d, tb, tr, b, hs, q, s0, vf, lane);
-        }
-      }
-    }
-    flush_pairs<F32L>(d, tb, tr, b, hs, q, s0, vf, lane);
-    __syncwarp();
-  }
-  add_pair_counts(d, n_tested, n_in_cut);
-}
-
 // ---- one thread per home species
-// The same pairs as phase_search, assigned differently: each lane takes one home species
+// One thread per home species: each lane takes one home species
 // (warps take 32 consecutive sorted slots by work stealing) and walks its own cell's later
 // slots and its 13 forward cells. Lanes of one cell walk the same ranges in step, so their
 // neighbour loads are broadcasts; the loops are warp-uniform (trip count = the longest
@@ -1163,8 +878,7 @@ struct TpsSmem {
   TpsQueue<F32L> q[W];
 };
 
-// Acceptance of one queued pair (the slow path of phase_search's pair_accept, with the
-// home species given by slot and packed id/type).
+// Acceptance of one queued pair (home species given by slot and packed id/type).
 template <bool F32L>
 __device__ __forceinline__ void tps_accept(const Dev& d, const Tables& tb, const Train& tr, int b, uint32_t si,
                                            uint32_t tid_i, uint32_t j, uint32_t tid_j, float fx, float fy,
@@ -1222,7 +936,7 @@ __device__ __forceinline__ void tps_flush(const Dev& d, const Tables& tb, TpsQue
 template <bool F32L, int W>
 __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
   using T = typename TpsSmem<F32L, W>::T;
-  if (status_of(d)) return;
+  if (status_of(d) || d.g->search_cells_now) return;  // this step runs the cell tiles
   const uint32_t n_live = d.g->n_total - d.g->n_dead;
   const uint32_t epoch = d.g->epoch;
   const uint32_t* vf = d.g->sort_any ? (d.g->sort_parity ? d.vals1 : d.vals0) : nullptr;
@@ -1377,7 +1091,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
         j = rs_l[32 * r];
         je = re_l[32 * r];
         const int k = rk_l[32 * r];
-        cx = c_fwd.x[k] * tr.hf; cy = c_fwd.y[k] * tr.hf; cz = c_fwd.z[k] * tr.hf;
+        cx = c_fwd.x[k]; cy = c_fwd.y[k]; cz = c_fwd.z[k];  // in cells
       };
       if (nr > 0) open(0);
       while (__any_sync(0xffffffffu, ri < nr)) {
@@ -1477,8 +1191,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           // the cutoff test for the four neighbours first; the separation is formed again,
           // identically, for the rare pairs inside the cutoff
           auto sep = [&](int u, float& fx, float& fy, float& fz) {
-            fx = cxu[u] + (vj[u].x - hv.x); fy = cyu[u] + (vj[u].y - hv.y); fz = czu[u] + (vj[u].z - hv.z);
-            return fx * fx + fy * fy + fz * fz;
+            return sep_f32(cxu[u], cyu[u], czu[u], htr->hf, vj[u], hv, fx, fy, fz);
           };
           bool pass[4];
           bool any = false;
@@ -1509,9 +1222,8 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
               const float cw = hrow[tjj];  // widened FP32 bound, -1 when the types do not react
               bool near = cw >= 0.f;
               if (near && pref) {
-                const float fx = cxu[u] + (vj[u].x - hv.x), fy = cyu[u] + (vj[u].y - hv.y),
-                            fz = czu[u] + (vj[u].z - hv.z);
-                near = fx * fx + fy * fy + fz * fz < cw;
+                float fx, fy, fz;
+                near = sep_f32(cxu[u], cyu[u], czu[u], htr->hf, vj[u], hv, fx, fy, fz) < cw;
               }
               if (near) {
                 const double c2 = htr->rc2_tt[tid_type(htid) * MAXT + tjj];

@@ -35,7 +35,7 @@ constexpr int SORT_ITEMS = 15;
 // the smallest sort tile (persistent kernel): sizes the look-back buffer
 constexpr int SORT_TILE_MIN = PERSIST_THREADS * SORT_ITEMS;
 constexpr int REACT_THREADS = 1024;
-constexpr int ITEM_HOME = 64;   // home species per pair-search work item (one cell)
+constexpr int ITEM_HOME = 32;   // most home species per pair-search work item (one cell)
 constexpr int N_FWD = 14;       // own cell + 13 forward neighbour cells (half shell)
 constexpr int N_FWD2 = 63;      // own cell + 62 forward cells within two cells (half shell)
 constexpr double END_SLACK = 1.0 + 1e-6;    // last-step trim slack (relative)
@@ -135,7 +135,9 @@ struct Global {
   uint32_t err_where;
   uint32_t steps_active;  // steps in which at least one train advanced
   uint32_t n_items;       // pair-search work items emitted by the gather
-  uint32_t item_home;     // home species per pair-search work item (<= ITEM_HOME)
+  uint32_t item_home;     // home species per cell-tile work item (<= ITEM_HOME; 0: no tiles)
+  uint32_t search_adaptive;   // choose the search mapping per step (below)
+  uint32_t search_cells_now;  // this step's mapping: 1 cell tiles, 0 one thread per species
   uint32_t n_conflict;    // accepted pairs sharing a species with another accepted pair
   uint32_t item_ctr;      // next pair-search work item (work stealing)
   uint32_t sort_parity;   // number of non-trivial passes of this step's cell sort, mod 2
@@ -152,6 +154,8 @@ struct Global {
   unsigned long long pairs_tested;     // neighbour pairs whose separation was tested
   unsigned long long pairs_in_cutoff;  // of them, reacting type pairs inside the cutoff
   unsigned long long pairs_accepted;   // of them, accepted (the steps' reactive pairs)
+  unsigned long long incut_mark;       // pairs_in_cutoff when the last step began
+  uint32_t cells_steps;                // steps searched with cell tiles (cumulative)
 };
 
 // Accepted reactive pair.
@@ -176,6 +180,7 @@ struct Dev {
   float4* s4; float4* t4;
   double* tdx; double* tdy; double* tdz;  // FP64 displacement of this step, pre-sort order
   float4* td4;                            // FP32-local displacement of this step, pre-sort order
+  float4* sd4;                            // the same in sorted order (gathered with the state)
   uint2* items;                           // pair-search work items {first home slot, cell}
   uint32_t cap_items;
   uint32_t* cell_sorted;

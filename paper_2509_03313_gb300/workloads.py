@@ -207,6 +207,17 @@ def single_pulse_tracks(seed: int, n_species: int = 1_000_000, n_tracks: int = 2
                     t_end=t_end)
 
 
+def tracks_same_density(seed: int, L: float, t_end: float = 1e-6) -> Workload:
+    """The single-pulse track workload in a box of side L (nm) with the benchmark's track
+    density per unit area (200 tracks per (5 um)^2) and species per nm of track (1e6
+    species over 200 tracks of 5 um: one per nm), so the local structure, the species
+    density and the time-step schedule are those of the 5 um workload: about 3.2e4
+    species at L = 1.6 um, 2e7 at L = 13.6 um."""
+    n_tracks = max(1, int(round(200.0 * (L / 5000.0) ** 2)))
+    per_track = max(1, int(round(L)))
+    return single_pulse_tracks(seed, n_species=n_tracks * per_track, n_tracks=n_tracks, L=L, t_end=t_end)
+
+
 def multi_pulse(seed: int, n_pulses: int = 10, period_s: float = 1e-4, fwhm_s: float = 1e-6,
                 n_tracks: int = 163, species_per_track: int = 1800, L: float = 5000.0,
                 dt_min: float = 1e-11, dt_max: float = 1e-6) -> Workload:

@@ -30,7 +30,7 @@ def test_tuning_mid_run_leaves_fp64_results_unchanged(launch_mode):
         chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
         chem.chem_run_until(ctx, 70e-9)
         spl, n_lim, ih, mode = chem.chem_autotune(ctx, 400.0)
-        assert spl in (8, 32) and ih in (0, 32, 64) and n_lim >= 3
+        assert spl in (8, 32) and ih == -1 and n_lim >= 3  # the mapping stays chosen per step
         assert mode in (chem.CHEM_LAUNCH_PHASES, chem.CHEM_LAUNCH_PERSISTENT)
         chem.chem_run_until(ctx, wl.t_end)
         ids, types, xyz = chem.chem_get_state(ctx)
@@ -65,7 +65,8 @@ def test_tuning_fp32_local_keeps_counts_consistent():
     assert int((tal["counts"] * W.CHARGE).sum()) == int((c0 * W.CHARGE).sum())
 
 
-@pytest.mark.parametrize("tuning", [(4, 12, 16, chem.CHEM_LAUNCH_PERSISTENT), (32, 200, 64, chem.CHEM_LAUNCH_PHASES)])
+@pytest.mark.parametrize("tuning", [(4, 12, 16, chem.CHEM_LAUNCH_PERSISTENT), (32, 200, 32, chem.CHEM_LAUNCH_PHASES),
+                                    (8, 200, -1, chem.CHEM_LAUNCH_PHASES), (8, 200, 0, chem.CHEM_LAUNCH_PHASES)])
 def test_set_tuning_mid_run_leaves_fp64_results_unchanged(tuning):
     wl = W.uniform_2000(seed=53, L=200.0, n_steps=200)
     ctx, keep = _ctx(wl, 53, chem.CHEM_FP64)
@@ -89,7 +90,7 @@ def test_set_tuning_rejects_out_of_range_values():
     wl = W.uniform_2000(seed=54, L=200.0, n_steps=10)
     ctx, keep = _ctx(wl, 54, chem.CHEM_FP64)
     try:
-        for bad in [(0, 12, 16, 1), (8, 2, 16, 1), (8, 12, 65, 1), (8, 12, -1, 1), (8, 12, 16, 0),
+        for bad in [(0, 12, 16, 1), (8, 2, 16, 1), (8, 12, 33, 1), (8, 12, -2, 1), (8, 12, 16, 0),
                     (8, 12, 16, 3)]:
             with pytest.raises(chem.ChemError) as ei:
                 chem.chem_set_tuning(ctx, *bad)
