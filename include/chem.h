@@ -291,10 +291,11 @@ typedef struct chem_stats {
                                    sort because a bucket held more than 64 keys          */
   int64_t max_conflict_pairs;   /* most conflicting accepted pairs in one step          */
   int64_t max_step_events;      /* most events in one step                              */
-  /* Pair-search work (device counters, summed over resets): neighbour pairs whose
-   * separation the search tested, those of reacting types inside their cutoff (each
-   * costs one acceptance test: a Philox block and the touch probability), and the
-   * accepted ones. */
+  /* Pair-search work (device counters, summed over resets): pairs of reacting types in
+   * the cells the search visits for each species (the box-gap test against the largest
+   * cutoff of the species' type; the same set for both search mappings), those inside
+   * their cutoff (each costs one acceptance test: a Philox block and the touch
+   * probability), and the accepted ones. */
   int64_t pairs_tested;
   int64_t pairs_in_cutoff;
   int64_t pairs_accepted;

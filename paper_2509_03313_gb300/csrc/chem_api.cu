@@ -665,10 +665,10 @@ chem_status state_one(chem_ctx* ctx, int b, int64_t cap, int32_t* type, uint32_t
     } else {
       std::memcpy(&tt, &v4[i].w, 4);
       const uint32_t loc = cell[i] - t.cell_base;
-      const uint32_t m = (1u << t.cb) - 1u;
+      const uint32_t m = (1u << t.cb_ref) - 1u;  // the grid of the last step
       const double h = t.h_ref;
-      const int ix = static_cast<int>(loc & m), iy = static_cast<int>((loc >> t.cb) & m),
-                iz = static_cast<int>(loc >> (2 * t.cb));
+      const int ix = static_cast<int>(loc & m), iy = static_cast<int>((loc >> t.cb_ref) & m),
+                iz = static_cast<int>(loc >> (2 * t.cb_ref));
       auto wrapb = [&](double q) {
         q -= t.L * std::floor((q + t.halfL) / t.L);
         if (q >= t.halfL) q -= t.L;
@@ -811,10 +811,11 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     }
     t.n_max = n_max;
     t.n_alloc = n_alloc;
-    t.cb = bits_for(static_cast<uint64_t>(n_alloc - 1));
+    t.cb_alloc = bits_for(static_cast<uint64_t>(n_alloc - 1));
+    t.cb = t.cb_ref = t.cb_alloc;
     t.inv_L = 1.0 / c.L_nm;
     t.cell_base = static_cast<uint32_t>(cells);
-    cells += 1ull << (3 * t.cb);
+    cells += 1ull << (3 * t.cb_alloc);
     t.pend_base = static_cast<uint32_t>(pend);
     t.pend_cap = static_cast<uint32_t>(c.capacity_pending);
     pend += static_cast<uint64_t>(c.capacity_pending);
@@ -1220,7 +1221,8 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   // step from the pairs inside the cutoffs, see phase_begin).
   const int n_alloc = tr0[0].n_alloc;
   std::vector<int> n_cands;
-  for (double f : {1.0, 0.75, 0.55, 0.4}) n_cands.push_back(std::max(3, static_cast<int>(n_alloc * f)));
+  // (half the allocated resolution minus one keeps one bit per axis less: one radix pass less)
+  for (int nm : {n_alloc, (3 * n_alloc) / 4, n_alloc / 2 - 1, (2 * n_alloc) / 5}) n_cands.push_back(std::max(3, nm));
   const int ih_cands[1] = {ctx->item_home};
   const int spl_cands[2] = {8, 32};
   const bool mode_cands[2] = {false, true};  // per-phase graph, persistent launch

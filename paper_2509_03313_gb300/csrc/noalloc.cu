@@ -257,7 +257,7 @@ extern "C" chem_status chem_step_noalloc(const chem_config* cfg, uint32_t step, 
   tr.key1 = static_cast<uint32_t>(cfg->seed >> 32) ^ cfg->train_id;
   tr.n_max = NA_CELLS_AXIS;
   tr.n_alloc = NA_CELLS_AXIS;
-  tr.cb = 5;  // 32 = 2^5 cells per axis
+  tr.cb = tr.cb_ref = tr.cb_alloc = 5;  // 32 = 2^5 cells per axis
   tr.inv_L = 1.0 / cfg->L_nm;
   tr.id_limit = (1u << 29) - 1u;
   tr.t = t_s;

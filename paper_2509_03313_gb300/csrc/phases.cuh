@@ -128,6 +128,10 @@ __device__ __forceinline__ int cell_index(double x, double halfL, double inv_h, 
   return min(max(i, 0), n - 1);
 }
 
+// Bits per axis of the cell index of a grid of n cells per axis: enough for the values
+// 0..n, so the all-ones index (>= n) is never a cell.
+__device__ __forceinline__ int axis_bits(int n) { return 32 - __clz(n); }
+
 __device__ __forceinline__ int wrap_cell(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
@@ -269,7 +273,7 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     if (sb.dt[b] <= 0.0) continue;
     Train& tr = d.trains[b];
     const double L = tr.L, inv_L = tr.inv_L;
-    const int n_max = tr.n_max, fj = tr.free_jump;
+    const int n_max = min(tr.n_max, (1 << tr.cb_alloc) - 1), fj = tr.free_jump;
     int n_ref = tr.n_ref;
     const double rcmax = __longlong_as_double(static_cast<long long>(sb.rcmax_bits[b]));
     // finest admissible grid: cells at least the largest cutoff (with slack), or at least
@@ -287,6 +291,7 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
       n_ref = n_target;
       tr.n_ref = n_target;
       tr.h_ref = __ddiv_rn(L, static_cast<double>(n_target));
+      tr.cb_ref = axis_bits(n_target);
     }
     // keep the current grid while it is valid and at most 2x too coarse; when the
     // cutoff outgrows it, move to cells 1.2x larger than needed (fewer regrids)
@@ -312,6 +317,7 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     const double h = __ddiv_rn(L, static_cast<double>(n));
     const double inv_h = __dmul_rn(static_cast<double>(n), inv_L);
     tr.n = n;
+    tr.cb = axis_bits(n);
     tr.reach = reach;
     tr.h = h;
     tr.inv_h = inv_h;
@@ -371,6 +377,14 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     }
     g->incut_mark = g->pairs_in_cutoff;
     if (g->search_cells_now && sb.any) g->cells_steps += 1;
+  }
+  __syncthreads();  // the grids above are written
+  if (tid == 0) {
+    // removed species sort after every live one: with one train the all-ones cell index
+    // of this step's width (no cell has it), so the top key bits stay zero and their
+    // radix pass is skipped; with several trains, past the last train's cells
+    const Train& t0 = d.trains[0];
+    d.g->sentinel_step = (d.n_trains == 1 && t0.active) ? t0.cell_base + ((1u << (3 * t0.cb)) - 1u) : d.sentinel;
   }
   for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&d.g->hist[0][0])[i] = 0u;
   __syncthreads();
@@ -480,7 +494,7 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
                           static_cast<float>(__dsub_rn(__dadd_rn(py, tr.halfL), __dmul_rn(iy, h))),
                           static_cast<float>(__dsub_rn(__dadd_rn(pz, tr.halfL), __dmul_rn(iz, h))),
                           __uint_as_float(tid));
-          cell = tr.cell_base + cell_encode(ix, iy, iz, tr.cb);
+          cell = tr.cell_base + cell_encode(ix, iy, iz, tr.cb_ref);
           d.s4[s] = v;
         } else {
           cell = tr.cell_base;  // FP64 mode recomputes cells from positions
@@ -504,7 +518,7 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
         }
       }
       if (dead) {
-        key = d.sentinel;
+        key = d.g->sentinel_step;
         ++n_dead_local;
       } else {
         const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
@@ -544,7 +558,7 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
           const float sig = tr.sigf[ty];
           const int nr = tr.n_ref;
           int ix, iy, iz;
-          cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
+          cell_decode(cell - tr.cell_base, tr.cb_ref, ix, iy, iz);
           const int n = tr.n;
           const float ex = sig * g0, ey = sig * g1, ez = sig * g2;
           d.td4[s] = make_float4(ex, ey, ez, 0.f);
@@ -649,7 +663,7 @@ __device__ void phase_gather(const Dev& d) {
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_live; s += stride) {
     const uint32_t key = kf[s];
     const uint32_t i = vf ? vf[s] : s;
-    if (key >= d.sentinel || i >= d.g->n_total) {  // only after a timed-out sort
+    if (key >= d.g->sentinel_step || i >= d.g->n_total) {  // only after a timed-out sort
       raise_status(d.g, CHEM_ETIMEOUT);
       continue;
     }
@@ -1198,9 +1212,10 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             float fx, fy, fz;
-            pass[u] = vu[u] && sep(u, fx, fy, fz) < hrow[__float_as_uint(vj[u].w) & 7u];
+            const float rc2u = hrow[__float_as_uint(vj[u].w) & 7u];  // -1 when the types do not react
+            pass[u] = vu[u] && sep(u, fx, fy, fz) < rc2u;
             any = any || pass[u];
-            n_tested += vu[u] ? 1u : 0u;
+            n_tested += (vu[u] && rc2u >= 0.f) ? 1u : 0u;  // reacting type pairs only
             n_in_cut += pass[u] ? 1u : 0u;
           }
           if (__any_sync(0xffffffffu, any)) {
@@ -1236,7 +1251,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
                 pass = d1sq < c2;
               }
             }
-            n_tested += vu[u] ? 1u : 0u;
+            n_tested += (vu[u] && hrow[tj[u] & 7u] >= 0.f) ? 1u : 0u;  // reacting type pairs only
             n_in_cut += pass ? 1u : 0u;
             push(pass, jj, 0.f, 0.f, 0.f, 0.f, rx1, ry1, rz1, d1sq);
           }
@@ -1980,6 +1995,7 @@ static __device__ void phase_end_step(const Dev& d, EndSmem& sm) {
       tr.dt_cur = fmin(__dmul_rn(tr.dt_cur, tr.dt_growth), tr.dt_max);
       tr.n_ref = tr.n;
       tr.h_ref = tr.h;
+      tr.cb_ref = tr.cb;
     }
     if (tr.t < tr.t_end) atomicOr(&sm.any, 1u);
   }

@@ -67,7 +67,11 @@ struct Train {
   int reset_on_release;
   int n_max;               // cells per axis limit used at run time (<= n_alloc)
   int n_alloc;             // cells per axis the hash table is allocated for
-  int cb;                  // bits per axis of the local cell index (n_alloc <= 2^cb)
+  int cb_alloc;            // bits per axis of the allocated hash (n_alloc <= 2^cb_alloc)
+  int cb;                  // bits per axis of this step's cell index (n < 2^cb <= 2^cb_alloc,
+                           // so the all-ones index is no cell): fewer key bits, fewer radix
+                           // passes on coarse grids
+  int cb_ref;              // the same for the grid that cell_sorted refers to
   double inv_L;
   uint32_t cell_base;      // first global cell of this train
   uint32_t pend_base;      // first pending slot of this train
@@ -156,6 +160,8 @@ struct Global {
   unsigned long long pairs_accepted;   // of them, accepted (the steps' reactive pairs)
   unsigned long long incut_mark;       // pairs_in_cutoff when the last step began
   uint32_t cells_steps;                // steps searched with cell tiles (cumulative)
+  uint32_t sentinel_step;              // key of removed species this step: above every cell
+                                       // key of the step (one train: the unused all-ones cell)
 };
 
 // Accepted reactive pair.

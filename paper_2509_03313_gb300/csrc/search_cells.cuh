@@ -133,13 +133,24 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
   __syncwarp();
   uint32_t n_tested = 0, n_in_cut = 0;  // pair-search counters of this lane
   const uint32_t item_home = min(max(d.g->item_home, 1u), static_cast<uint32_t>(SC_HOMES));
-  uint32_t it = 0;
-  if (lane == 0) it = atomicAdd(&d.g->item_ctr, 1u);
+  const uint32_t n_live = d.g->n_total - d.g->n_dead;
+  // work stealing two items ahead: while an item is processed, lane 0 holds the claim of
+  // the item after next and the record of the next one, both in flight
+  uint32_t it = 0, it_n1 = 0;
+  if (lane == 0) {
+    it = atomicAdd(&d.g->item_ctr, 1u);
+    it_n1 = atomicAdd(&d.g->item_ctr, 1u);
+  }
   it = __shfl_sync(FULL, it, 0);
+  it_n1 = __shfl_sync(FULL, it_n1, 0);
+  uint2 rec = it < n_items ? d.items[it] : make_uint2(0u, 0u);
   while (it < n_items) {
-    const uint2 rec = d.items[it];
-    uint32_t it_next = 0;
-    if (lane == 0) it_next = atomicAdd(&d.g->item_ctr, 1u);  // claimed now, used at the end
+    uint32_t it_n2 = 0;
+    uint2 rec_n1 = make_uint2(0u, 0u);
+    if (lane == 0) {
+      it_n2 = atomicAdd(&d.g->item_ctr, 1u);
+      if (it_n1 < n_items) rec_n1 = d.items[it_n1];
+    }
     const uint32_t s0 = rec.x, cell = rec.y;
     const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
     const Train& tr = d.trains[b];
@@ -149,26 +160,49 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
       if (lane == 0) w.ct_b = b;
       __syncwarp();
     }
-    // homes: from s0 to the cell's end or the next multiple of the item size, where the
-    // gather starts the next item
-    const uint32_t own_end = static_cast<uint32_t>(d.cell_info[cell].y);
-    const uint32_t item_end = min(own_end, (s0 / item_home + 1u) * item_home);
-    const uint32_t nh = item_end - s0;  // 1..32 homes
     const int n_fwd = tr.reach == 2 ? N_FWD2 : N_FWD;
     const float hf = tr.hf;
     int cx, cy, cz;
     cell_decode(cell - tr.cell_base, tr.cb, cx, cy, cz);
+    // independent loads issued together: this lane's home (speculatively, up to the item
+    // size), the own cell's end, and the occupancy bits of the half-shell cells k = lane
+    // and lane + 32
+    const uint32_t s_home = s0 + static_cast<uint32_t>(lane);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (static_cast<uint32_t>(lane) < item_home && s_home < n_live) v = d.s4[s_home];
+    const uint32_t own_end = static_cast<uint32_t>(d.cell_info[cell].y);
+    uint32_t nc0 = 0, nc1 = 0;
+    bool occ0 = false, occ1 = false;
+    {
+      const int n = tr.n;
+      const int k0 = lane, k1 = lane + 32;
+      if (k0 >= 1 && k0 < n_fwd) {
+        nc0 = tr.cell_base + cell_encode(step_cell(cx, c_fwd.x[k0], n), step_cell(cy, c_fwd.y[k0], n),
+                                         step_cell(cz, c_fwd.z[k0], n), tr.cb);
+        occ0 = (d.occ[nc0 >> 5] >> (nc0 & 31u)) & 1u;
+      }
+      if (k1 < n_fwd) {
+        nc1 = tr.cell_base + cell_encode(step_cell(cx, c_fwd.x[k1], n), step_cell(cy, c_fwd.y[k1], n),
+                                         step_cell(cz, c_fwd.z[k1], n), tr.cb);
+        occ1 = (d.occ[nc1 >> 5] >> (nc1 & 31u)) & 1u;
+      }
+    }
+    // homes: from s0 to the cell's end or the next multiple of the item size, where the
+    // gather starts the next item
+    const uint32_t item_end = min(own_end, (s0 / item_home + 1u) * item_home);
+    const uint32_t nh = item_end - s0;  // 1..32 homes
+    // cells worth looking at: the own cell, and forward cells with their occupancy bit set
+    const unsigned long long occ_mask = 1ull | (static_cast<unsigned long long>(__ballot_sync(FULL, occ0))) |
+                                        (static_cast<unsigned long long>(__ballot_sync(FULL, occ1)) << 32);
     // 1. homes and the cells each can reach
     unsigned long long km = 0ull;
     uint32_t rmask = 0u;  // partner types of this lane's home
     if (static_cast<uint32_t>(lane) < nh) {
-      const uint32_t s = s0 + lane;
-      const float4 v = d.s4[s];
       w.hv[lane] = v;
       const uint32_t t = tid_type(__float_as_uint(v.w));
       rmask = tb.reactive_mask[t];
       if (rmask != 0u) {
-        if (s + 1u < own_end) km = 1ull;
+        if (s_home + 1u < own_end) km = 1ull;
         float rcmax2 = -1.f;
 #pragma unroll
         for (int u = 0; u < MAXT; ++u) rcmax2 = fmaxf(rcmax2, w.ct[t * MAXT + u]);
@@ -180,7 +214,8 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
           const float g = o > 0 ? static_cast<float>(o) * hf - of : (o < 0 ? of + static_cast<float>(-o - 1) * hf : 0.f);
           return fmaxf(g - eps, 0.f);
         };
-        for (int k = 1; k < n_fwd; ++k) {
+        for (unsigned long long rem = occ_mask & ~1ull; rem != 0ull; rem &= rem - 1ull) {
+          const int k = __ffsll(static_cast<long long>(rem)) - 1;
           const float gx = gap(c_fwd.x[k], v.x), gy = gap(c_fwd.y[k], v.y), gz = gap(c_fwd.z[k], v.z);
           if (gx * gx + gy * gy + gz * gz <= rcmax2) km |= 1ull << k;
         }
@@ -210,15 +245,11 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
           st = s0 + 1u;
           len = own_end - st;
         } else {
-          const int n = tr.n;
-          const uint32_t nc = tr.cell_base + cell_encode(step_cell(cx, c_fwd.x[k], n), step_cell(cy, c_fwd.y[k], n),
-                                                         step_cell(cz, c_fwd.z[k], n), tr.cb);
-          if ((d.occ[nc >> 5] >> (nc & 31u)) & 1u) {
-            const int4 ci = d.cell_info[nc];
-            if (static_cast<uint32_t>(ci.z) == epoch && ci.y > ci.x) {
-              st = static_cast<uint32_t>(ci.x);
-              len = static_cast<uint32_t>(ci.y - ci.x);
-            }
+          // occupied (the bit was tested above); the epoch-stamped entry confirms
+          const int4 ci = d.cell_info[round == 0 ? nc0 : nc1];
+          if (static_cast<uint32_t>(ci.z) == epoch && ci.y > ci.x) {
+            st = static_cast<uint32_t>(ci.x);
+            len = static_cast<uint32_t>(ci.y - ci.x);
           }
         }
       }
@@ -309,7 +340,9 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
         if (w.qn > static_cast<uint32_t>(SC_QCAP) - 32u) sc_flush<F32L>(d, tb, w, vf, lane, n_in_cut);
       }
     }
-    it = __shfl_sync(FULL, it_next, 0);
+    it = it_n1;
+    rec = make_uint2(__shfl_sync(FULL, rec_n1.x, 0), __shfl_sync(FULL, rec_n1.y, 0));
+    it_n1 = __shfl_sync(FULL, it_n2, 0);
   }
   sc_flush<F32L>(d, tb, w, vf, lane, n_in_cut);
   add_pair_counts(d, n_tested, n_in_cut);
