@@ -301,6 +301,9 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
   t.hx_sel = 0;
   t.hx_stage = 0;
   t.mat_n = 0;
+  t.park_n = 0;
+  t.park_now = 0;
+  t.rel_park = 0;
   t.rel_mat = 0;
   t.hx_t_end = 0.0;
   t.hx_steps = 0;
@@ -472,6 +475,7 @@ chem_status homogeneous_run(chem_ctx* ctx, const double* t_end) {
     for (size_t i = t.p_head; i < due_end[b]; ++i) t.counts[buf.type[i]] += 1;
     t.p_head = static_cast<uint32_t>(due_end[b]);
     t.hx_sel = 1;
+    t.park_n = 0;  // parked particles are removed with the others (their counts stay)
     t.hx_t_end = t_end[b];
   }
   s = upload_trains(ctx, tr);
@@ -631,22 +635,36 @@ chem_status state_one(chem_ctx* ctx, int b, int64_t cap, int32_t* type, uint32_t
   std::vector<Train> tr;
   s = download_trains(ctx, tr);
   if (s) return s;
-  const uint32_t n = ctx->g_pinned->n_total;
-  std::vector<uint8_t> dead(n);
+  const uint32_t n_slots = ctx->g_pinned->n_total;
+  // the stepped slots, then the train's parked species (idle trains of a batch)
+  const uint32_t np = ctx->d.pk_cell ? tr[b].park_n : 0u, pb = tr[b].park_base;
+  const uint32_t n = n_slots + np;
+  std::vector<uint8_t> dead(n, 0);
   std::vector<uint32_t> cell(n), tid(n);
   std::vector<double> x(n), y(n), z(n);
   std::vector<float4> v4;
-  if (n) {
-    CK(cudaMemcpy(dead.data(), ctx->d.dead, n, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(cell.data(), ctx->d.cell_sorted, n * 4, cudaMemcpyDeviceToHost));
+  if (ctx->precision != CHEM_FP64) v4.resize(n);
+  if (n_slots) {
+    CK(cudaMemcpy(dead.data(), ctx->d.dead, n_slots, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cell.data(), ctx->d.cell_sorted, n_slots * 4, cudaMemcpyDeviceToHost));
     if (ctx->precision == CHEM_FP64) {
-      CK(cudaMemcpy(tid.data(), ctx->d.stid, n * 4, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(x.data(), ctx->d.sx, n * 8, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(y.data(), ctx->d.sy, n * 8, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(z.data(), ctx->d.sz, n * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(tid.data(), ctx->d.stid, n_slots * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(x.data(), ctx->d.sx, n_slots * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(y.data(), ctx->d.sy, n_slots * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(z.data(), ctx->d.sz, n_slots * 8, cudaMemcpyDeviceToHost));
     } else {
-      v4.resize(n);
-      CK(cudaMemcpy(v4.data(), ctx->d.s4, n * 16, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(v4.data(), ctx->d.s4, n_slots * 16, cudaMemcpyDeviceToHost));
+    }
+  }
+  if (np) {
+    CK(cudaMemcpy(cell.data() + n_slots, ctx->d.pk_cell + pb, np * 4, cudaMemcpyDeviceToHost));
+    if (ctx->precision == CHEM_FP64) {
+      CK(cudaMemcpy(tid.data() + n_slots, ctx->d.pk_tid + pb, np * 4, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(x.data() + n_slots, ctx->d.pkx + pb, np * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(y.data() + n_slots, ctx->d.pky + pb, np * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(z.data() + n_slots, ctx->d.pkz + pb, np * 8, cudaMemcpyDeviceToHost));
+    } else {
+      CK(cudaMemcpy(v4.data() + n_slots, ctx->d.pk4 + pb, np * 16, cudaMemcpyDeviceToHost));
     }
   }
   int64_t k = 0;
@@ -821,6 +839,8 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     pend += static_cast<uint64_t>(c.capacity_pending);
     t.id_limit = (tbits + 29 <= 32) ? (1u << 29) - 1u : (1u << (32 - tbits)) - 1u;
     init_train_dynamic(t, c, n_alloc);
+    t.park_base = static_cast<uint32_t>(cap);
+    t.park_cap = static_cast<uint32_t>(c.capacity_species);
     cap += static_cast<uint64_t>(c.capacity_species);
     cand += static_cast<uint64_t>(c.capacity_candidates);
     evlog += static_cast<uint64_t>(c.capacity_event_log);
@@ -907,6 +927,15 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     d.t4 = static_cast<float4*>(A(cap * 16));
     d.td4 = static_cast<float4*>(A(cap * 16));
     d.sd4 = static_cast<float4*>(A(cap * 16));
+  }
+  if (n_trains > 1) {  // parking buffers of idle trains
+    d.pk_cell = static_cast<uint32_t*>(A(cap * 4));
+    if (ctx->precision == CHEM_FP64) {
+      d.pkx = static_cast<double*>(A(cap * 8)); d.pky = static_cast<double*>(A(cap * 8));
+      d.pkz = static_cast<double*>(A(cap * 8)); d.pk_tid = static_cast<uint32_t*>(A(cap * 4));
+    } else {
+      d.pk4 = static_cast<float4*>(A(cap * 16));
+    }
   }
   d.cap_items = static_cast<uint32_t>(cap + cap / ITEM_HOME + 64);
   d.items = static_cast<uint2*>(A(static_cast<size_t>(d.cap_items) * 8));

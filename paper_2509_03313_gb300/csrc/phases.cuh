@@ -172,10 +172,13 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     const uint32_t p_head = tr.p_head, p_tail = tr.p_tail, pend_base = tr.pend_base;
     const uint32_t next_id = tr.next_id, id_limit = tr.id_limit;
     const uint32_t mat = tr.mat_n;  // survivors of a homogeneous stage (already counted)
+    const uint32_t parked = tr.park_n;  // species parked while the train was idle (counted)
     const int reset = tr.reset_on_release;
     long long live = 0;
     for (int ty = 0; ty < MAXT; ++ty) live += (ty < tb.n_types) ? tr.counts[ty] : 0;
     const bool act = (st == 0) && (t < t_end);
+    // an idle train with species among the stepped slots parks them this step
+    tr.park_now = (!act && d.pk_cell != nullptr && live > static_cast<long long>(parked) + mat) ? 1u : 0u;
     uint32_t rel = 0;
     int free_jump = 0;
     double dt = 0.0;
@@ -214,8 +217,11 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
       tr.dt = dt;
       tr.t_next = t_next;
       tr.t_start = t;
-      // releases: the re-created survivors first, then the arrived species
-      tr.rel_n = rel + mat;
+      // releases: the unparked species first (they keep their ids), then the re-created
+      // survivors, then the arrived species
+      tr.rel_n = parked + rel + mat;
+      tr.rel_park = parked;
+      tr.park_n = 0;
       tr.rel_mat = mat;
       tr.mat_n = 0;
       tr.rel_id0 = next_id;
@@ -229,10 +235,11 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     } else {
       tr.rel_n = 0;
       tr.rel_mat = 0;
+      tr.rel_park = 0;
     }
     tr.active = act ? 1 : 0;
     tr.free_jump = free_jump;
-    sb.rel[b] = act ? rel + mat : 0u;
+    sb.rel[b] = act ? parked + rel + mat : 0u;
     sb.dt[b] = act ? dt : 0.0;
   }
   __syncthreads();
@@ -473,7 +480,23 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
         // queue; ids in that order (arrival, call order within the queue)
         rel_b = train_of_release(d, s);
         const Train& tr = d.trains[rel_b];
-        const uint32_t k = s - tr.rel_off;
+        const uint32_t kp = s - tr.rel_off;
+        if (kp < tr.rel_park) {
+          // an unparked species: its state and cell key as they were parked (the train's
+          // grid has not changed since); it then takes the step like any other
+          const uint32_t q = tr.park_base + kp;
+          cell = d.pk_cell[q];
+          if (F32L) {
+            v = d.pk4[q];
+            d.s4[s] = v;
+          } else {
+            px = d.pkx[q]; py = d.pky[q]; pz = d.pkz[q]; tid = d.pk_tid[q];
+            d.sx[s] = px; d.sy[s] = py; d.sz[s] = pz; d.stid[s] = tid;
+          }
+          d.cell_sorted[s] = cell;
+          d.dead[s] = 0;
+        } else {
+        const uint32_t k = kp - tr.rel_park;
         if (k < tr.rel_mat) {
           rel_type = recreated_type(tr, k);
           recreated_position(tr, tr.rel_id0 + k, px, py, pz);
@@ -502,6 +525,7 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
         }
         d.cell_sorted[s] = cell;
         d.dead[s] = 0;
+        }  // unparked or new
       } else {
         cell = d.cell_sorted[s];
         // the occupancy bitmap is rebuilt by this step's gather: clear the words holding
@@ -523,7 +547,27 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
       } else {
         const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, cell);
         const Train& tr = d.trains[b];
-        if (!tr.active) {
+        if (!tr.active && tr.park_now) {
+          // park: the species moves to its train's parking buffers and leaves the
+          // stepped slots (sorted out with the removed ones)
+          const uint32_t am = __activemask();
+          const uint32_t peers = __match_any_sync(am, static_cast<uint32_t>(b));
+          const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+          uint32_t base = 0;
+          if (lane == leader) base = atomicAdd(&d.trains[b].park_n, static_cast<uint32_t>(__popc(peers)));
+          base = __shfl_sync(peers, base, leader);
+          const uint32_t k = base + __popc(peers & ((1u << lane) - 1u));
+          if (k < tr.park_cap) {
+            const uint32_t q = tr.park_base + k;
+            d.pk_cell[q] = cell;
+            if (F32L) d.pk4[q] = v;
+            else { d.pkx[q] = px; d.pky[q] = py; d.pkz[q] = pz; d.pk_tid[q] = tid; }
+          } else {
+            raise_status(d.g, CHEM_ECAPACITY);
+          }
+          key = d.g->sentinel_step;
+          ++n_dead_local;
+        } else if (!tr.active) {
           if (F32L) d.t4[s] = v;
           else { d.tx[s] = px; d.ty[s] = py; d.tz[s] = pz; d.ttid[s] = tid; }
           key = cell;

@@ -116,6 +116,14 @@ struct Train {
   uint32_t mat_n;          // survivors to re-create at the next release
   uint32_t rel_mat;        // of this step's releases, the re-created survivors (first)
   uint32_t mat_cum[MAXT];  // survivors of types <= t (inclusive prefix)
+  // parking (batched contexts): the species of a train that does not advance are moved
+  // out of the stepped slots, so that idle trains cost no diffusion, sort or gather, and
+  // come back as the first releases of the train's next step
+  uint32_t park_base;      // first slot of this train in the parking buffers
+  uint32_t park_cap;       // slots there (the train's species capacity)
+  uint32_t park_n;         // species parked
+  uint32_t park_now;       // this step moves the train's species to the parking buffers
+  uint32_t rel_park;       // of this step's releases, the unparked species (first)
   double hx_t_end;
   double hx_e[MAXR];       // real extents of the last stage (events)
   long long hx_E[MAXR];    // whole events of the last stage
@@ -187,6 +195,10 @@ struct Dev {
   double* tdx; double* tdy; double* tdz;  // FP64 displacement of this step, pre-sort order
   float4* td4;                            // FP32-local displacement of this step, pre-sort order
   float4* sd4;                            // the same in sorted order (gathered with the state)
+  // parking buffers (batched contexts; nullptr otherwise): the state and cell key of
+  // species of idle trains, per train from Train::park_base
+  float4* pk4; uint32_t* pk_cell;
+  double* pkx; double* pky; double* pkz; uint32_t* pk_tid;
   uint2* items;                           // pair-search work items {first home slot, cell}
   uint32_t cap_items;
   uint32_t* cell_sorted;
