@@ -11,8 +11,9 @@ species already resident in HBM (CUDA events around chem_run_until on the librar
 stream, L2 flushed before every timed trajectory); the FP64 form, the matched G-values
 and the end-to-end number through host buffers are reported beside it.
 
-``--impl reference`` times the FP64 reference on the host cores instead (bounded
-sample of the same workload: a few SBS steps of the ~1e6-species trajectory per step).
+``--impl reference`` times the FP64 reference (the plain C++ program, one
+single-threaded process per host core) instead: whole trajectories of the same workload
+in a smaller box at the same track and species density, one per process and step.
 """
 from __future__ import annotations
 
@@ -137,17 +138,29 @@ def aggregate_over_ranks(species_steps, seconds, device=None):
 # time-step schedule (workloads.tracks_same_density): its species-steps cost what the
 # 1e6-species trajectory's cost, early and late steps alike, in seconds of CPU time.
 ORACLE_L_NM = 1600.0
-ORACLE_KIND = "oracle (numpy/scipy FP64, the repository's reference)"
+ORACLE_KINDS = {
+    "cxx": "oracle (plain FP64 C++ program, one single-threaded process per core)",
+    "numpy": "oracle (numpy/scipy FP64, one process per core)",
+}
+
+
+def _oracle_module(name: str):
+    if name == "cxx":
+        from oracle import cxx
+        cxx.load()
+        return cxx
+    from oracle import sbs
+    return sbs
 
 
 def _oracle_worker(args):
-    seed, L, n_warm, n_timed = args
-    from oracle import sbs
+    seed, L, n_warm, n_timed, impl = args
     from paper_2509_03313_gb300 import workloads as W
+    ref = _oracle_module(impl)
     ss, busy = 0, 0.0
     for k in range(n_warm + n_timed):
         wl = W.tracks_same_density(seed + 7919 * k, L)
-        o = sbs.from_workload(wl, seed=seed + 7919 * k, record=False)
+        o = ref.from_workload(wl, seed=seed + 7919 * k, record=False)
         t0 = time.perf_counter()
         o.run_until(wl.t_end)
         if k >= n_warm:
@@ -156,13 +169,14 @@ def _oracle_worker(args):
     return ss, busy
 
 
-def oracle_rate(n_proc: int, L: float, n_warm: int, n_timed: int):
+def oracle_rate(n_proc: int, L: float, n_warm: int, n_timed: int, impl: str = "cxx"):
     """Aggregate species-steps/s of n_proc reference processes (one per core), each timing
     n_timed whole trajectories after n_warm untimed ones."""
+    _oracle_module(impl)  # the C++ program is compiled once, before the workers start
     ctx = mp.get_context("spawn")
     with ctx.Pool(n_proc) as pool:
         t0 = time.perf_counter()
-        res = pool.map(_oracle_worker, [(1000 + i, L, n_warm, n_timed) for i in range(n_proc)])
+        res = pool.map(_oracle_worker, [(1000 + i, L, n_warm, n_timed, impl) for i in range(n_proc)])
         wall = time.perf_counter() - t0
     ss = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
@@ -184,15 +198,15 @@ def run_reference_arm(args):
     cores = os.cpu_count() or 1
     n_proc = max(1, min(cores, args.ref_procs or cores))
     # each benchmark step: every process runs one whole trajectory
-    rate, ss, busy, wall = oracle_rate(n_proc, ORACLE_L_NM, args.warmup, args.steps)
+    rate, ss, busy, wall = oracle_rate(n_proc, ORACLE_L_NM, args.warmup, args.steps, args.cpu_oracle)
     sample = oracle_sample_text(n_proc, args.steps, ORACLE_L_NM)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * busy / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "species": args.species, "L_nm": 5000.0, "sample": sample},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": n_proc, "kind": ORACLE_KIND,
-                             "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": n_proc,
+                             "kind": ORACLE_KINDS[args.cpu_oracle], "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -315,8 +329,8 @@ def run_gpu_arm(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_proc = max(1, min(cores, args.ref_procs or cores))
-        rate, ss, busy, wall = oracle_rate(n_proc, ORACLE_L_NM, 0, args.cpu_trajectories)
-        cpu = {"value": rate, "unit": UNIT, "cores": n_proc, "kind": ORACLE_KIND,
+        rate, ss, busy, wall = oracle_rate(n_proc, ORACLE_L_NM, 0, args.cpu_trajectories, args.cpu_oracle)
+        cpu = {"value": rate, "unit": UNIT, "cores": n_proc, "kind": ORACLE_KINDS[args.cpu_oracle],
                "sample": oracle_sample_text(n_proc, args.cpu_trajectories, ORACLE_L_NM) + f"; {busy:.1f} s"}
     seed0 = 10_000 * (rank + 1)
     wl = W.single_pulse_tracks(seed0, n_species=args.species, n_tracks=args.tracks)
@@ -971,8 +985,10 @@ def main():
                     help="number of tracks (species per track = species / tracks)")
     ap.add_argument("--fp64-steps", type=int, default=0,
                     help="FP64 trajectories (default: as many as --steps, same seeds)")
-    ap.add_argument("--cpu-trajectories", type=int, default=1,
+    ap.add_argument("--cpu-trajectories", type=int, default=4,
                     help="whole reference trajectories per process in the cpu_baseline sample")
+    ap.add_argument("--cpu-oracle", default="cxx", choices=["cxx", "numpy"],
+                    help="reference timed on the host cores: the plain C++ program or the numpy one")
     ap.add_argument("--ref-procs", type=int, default=0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -21,3 +21,15 @@ def read_golden(name):
             if line and not line.startswith("#"):
                 rows.append(line.split())
     return rows
+
+
+@pytest.fixture(params=["numpy", "cxx"])
+def impl(request):
+    """The FP64 reference under test: the numpy one (``oracle.sbs``) or the plain C++
+    program behind the same interface (``oracle.cxx``); pins run on both."""
+    if request.param == "cxx":
+        from oracle import cxx
+        cxx.load()
+        return cxx
+    from oracle import sbs
+    return sbs

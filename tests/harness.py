@@ -55,9 +55,14 @@ def gpu_run(wl, seed, precision=chem.CHEM_FP64, t_end=None, capacity=None, recor
     return out
 
 
-def oracle_run(wl, seed, t_end=None, train_id=0, t_stops=None):
-    from oracle import sbs
-    o = sbs.from_workload(wl, seed=seed, train_id=train_id)
+def oracle_run(wl, seed, t_end=None, train_id=0, t_stops=None, impl="numpy"):
+    """The FP64 reference on a workload: the numpy one, or the plain C++ program
+    (impl="cxx") for the larger cases."""
+    if impl == "cxx":
+        from oracle import cxx as ref
+    else:
+        from oracle import sbs as ref
+    o = ref.from_workload(wl, seed=seed, train_id=train_id)
     stops = list(t_stops or []) + [t_end if t_end is not None else wl.t_end]
     counts = []
     for t in stops:

@@ -63,3 +63,26 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     from paper_2509_03313_gb300 import chem
     with pytest.raises(ImportError):
         chem.load(str(tmp_path / "libchem.so"))
+
+
+def test_library_and_references_stay_apart():
+    """The library never loads a reference, and the C++ reference includes nothing of the
+    CUDA path (each side computes the method on its own)."""
+    import subprocess
+    import sys
+    code = ("import sys; import paper_2509_03313_gb300 as p; "
+            "from paper_2509_03313_gb300 import chem, workloads, physchem, hybrid, build; "
+            "bad = [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; "
+            "print(bad); sys.exit(1 if bad else 0)")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    pkg = os.path.join(ROOT, "paper_2509_03313_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f), errors="replace").read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
+                assert "sbs_oracle" not in text, f
+    src = open(os.path.join(ROOT, "oracle", "csrc", "sbs_oracle.cpp")).read()
+    includes = re.findall(r'#include\s*[<"]([^>"]+)[>"]', src)
+    assert includes and all("/" not in i and not i.endswith((".h", ".cuh")) for i in includes), includes

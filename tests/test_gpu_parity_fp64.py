@@ -39,6 +39,17 @@ def test_tracks_with_log_steps_and_staggered_arrivals():
     assert_fp64_parity(g, o, wl.L)
 
 
+def test_tracks_whole_trajectory_at_benchmark_density():
+    # The benchmark's track workload in a 1.6 um box at its track and species density
+    # (20 tracks, 32,000 species), every step from 1 ps to 1 us (about 150 log-growing
+    # steps, more than 10,000 events): checked against the C++ reference.
+    wl = W.tracks_same_density(21, 1600.0)
+    g = gpu_run(wl, 21)
+    o = oracle_run(wl, 21, impl="cxx")
+    assert o.events_total.sum() > 10_000
+    assert_fp64_parity(g, o, wl.L)
+
+
 def test_run_until_in_chunks_equals_oracle_chunks():
     wl = W.uniform_2000(seed=4, L=200.0, n_steps=100)
     stops = [13e-9, 50e-9, 50e-9, 77.5e-9]

@@ -1,6 +1,7 @@
-"""Pins of the FP64 reference against facts fixed outside it: published known answers,
-closed forms, invariants, limits and brute force. A plausible slip in the reference
-(a dropped factor, a swapped operand, a wrong sign) fails at least one of these."""
+"""Pins of the FP64 references (numpy, ``oracle.sbs``, and the plain C++ program,
+``oracle.cxx``) against facts fixed outside them: published known answers, closed forms,
+invariants, limits and brute force. A plausible slip in either reference (a dropped
+factor, a swapped operand, a wrong sign) fails at least one of these."""
 import math
 
 import numpy as np
@@ -13,27 +14,27 @@ from paper_2509_03313_gb300 import workloads as W
 
 
 # ---------------------------------------------------------------- random numbers
-def test_philox_known_answers():
+def test_philox_known_answers(impl):
     for row in read_golden("philox4x32_10_kat.txt"):
         v = [int(x, 16) for x in row]
-        out = sbs.philox4x32_10(v[0:4], v[4:6])
+        out = impl.philox4x32_10(v[0:4], v[4:6])
         assert [int(o) for o in out] == v[6:10]
 
 
-def test_uniform_maps_extremes():
+def test_uniform_maps_extremes(impl):
     # (0, 1] and [0, 1) from the top 53 bits of a 64-bit word pair.
-    assert sbs.uniform_open0(0, 0) == math.ldexp(1.0, -53)
-    assert sbs.uniform_open0(0xFFFFFFFF, 0xFFFFFFFF) == 1.0
-    assert sbs.uniform_closed0(0, 0) == 0.0
-    assert sbs.uniform_closed0(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - math.ldexp(1.0, -53)
+    assert impl.uniform_open0(0, 0) == math.ldexp(1.0, -53)
+    assert impl.uniform_open0(0xFFFFFFFF, 0xFFFFFFFF) == 1.0
+    assert impl.uniform_closed0(0, 0) == 0.0
+    assert impl.uniform_closed0(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - math.ldexp(1.0, -53)
     # The low 11 bits are dropped.
-    assert sbs.uniform_closed0(0, 0x7FF) == 0.0
-    assert sbs.uniform_closed0(0, 0x800) == math.ldexp(1.0, -53)
+    assert impl.uniform_closed0(0, 0x7FF) == 0.0
+    assert impl.uniform_closed0(0, 0x800) == math.ldexp(1.0, -53)
 
 
-def test_gaussians_are_standard_normal():
-    key = sbs.philox_key(12345, 3)
-    g = sbs.gaussians(np.arange(200_000), 7, key)
+def test_gaussians_are_standard_normal(impl):
+    key = impl.philox_key(12345, 3)
+    g = impl.gaussians(np.arange(200_000), 7, key)
     for a in range(3):
         x = g[:, a]
         assert abs(x.mean()) < 5 / math.sqrt(x.size)
@@ -42,42 +43,42 @@ def test_gaussians_are_standard_normal():
     # Independent axes and independent steps.
     assert abs(np.corrcoef(g[:, 0], g[:, 1])[0, 1]) < 0.02
     assert abs(np.corrcoef(g[:, 0], g[:, 2])[0, 1]) < 0.02
-    g2 = sbs.gaussians(np.arange(200_000), 8, key)
+    g2 = impl.gaussians(np.arange(200_000), 8, key)
     assert abs(np.corrcoef(g[:, 0], g2[:, 0])[0, 1]) < 0.02
 
 
-def test_acceptance_uniform_is_uniform_and_symmetric_in_keying():
-    key = sbs.philox_key(99, 0)
-    u = sbs.acceptance_uniform(np.arange(100_000), np.arange(100_000) + 5, 3, key)
+def test_acceptance_uniform_is_uniform_and_symmetric_in_keying(impl):
+    key = impl.philox_key(99, 0)
+    u = impl.acceptance_uniform(np.arange(100_000), np.arange(100_000) + 5, 3, key)
     assert stats.kstest(u, "uniform").pvalue > 1e-3
     assert u.min() >= 0.0 and u.max() < 1.0
 
 
 # ---------------------------------------------------------------- Eq. 1 and Eq. 2
-def test_wrap_eq1_cases():
+def test_wrap_eq1_cases(impl):
     L = 10.0
     x = np.array([4.999, 5.0, -5.0, -5.0001, 0.0, 15.0, -15.0, 27.5, -27.5, 5.0 + 1e-12])
-    y = sbs.wrap(x, L)
+    y = impl.wrap(x, L)
     assert np.all(y >= -5.0) and np.all(y < 5.0)
     np.testing.assert_allclose(y, [4.999, -5.0, -5.0, 4.9999, 0.0, -5.0, -5.0, -2.5, 2.5,
                                    -5.0 + 1e-12], rtol=0, atol=1e-12)
 
 
-def test_minimum_image_eq2_cases():
+def test_minimum_image_eq2_cases(impl):
     L = 10.0
     dx = np.array([4.9, 5.0, -5.0, -5.1, 9.0, -9.0, 0.0])
-    np.testing.assert_allclose(sbs.minimum_image(dx, L), [4.9, -5.0, -5.0, 4.9, -1.0, 1.0, 0.0],
+    np.testing.assert_allclose(impl.minimum_image(dx, L), [4.9, -5.0, -5.0, 4.9, -1.0, 1.0, 0.0],
                                atol=1e-12)
 
 
 # ---------------------------------------------------------------- P2: free diffusion
-def test_msd_equals_6Dt_per_species():
+def test_msd_equals_6Dt_per_species(impl):
     L = 1000.0
     n_per = 4000
     wl_types = np.repeat(np.arange(7), n_per).astype(np.int32)
     rng = np.random.default_rng(5)
     xyz = rng.uniform(-L / 2, L / 2, size=(wl_types.size, 3))
-    o = sbs.SBSOracle(W.D_NM2_S, [], L, seed=17, dt_min=2e-9, dt_max=2e-9, record=False)
+    o = impl.SBSOracle(W.D_NM2_S, [], L, seed=17, dt_min=2e-9, dt_max=2e-9, record=False)
     o.inject(wl_types, xyz, np.zeros(wl_types.size))
     # All arrive at t = 0, so ids follow the input order.
     ids0, p0 = np.arange(wl_types.size), xyz
@@ -87,7 +88,7 @@ def test_msd_equals_6Dt_per_species():
     for _ in range(n_steps):
         o.step_once(math.inf)
         _, _, p = o.state()
-        disp += sbs.minimum_image(p - prev, L)
+        disp += impl.minimum_image(p - prev, L)
         prev = p
     t = n_steps * 2e-9
     for ty in range(7):
@@ -100,13 +101,13 @@ def test_msd_equals_6Dt_per_species():
             assert abs(va - 1.0) < 5 * math.sqrt(2.0 / n_per)
 
 
-def test_zero_dose_and_inert_species():
-    o = sbs.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, 500.0, seed=1)
+def test_zero_dose_and_inert_species(impl):
+    o = impl.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, 500.0, seed=1)
     assert o.run_until(5e-9) == 5
     assert o.species_steps == 0 and o.events_total.sum() == 0
     # Only H2: nothing reacts, counts are constant.
     rng = np.random.default_rng(2)
-    o = sbs.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, 500.0, seed=1)
+    o = impl.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, 500.0, seed=1)
     o.inject(np.full(300, W.H2), rng.uniform(-250, 250, (300, 3)), np.zeros(300))
     o.run_until(20e-9)
     assert o.events_total.sum() == 0
@@ -114,9 +115,9 @@ def test_zero_dose_and_inert_species():
 
 
 # ---------------------------------------------------------------- time-step policy
-def test_log_dt_schedule_is_a_geometric_series():
+def test_log_dt_schedule_is_a_geometric_series(impl):
     g = W.LOG_GROWTH_20_PER_DECADE
-    o = sbs.SBSOracle(W.D_NM2_S, [], 5000.0, seed=0, dt_min=1e-12, dt_max=1.0, dt_growth=g)
+    o = impl.SBSOracle(W.D_NM2_S, [], 5000.0, seed=0, dt_min=1e-12, dt_max=1.0, dt_growth=g)
     o.inject([0], [[0.0, 0.0, 0.0]], [0.0])
     o.run_until(1e-6)
     steps = o.step_log
@@ -129,8 +130,8 @@ def test_log_dt_schedule_is_a_geometric_series():
     assert abs(len(steps) - 20 * math.log10(1e6 * (g - 1) + 1)) <= 2
 
 
-def test_release_rounds_arrivals_up_and_resets_dt():
-    o = sbs.SBSOracle(W.D_NM2_S, [], 1000.0, seed=0, dt_min=1e-9, dt_max=4e-9, dt_growth=2.0)
+def test_release_rounds_arrivals_up_and_resets_dt(impl):
+    o = impl.SBSOracle(W.D_NM2_S, [], 1000.0, seed=0, dt_min=1e-9, dt_max=4e-9, dt_growth=2.0)
     o.inject([0, 1, 2], np.zeros((3, 3)), [0.0, 2.5e-9, 2.5e-9])
     o.inject([3], np.zeros((1, 3)), [1.0e-9])
     o.run_until(10e-9)
@@ -146,14 +147,14 @@ def test_release_rounds_arrivals_up_and_resets_dt():
 
 # ---------------------------------------------------------------- P5: brute force
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_pair_query_matches_brute_force(seed):
+def test_pair_query_matches_brute_force(seed, impl):
     rng = np.random.default_rng(seed)
     L = 100.0
     pos = rng.uniform(-L / 2, L / 2, size=(500, 3))
     pos[:20, 0] = -L / 2 + rng.uniform(0, 0.5, 20)   # crowd both faces
     pos[20:40, 0] = L / 2 - rng.uniform(1e-9, 0.5, 20)
-    for r in (3.0, 9.5, 30.0):
-        a = {tuple(p) for p in sbs.all_pairs_within(pos, L, r)}
+    for r in (3.0, 9.5, 30.0, 40.0):
+        a = {tuple(p) for p in impl.all_pairs_within(pos, L, r)}
         b = {tuple(p) for p in sbs.all_pairs_within_bruteforce(pos, L, r)}
         assert a == b
 
@@ -179,7 +180,7 @@ def _locally_dominant(id_lo, id_hi, d1sq):
 
 
 @pytest.mark.parametrize("seed", range(6))
-def test_greedy_matching_equals_locally_dominant_rounds(seed):
+def test_greedy_matching_equals_locally_dominant_rounds(seed, impl):
     rng = np.random.default_rng(seed)
     n_sp, n_c = 40, 120
     a = rng.integers(0, n_sp, n_c)
@@ -189,14 +190,14 @@ def test_greedy_matching_equals_locally_dominant_rounds(seed):
     _, u = np.unique(np.stack([lo, hi], 1), axis=0, return_index=True)
     lo, hi = lo[u], hi[u]
     d = rng.integers(0, 5, lo.size).astype(np.float64)  # many exact ties
-    got = sorted(sbs.greedy_matching(lo, hi, d).tolist())
+    got = sorted(impl.greedy_matching(lo, hi, d).tolist())
     assert got == _locally_dominant(lo, hi, d)
 
 
 # ---------------------------------------------------------------- P1: conservation
-def test_charge_and_atoms_conserved_dense_mixture():
+def test_charge_and_atoms_conserved_dense_mixture(impl):
     wl = W.uniform_2000(seed=3, L=200.0, n_steps=300)
-    o = sbs.from_workload(wl, seed=3)
+    o = impl.from_workload(wl, seed=3)
     c0 = o.p_types.copy()
 
     def totals(counts, water):
@@ -214,13 +215,13 @@ def test_charge_and_atoms_conserved_dense_mixture():
     assert np.unique(ids).size == ids.size
 
 
-def test_products_sit_at_the_diffusion_weighted_encounter_point():
+def test_products_sit_at_the_diffusion_weighted_encounter_point(impl):
     # e_aq + OH at 0.3 nm (inside R2 = 0.565 nm) with a negligible step: they react in
     # step 0 and the OH- sits nearer the slower OH, D_e / (D_e + D_OH) of the way.
     L = 100.0
     xe = np.array([1.0, 2.0, 3.0])
     xoh = xe + np.array([0.3, 0.0, 0.0])
-    o = sbs.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, L, seed=4, dt_min=1e-26, dt_max=1e-26)
+    o = impl.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, L, seed=4, dt_min=1e-26, dt_max=1e-26)
     o.inject([W.E_AQ, W.OH], np.stack([xe, xoh]), [0.0, 0.0])
     o.step_once(1.0)
     ids, types, pos = o.state()
@@ -229,7 +230,7 @@ def test_products_sit_at_the_diffusion_weighted_encounter_point():
     assert frac == pytest.approx(W.D_NM2_S[W.E_AQ] / (W.D_NM2_S[W.E_AQ] + W.D_NM2_S[W.OH]),
                                  abs=1e-6)
     # A self reaction puts its product at the midpoint, across a periodic face too.
-    o = sbs.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, L, seed=4, dt_min=1e-26, dt_max=1e-26)
+    o = impl.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, L, seed=4, dt_min=1e-26, dt_max=1e-26)
     o.inject([W.OH, W.OH], [[49.95, 0, 0], [-49.95, 0, 0]], [0.0, 0.0])
     o.step_once(1.0)
     _, types, pos = o.state()
@@ -250,26 +251,26 @@ def _pairs_on_lattice(n_side, spacing, r0, seed):
     return a, b, n_side * spacing
 
 
-def test_touch_probability_limits():
+def test_touch_probability_limits(impl):
     R, Ddt = 0.5, 4.0
     d0 = np.array([0.6, 1.0, 3.0, 8.0])
     d1 = np.array([0.7, 2.0, 1.5, 9.0])
-    p = sbs.touch_probability(d0, d1, R, Ddt)
+    p = impl.touch_probability(d0, d1, R, Ddt)
     planar = np.exp(-(d0 - R) * (d1 - R) / Ddt)
     assert np.all((p > 0) & (p <= planar))
-    np.testing.assert_allclose(p, sbs.touch_probability(d1, d0, R, Ddt))  # time reversal
-    assert np.all(sbs.touch_probability([0.4, 0.6], [0.6, 0.5], R, Ddt) == 1.0)
+    np.testing.assert_allclose(p, impl.touch_probability(d1, d0, R, Ddt))  # time reversal
+    assert np.all(impl.touch_probability([0.4, 0.6], [0.6, 0.5], R, Ddt) == 1.0)
     # a point target is never touched; a sphere much larger than the step looks flat
-    assert np.all(sbs.touch_probability(d0, d1, 1e-12, Ddt) < 1e-11)
+    assert np.all(impl.touch_probability(d0, d1, 1e-12, Ddt) < 1e-11)
     big = 1000.0
-    np.testing.assert_allclose(sbs.touch_probability(big + d0, big + d1, big, Ddt),
+    np.testing.assert_allclose(impl.touch_probability(big + d0, big + d1, big, Ddt),
                                np.exp(-d0 * d1 / Ddt), rtol=5e-3)
     # decreasing in the end separation
-    q = sbs.touch_probability(1.0, np.linspace(0.6, 10.0, 50), R, Ddt)
+    q = impl.touch_probability(1.0, np.linspace(0.6, 10.0, 50), R, Ddt)
     assert np.all(np.diff(q) < 0)
 
 
-def test_touch_probability_matches_simulated_paths():
+def test_touch_probability_matches_simulated_paths(impl):
     """Brute force: fine-grained free relative paths from distance d0; the fraction that
     came within R, binned by end distance, against the formula (discrete monitoring
     misses a little, so the simulated fraction sits slightly below)."""
@@ -287,21 +288,21 @@ def test_touch_probability_matches_simulated_paths():
     for lo, hi in ((1.2, 2.0), (2.0, 3.0), (3.0, 4.5), (4.5, 7.0)):
         m = (d1 >= lo) & (d1 < hi)
         sim = hit[m].mean()
-        ref = sbs.touch_probability(d0, d1[m], R, D * dt).mean()
+        ref = impl.touch_probability(d0, d1[m], R, D * dt).mean()
         assert abs(sim - ref) < 4 * math.sqrt(ref * (1 - ref) / m.sum()) + 0.04 * ref, (lo, sim, ref)
 
 
 @pytest.mark.parametrize("dt", [1e-12, 1e-11, 1e-10, 1e-9])
-def test_first_passage_probability_of_one_pair(dt):
+def test_first_passage_probability_of_one_pair(dt, impl):
     """P(react by t | r0) = (R/r0) erfc((r0 - R) / sqrt(4 D_AB t)) (Eq. PDF0, read with
     the standard sign) for isolated A + B pairs."""
     D = np.array([9.3e9, 5.3e9])
     rx = [(0, 1, 11.0e10, (), 0)]
-    R = sbs.reaction_radius(11.0e10, 14.6e9)
+    R = impl.reaction_radius(11.0e10, 14.6e9)
     r0 = 1.6
     a, b, L = _pairs_on_lattice(22, 60.0, r0, seed=int(dt * 1e13))
     n = a.shape[0]
-    o = sbs.SBSOracle(D, rx, L, seed=77, dt_min=dt, dt_max=dt, record=False)
+    o = impl.SBSOracle(D, rx, L, seed=77, dt_min=dt, dt_max=dt, record=False)
     o.inject(np.r_[np.zeros(n), np.ones(n)].astype(int), np.r_[a, b], np.zeros(2 * n))
     for t in ((0.1e-9, 0.5e-9) if dt < 1e-10 else (1e-9, 5e-9)):
         o.run_until(t)
@@ -319,12 +320,12 @@ def _ode_counts(D, rx, counts0, L, times):
 
 
 @pytest.mark.parametrize("dt", [5e-12, 1e-10, 2e-9])
-def test_smoluchowski_rate_A_plus_B(dt):
+def test_smoluchowski_rate_A_plus_B(dt, impl):
     D = np.array([9.3e9, 5.3e9])
     rx = [(0, 1, 11.0e10, (), 0)]
     n, L = 1500, 200.0
     rng = np.random.default_rng(11)
-    o = sbs.SBSOracle(D, rx, L, seed=5, dt_min=dt, dt_max=dt, record=False)
+    o = impl.SBSOracle(D, rx, L, seed=5, dt_min=dt, dt_max=dt, record=False)
     o.inject(np.r_[np.zeros(n), np.ones(n)].astype(int), rng.uniform(-L / 2, L / 2, (2 * n, 3)),
              np.zeros(2 * n))
     times = np.array([2e-9, 6e-9, 12e-9])
@@ -337,13 +338,13 @@ def test_smoluchowski_rate_A_plus_B(dt):
         assert abs((n - got) - reacted_ref) < 3 * sigma + 0.05 * reacted_ref, (t, got, ref[0])
 
 
-def test_smoluchowski_rate_self_reaction_uses_tabulated_2k():
+def test_smoluchowski_rate_self_reaction_uses_tabulated_2k(impl):
     # OH + OH -> H2O2 with the printed 2k: -d[OH]/dt = k_tab [OH]^2 (Eq. rateequation2).
     D = np.array([2.2e9, 2.3e9])
     rx = [(0, 0, 0.95e10, (1,), 0)]
     n, L = 3000, 150.0
     rng = np.random.default_rng(12)
-    o = sbs.SBSOracle(D, rx, L, seed=6, dt_min=2e-11, dt_max=2e-11, record=False)
+    o = impl.SBSOracle(D, rx, L, seed=6, dt_min=2e-11, dt_max=2e-11, record=False)
     o.inject(np.zeros(n, int), rng.uniform(-L / 2, L / 2, (n, 3)), np.zeros(n))
     times = np.array([10e-9, 30e-9])
     ode = _ode_counts(D, rx, [n, 0], L, times)
@@ -381,7 +382,7 @@ def test_ode_full_table_conserves_and_agrees_across_schemes():
     np.testing.assert_allclose(q, q[0], rtol=0, atol=1e-12 * np.abs(conc0).sum())
 
 
-def test_sbs_mixture_tracks_the_rate_equations():
+def test_sbs_mixture_tracks_the_rate_equations(impl):
     """The full water table step by step (0.4 mM mixture, 0.2 um box, dt up to 1 ns)
     against the rate equations with the transient Smoluchowski factor: within 25 % for
     every species with at least 40 molecules at 0.3 us (the paper saw 20 % and 12 % for H2
@@ -391,7 +392,7 @@ def test_sbs_mixture_tracks_the_rate_equations():
     runs = []
     for seed in range(3):
         wl = W.volume_scaling(200.0, seed=100 + seed, dt_max=1e-9)
-        o = sbs.from_workload(wl, seed=seed, record=False)
+        o = impl.from_workload(wl, seed=seed, record=False)
         row = []
         for t in T:
             o.run_until(t)
