@@ -88,9 +88,17 @@ struct chem_ctx {
   std::vector<std::pair<void*, size_t>> allocs;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  bool graph_events = false;  // the captured graph records the phase events
   int steps_per_launch = 16;
   bool persistent = false;
   int cell_factor_x100 = 1600;  // hash cells per species (x100) of the runtime grid limit
+  // radix passes of the cell sort: with one train only as many as the runtime grid limit
+  // needs (pass_nmax cells per axis at most, and pass_cbref bits per axis for the cells
+  // the species were last sorted in); with several trains all of the allocated key bits
+  int passes_alloc = 1;
+  int cb_alloc0 = 0;
+  int pass_nmax = 3;
+  int pass_cbref = 0;
   int item_home = -1;            // pair search: 0 = one thread per home species, 1..32 =
                                  // cell tiles of that many homes, -1 = chosen per step
   Global* g_pinned = nullptr;  // host copy of the global counters
@@ -320,12 +328,22 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
 
 int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 7 + ctx->d.passes; }
 
+// Radix passes for the captured graph (see chem_ctx::passes_alloc).
+int sort_passes(const chem_ctx* ctx) {
+  if (ctx->B != 1) return ctx->passes_alloc;
+  const int nm = std::min(ctx->pass_nmax, (1 << ctx->cb_alloc0) - 1);
+  const int cb = std::min(ctx->cb_alloc0, std::max(bits_for(static_cast<uint64_t>(nm)), ctx->pass_cbref));
+  return std::max(1, std::min(ctx->passes_alloc, (3 * cb + 7) / 8));
+}
+
 chem_status capture_graph(chem_ctx* ctx) {
   ctx->lc.search_tps = ctx->item_home == 0 ? 1 : (ctx->item_home > 0 ? 0 : 2);
+  ctx->d.passes = sort_passes(ctx);
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
   }
+  ctx->graph_events = false;
   const size_t n_ev = (ctx->profiling && !ctx->persistent)
                           ? static_cast<size_t>(ctx->steps_per_launch) * 2 * N_PHASES : 0;
   while (ctx->events.size() < n_ev) {
@@ -358,6 +376,7 @@ chem_status capture_graph(chem_ctx* ctx) {
   cudaGraphDestroy(g);
   CK(e);
   ctx->graph_steps = ctx->steps_per_launch;
+  ctx->graph_events = n_ev > 0;
   return CHEM_OK;
 }
 
@@ -392,7 +411,7 @@ chem_status run_loop(chem_ctx* ctx) {
     active_before = g.steps_active;
     if (ctx->persistent) {
       ctx->stats.phase_launches[PH_PERSISTENT] += 1;
-    } else if (!ctx->events.empty()) {
+    } else if (ctx->graph_events) {
       for (uint32_t st = 0; st < stepped && st < static_cast<uint32_t>(ctx->graph_steps); ++st) {
         for (int ph = 0; ph < PH_PERSISTENT; ++ph) {
           float ms = 0.f;
@@ -400,6 +419,8 @@ chem_status run_loop(chem_ctx* ctx) {
           if (cudaEventElapsedTime(&ms, ev[2 * ph], ev[2 * ph + 1]) == cudaSuccess) {
             ctx->stats.phase_ms[ph] += ms;
             ctx->stats.phase_launches[ph] += ph == PH_SORT ? ctx->d.passes : (ph == PH_RELEASE ? 0 : 1);
+          } else {
+            cudaGetLastError();  // a phase not timed: no error is left for the next launch check
           }
         }
       }
@@ -831,6 +852,11 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     t.n_alloc = n_alloc;
     t.cb_alloc = bits_for(static_cast<uint64_t>(n_alloc - 1));
     t.cb = t.cb_ref = t.cb_alloc;
+    if (b == 0) {
+      ctx->cb_alloc0 = t.cb_alloc;
+      ctx->pass_nmax = n_max;
+      ctx->pass_cbref = 0;  // no species sorted yet: the first step picks the grid
+    }
     t.inv_L = 1.0 / c.L_nm;
     t.cell_base = static_cast<uint32_t>(cells);
     cells += 1ull << (3 * t.cb_alloc);
@@ -904,6 +930,7 @@ chem_status chem_batch_init(const chem_config* cfgs, int32_t n_trains, chem_ctx*
     *out = ctx;
     return fail(ctx, CHEM_EINVAL, "too many hash cells");
   }
+  ctx->passes_alloc = d.passes;
   d.precision = ctx->precision;
   d.max_tiles = static_cast<uint32_t>(cap / SORT_TILE_MIN + 2);
   bool ok = true;
@@ -1266,6 +1293,8 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   const int saved_spl = ctx->steps_per_launch;
   const bool saved_prof = ctx->profiling;
   ctx->profiling = false;
+  // each trial's graph sorts the key bits its grid limit needs
+  ctx->pass_cbref = tr0[0].n_ref != 0 ? tr0[0].cb_ref : 0;
   for (int combo = 0; combo < 4; ++combo) {
     const bool pers = mode_cands[combo / 2];
     const int spl = spl_cands[combo % 2];
@@ -1273,8 +1302,6 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
     ctx->persistent = pers;
     ctx->steps_per_launch = spl;
     ctx->item_home = ih;  // selects the search kernel of the captured graph
-    s = capture_graph(ctx);
-    if (s) break;
     {
       for (int nm : n_cands) {
         const double spent = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
@@ -1287,6 +1314,9 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
         std::vector<Train> tr = tr0;
         for (auto& t : tr) { t.n_max = std::min(nm, t.n_alloc); t.t_end = std::numeric_limits<double>::infinity(); }
         s = upload_trains(ctx, tr);
+        if (s) break;
+        ctx->pass_nmax = tr[0].n_max;
+        s = capture_graph(ctx);
         if (s) break;
         Global& gfix = *ctx->g_pinned;
         CK(cudaMemcpyAsync(&gfix, d.g, sizeof(Global), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1341,6 +1371,7 @@ chem_status chem_autotune(chem_ctx* ctx, double budget_ms, int32_t* chosen) {
   }
   for (auto& t : tr0) t.n_max = std::min(best_n, t.n_alloc);
   chem_status s2 = upload_trains(ctx, tr0);
+  ctx->pass_nmax = tr0[0].n_max;
   // release the snapshot
   for (size_t i = 0; i < ctx->allocs.size(); ++i) {
     if (ctx->allocs[i].first == snap) {
@@ -1381,6 +1412,8 @@ chem_status chem_set_tuning(chem_ctx* ctx, const int32_t* tuning) {
   for (auto& t : tr) t.n_max = std::min(n_lim, t.n_alloc);
   s = upload_trains(ctx, tr);
   if (s) return s;
+  ctx->pass_nmax = tr[0].n_max;
+  ctx->pass_cbref = tr[0].n_ref != 0 ? tr[0].cb_ref : 0;
   s = upload_mapping(ctx, ih);
   if (s) return s;
   ctx->item_home = ih;

@@ -388,10 +388,13 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
   __syncthreads();  // the grids above are written
   if (tid == 0) {
     // removed species sort after every live one: with one train the all-ones cell index
-    // of this step's width (no cell has it), so the top key bits stay zero and their
-    // radix pass is skipped; with several trains, past the last train's cells
+    // of the grid's width (this step's grid, or the last one when the train is idle; no
+    // cell has it, and it stays within the bits the launched passes sort), so the top
+    // key bits stay zero and their radix pass is skipped; with several trains, past the
+    // last train's cells
     const Train& t0 = d.trains[0];
-    d.g->sentinel_step = (d.n_trains == 1 && t0.active) ? t0.cell_base + ((1u << (3 * t0.cb)) - 1u) : d.sentinel;
+    const int kb = min(3 * t0.cb, 8 * d.passes);
+    d.g->sentinel_step = d.n_trains == 1 ? t0.cell_base + (kb >= 32 ? 0xFFFFFFFFu : (1u << kb) - 1u) : d.sentinel;
   }
   for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&d.g->hist[0][0])[i] = 0u;
   __syncthreads();
@@ -1087,10 +1090,26 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
                                 : (o < 0 ? of + static_cast<float>(-o - 1) * hcell : 0.f);
           return fmaxf(g - eps, 0.f);
         };
-        const int n_fwd = tr.reach == 2 ? N_FWD2 : N_FWD;
-        for (int k = 1; k < n_fwd; ++k) {
-          const float gx = gap(c_fwd.x[k], ofx), gy = gap(c_fwd.y[k], ofy), gz = gap(c_fwd.z[k], ofz);
-          if (gx * gx + gy * gy + gz * gz <= rcmax2) kmask |= 1ull << k;
+        if (tr.reach == 2) {
+          for (int k = 1; k < N_FWD2; ++k) {
+            const float gx = gap(c_fwd.x[k], ofx), gy = gap(c_fwd.y[k], ofy), gz = gap(c_fwd.z[k], ofz);
+            if (gx * gx + gy * gy + gz * gz <= rcmax2) kmask |= 1ull << k;
+          }
+        } else {
+          // one cell out: per axis the gap is 0 (same layer), the distance to the lower
+          // face (offset -1) or to the upper face (offset +1); the 13 offsets unrolled
+          const float xm = gap(-1, ofx), xp = gap(1, ofx), ym = gap(-1, ofy), yp = gap(1, ofy);
+          const float zp = gap(1, ofz);
+          const float xm2 = xm * xm, xp2 = xp * xp, ym2 = ym * ym, yp2 = yp * yp, zp2 = zp * zp;
+#pragma unroll
+          for (int k = 1; k < N_FWD; ++k) {
+            int dx, dy, dz;
+            fwd_offset(k, dx, dy, dz);
+            const float sx = dx < 0 ? xm2 : (dx > 0 ? xp2 : 0.f);
+            const float sy = dy < 0 ? ym2 : (dy > 0 ? yp2 : 0.f);
+            const float sz = dz > 0 ? zp2 : 0.f;
+            if ((sx + sy) + sz <= rcmax2) kmask |= 1ull << k;
+          }
         }
       }
       // kept in shared memory while the ranges are walked (registers are the walk's)
@@ -1164,9 +1183,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             const bool give = ((donors >> lane) & 1u) && __popc(donors & lanemask_lt) < n_pairs;
             int src = lane;
             if (take) {  // the k-th idle lane borrows from the k-th donor
-              uint32_t m = donors;
-              for (int qq = __popc(idle & lanemask_lt); qq > 0; --qq) m &= m - 1u;
-              src = __ffs(m) - 1;
+              src = static_cast<int>(__fns(donors, 0u, __popc(idle & lanemask_lt) + 1));
             }
             const uint32_t mid = j + rem / 2u;
             const uint32_t s2 = __shfl_sync(0xffffffffu, hs, src);

@@ -97,3 +97,32 @@ def test_set_tuning_rejects_out_of_range_values():
             assert ei.value.status == chem.CHEM_EINVAL
     finally:
         chem.chem_destroy(ctx)
+
+
+def test_profiling_on_then_off_mid_run_leaves_fp64_results_unchanged():
+    # Phase events are recorded only by graphs captured with profiling on; a run after
+    # profiling is switched off (and the grid limit changed) must neither query them nor
+    # fail, and the results stay the reference's.
+    wl = W.uniform_2000(seed=53, L=200.0, n_steps=120)
+    ctx, keep = _ctx(wl, 53, chem.CHEM_FP64)
+    try:
+        p = wl.pulses[0]
+        chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        chem.chem_set_profiling(ctx, True)
+        chem.chem_set_tuning(ctx, 1, 40, -1, 1)
+        chem.chem_run_until(ctx, 40e-9)
+        st = chem.chem_get_stats(ctx)
+        assert st["phase_launches"]["search"] == 40 and st["phase_ms"]["search"] > 0.0
+        chem.chem_set_profiling(ctx, False)
+        chem.chem_set_tuning(ctx, 8, 25, -1, 1)
+        chem.chem_run_until(ctx, 90e-9)
+        chem.chem_set_tuning(ctx, 4, 60, -1, 1)
+        chem.chem_run_until(ctx, wl.t_end)
+        ids, types, xyz = chem.chem_get_state(ctx)
+        o = np.argsort(ids)
+        g = {"tally": chem.chem_tally(ctx, 7, 9), "events": chem.chem_get_events(ctx),
+             "steps": chem.chem_get_step_log(ctx),
+             "state": (ids[o].astype(np.int64), types[o].astype(np.int64), xyz[o])}
+    finally:
+        chem.chem_destroy(ctx)
+    assert_fp64_parity(g, oracle_run(wl, 53, t_stops=[40e-9, 90e-9]), wl.L)
