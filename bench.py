@@ -344,8 +344,10 @@ def run_gpu_arm(args):
     if not args.no_fp64:
         modes.append(("fp64", chem.CHEM_FP64, args.fp64_steps if args.fp64_steps > 0 else args.steps))
     for name, prec, k_steps in modes:
-        ctx, keep = make_ctx(chem, wl, prec, seed0, cap, stream.cuda_stream, alloc,
-                             profiling=not args.no_phase_events)
+        # the timed trajectories run without phase events (recorded around every phase of
+        # every step they cost about 13 % of the step); the phase times come from
+        # profiled trajectories right after the timed and end-to-end ones
+        ctx, keep = make_ctx(chem, wl, prec, seed0, cap, stream.cuda_stream, alloc, profiling=False)
         tuned = None
         try:
             if name == "fp32l" and args.tuned:
@@ -357,8 +359,6 @@ def run_gpu_arm(args):
                 tuned = chem.chem_autotune(ctx, args.autotune_ms)
             for w in range(args.warmup):
                 trajectory(chem, ctx, pulse, seed0 + 7 + w, wl.t_end, torch, stream, flush, ev)
-            if not args.no_phase_events:
-                chem.chem_set_profiling(ctx, True)  # zero the phase timers after warm-up
             st0 = chem.chem_get_stats(ctx)
             times, ss, g_h2o2, g_oh, g_e = [], 0, [], [], []
             if world > 1:
@@ -387,17 +387,29 @@ def run_gpu_arm(args):
                 tal = chem.chem_tally(ctx, 7, 9)
                 e2e_t.append(time.perf_counter() - t0)
                 e2e_ss += tal["species_steps"]
+            # profiled trajectories: CUDA events around every phase on the library's stream
+            prof_times, prof_ss, stp0, stp1 = [], 0, st1, st1
+            if not args.no_phase_events:
+                chem.chem_set_profiling(ctx, True)  # recaptures with phase events, timers zeroed
+                stp0 = chem.chem_get_stats(ctx)
+                for k in range(args.profiled):
+                    prof_times.append(trajectory(chem, ctx, pulse, seed0 + 100 + k, wl.t_end, torch, stream,
+                                                 flush, ev))
+                    prof_ss += chem.chem_tally(ctx, 7, 9)["species_steps"]
+                stp1 = chem.chem_get_stats(ctx)
         finally:
             chem.chem_destroy(ctx)
         tot = float(np.sum(times))
         per_phase = {}
         for ph in ("diffuse", "sort", "gather", "search", "react", "begin", "release"):
-            ms = st1["phase_ms"][ph]
-            nl = st1["phase_launches"][ph]
+            ms = stp1["phase_ms"][ph]
+            nl = stp1["phase_launches"][ph]
             per_phase[ph] = {"ms_total": ms, "launches": nl}
-        work = {k: st1[k] - st0[k] for k in ("pairs_tested", "pairs_in_cutoff", "pairs_accepted",
-                                             "steps_advanced")}
+        keys = ("pairs_tested", "pairs_in_cutoff", "pairs_accepted", "steps_advanced")
+        work = {k: st1[k] - st0[k] for k in keys}
+        work_prof = {k: stp1[k] - stp0[k] for k in keys}
         results[name] = dict(times=times, ss=ss, tot=tot, G_H2O2=g_h2o2, G_OH=g_oh, G_e=g_e, work=work,
+                             work_prof=work_prof, prof_times=prof_times, prof_ss=prof_ss,
                              launches=st1["kernel_launches"] - st0["kernel_launches"],
                              phases=per_phase, clocks=clk.summary(), e2e_t=e2e_t, e2e_ss=e2e_ss,
                              tuned=tuned,
@@ -423,11 +435,11 @@ def run_gpu_arm(args):
     dom = max(phases, key=lambda p: phases[p]["ms_total"])
     have_phases = phases[dom]["ms_total"] > 0.0
     sb = STATE_BYTES["fp32l"]
-    dom_bytes = PHASE_BYTES[dom](sb) * r["ss"] * (1 if dom != "sort" else 1)
+    dom_bytes = PHASE_BYTES[dom](sb) * r["prof_ss"]
     n_launch = max(1, phases[dom]["launches"])
     if dom == "sort":
         # species-steps per pass launch: every pass moves every species once
-        dom_bytes = PHASE_BYTES["sort"](sb) * r["ss"] * (phases["sort"]["launches"] / max(1, phases["diffuse"]["launches"]))
+        dom_bytes = PHASE_BYTES["sort"](sb) * r["prof_ss"] * (phases["sort"]["launches"] / max(1, phases["diffuse"]["launches"]))
     achieved = dom_bytes / max(1e-12, phases[dom]["ms_total"] * 1e-3) / 1e9
     tuned = list(r["tuned"]) if r["tuned"] is not None else None
 
@@ -451,7 +463,7 @@ def run_gpu_arm(args):
         # against the issue ceiling of the part (one warp instruction per cycle and
         # scheduler: 152 SMs x 4 x 32 lanes x the maximum SM clock).
         ph = res["phases"]["search"]
-        w = res["work"]
+        w = res["work_prof"]
         if ph["ms_total"] <= 0.0 or w["pairs_tested"] <= 0:
             return None
         ops = ALU_OPS_TESTED * w["pairs_tested"] + ALU_OPS_IN_CUTOFF * w["pairs_in_cutoff"]
@@ -473,7 +485,7 @@ def run_gpu_arm(args):
         ph = phases[phase]
         if ph["ms_total"] <= 0.0:
             return None
-        nb = PHASE_BYTES[phase](sb) * r["ss"]
+        nb = PHASE_BYTES[phase](sb) * r["prof_ss"]
         if phase == "sort":
             nb *= phases["sort"]["launches"] / max(1, phases["diffuse"]["launches"])
         ach = nb / (ph["ms_total"] * 1e-3) / 1e9
@@ -490,7 +502,10 @@ def run_gpu_arm(args):
                    "t_end_s": wl.t_end, "sbs_steps_per_trajectory": r["work"]["steps_advanced"] / len(r["times"]),
                    "mode": "FP32-local positions, FP64 clock/probabilities/tallies",
                    "l2": "flushed (256 MiB write) before every timed trajectory",
-                   "phase_events": not args.no_phase_events,
+                   "phase_events": ("none in the timed trajectories; CUDA events around every phase in "
+                                    f"{len(r['prof_times'])} profiled trajectories after them (rooflines, phases_ms)")
+                   if not args.no_phase_events else "off",
+                   "profiled_ms_per_trajectory": (1e3 * float(np.mean(r["prof_times"])) if r["prof_times"] else None),
                    "autotuned": None if r["tuned"] is None else
                    dict(zip(("steps_per_launch", "cells_per_axis_limit", "species_per_item", "launch_mode"), r["tuned"])),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -503,6 +518,7 @@ def run_gpu_arm(args):
         "roofline_diffuse": roofline_of("diffuse") if have_phases else None,
         "search_work_per_trajectory": {k: v / len(r["times"]) for k, v in r["work"].items()},
         "phases_ms": {p: round(v["ms_total"], 3) for p, v in phases.items()},
+        "phases_ms_over": f"{len(r['prof_times'])} profiled trajectories",
         "clocks": r["clocks"],
         "G_per_100eV_fp32l": {"H2O2": float(np.mean(r["G_H2O2"])), "OH": float(np.mean(r["G_OH"])),
                               "e_aq": float(np.mean(r["G_e"]))},
@@ -993,6 +1009,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-phase-events", action="store_true")
+    ap.add_argument("--profiled", type=int, default=3,
+                    help="trajectories with phase events after the timed ones (phase times, rooflines)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--autotune-ms", type=float, default=1500.0)
     ap.add_argument("--tuned", default="",
