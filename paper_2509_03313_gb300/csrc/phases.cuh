@@ -900,6 +900,9 @@ __device__ __forceinline__ bool accept_f64(double d0sq, double d1sq, int r, cons
   return u < bridge_p(sqrt(d0sq), sqrt(d1sq), tb.R[r], tr.ddt[r]);
 }
 
+// Neighbours whose loads one iteration of the per-species walk keeps in flight together.
+constexpr int TPS_UNROLL = 4;
+
 // ---- one thread per home species
 // One thread per home species: each lane takes one home species
 // (warps take 32 consecutive sorted slots by work stealing) and walks its own cell's later
@@ -1115,13 +1118,13 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       // kept in shared memory while the ranges are walked (registers are the walk's)
       sm.km[wib][lane] = kmask;
       sm.cl[wib][lane] = cell;
-      // the walk's home state is per lane and movable: a lane that has finished its own
-      // list takes the second half of another lane's current range (home data and all),
-      // so that lanes with few neighbours do not idle while one lane walks a dense cell
-      uint32_t hs = s, htid = tid_i;
-      int hb = b;
-      float4 hv = vi;
-      double hx = xi, hy = yi, hz = zi;
+      // the lane's home for the walk (ranges are not moved between lanes: on clustered
+      // tracks, taking over half of a busy lane's range cost more issue slots than the
+      // idle lanes it saved; dense cells go to the cell-tile mapping instead)
+      const uint32_t hs = s, htid = tid_i;
+      const int hb = b;
+      const float4 hv = vi;
+      const double hx = xi, hy = yi, hz = zi;
       const T* hrow = rc2;
       const Train* htr = &tr;
       while (__any_sync(0xffffffffu, sm.km[wib][lane] != 0ull)) {
@@ -1159,7 +1162,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       }
       sm.km[wib][lane] = kmask;
       }
-      // walk the ranges as one flattened list, four neighbours per iteration whose loads
+      // walk the ranges as one flattened list, TPS_UNROLL neighbours per iteration whose loads
       // are in flight together; lanes of one cell stay in step (broadcast loads)
       int ri = 0;
       uint32_t j = 0, je = 0;
@@ -1172,56 +1175,11 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       };
       if (nr > 0) open(0);
       while (__any_sync(0xffffffffu, ri < nr)) {
-        // a lane with cells still to collect keeps its own home
-        const uint32_t idle = __ballot_sync(0xffffffffu, ri >= nr && sm.km[wib][lane] == 0ull);
-        if (idle != 0u) {
-          const uint32_t rem = (ri < nr) ? je - j : 0u;
-          const uint32_t donors = __ballot_sync(0xffffffffu, rem >= 4u);
-          if (donors != 0u) {
-            const int n_pairs = min(__popc(idle), __popc(donors));
-            const bool take = ((idle >> lane) & 1u) && __popc(idle & lanemask_lt) < n_pairs;
-            const bool give = ((donors >> lane) & 1u) && __popc(donors & lanemask_lt) < n_pairs;
-            int src = lane;
-            if (take) {  // the k-th idle lane borrows from the k-th donor
-              src = static_cast<int>(__fns(donors, 0u, __popc(idle & lanemask_lt) + 1));
-            }
-            const uint32_t mid = j + rem / 2u;
-            const uint32_t s2 = __shfl_sync(0xffffffffu, hs, src);
-            const uint32_t t2 = __shfl_sync(0xffffffffu, htid, src);
-            const int b2 = __shfl_sync(0xffffffffu, hb, src);
-            const uint32_t j2 = __shfl_sync(0xffffffffu, mid, src);
-            const uint32_t e2 = __shfl_sync(0xffffffffu, je, src);
-            const unsigned long long row2 =
-                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(hrow), src);
-            const float4 v2 =
-                make_float4(__shfl_sync(0xffffffffu, hv.x, src), __shfl_sync(0xffffffffu, hv.y, src),
-                            __shfl_sync(0xffffffffu, hv.z, src), __shfl_sync(0xffffffffu, hv.w, src));
-            const float cx2 = __shfl_sync(0xffffffffu, cx, src);
-            const float cy2 = __shfl_sync(0xffffffffu, cy, src);
-            const float cz2 = __shfl_sync(0xffffffffu, cz, src);
-            double x2 = 0, y2 = 0, z2 = 0;
-            if constexpr (!F32L) {
-              x2 = __shfl_sync(0xffffffffu, hx, src);
-              y2 = __shfl_sync(0xffffffffu, hy, src);
-              z2 = __shfl_sync(0xffffffffu, hz, src);
-            }
-            if (give) je = mid;  // the donor keeps the first half
-            if (take) {
-              hs = s2; htid = t2; hb = b2;
-              hrow = reinterpret_cast<const T*>(row2);
-              htr = &d.trains[b2];
-              j = j2; je = e2;
-              ri = 0; nr = 1;  // one borrowed range; no further range is opened
-              hv = v2; cx = cx2; cy = cy2; cz = cz2;
-              if constexpr (!F32L) { hx = x2; hy = y2; hz = z2; }
-            }
-          }
-        }
-        uint32_t ju[4];
-        bool vu[4];
-        float cxu[4], cyu[4], czu[4];
+        uint32_t ju[TPS_UNROLL];
+        bool vu[TPS_UNROLL];
+        float cxu[TPS_UNROLL], cyu[TPS_UNROLL], czu[TPS_UNROLL];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < TPS_UNROLL; ++u) {
           vu[u] = ri < nr;
           ju[u] = j;
           cxu[u] = cx; cyu[u] = cy; czu[u] = cz;
@@ -1229,10 +1187,10 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             if (++ri < nr) open(ri);
           }
         }
-        float4 vj[4];
-        uint32_t tj[4];
+        float4 vj[TPS_UNROLL];
+        uint32_t tj[TPS_UNROLL];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < TPS_UNROLL; ++u) {
           vj[u] = make_float4(0.f, 0.f, 0.f, 0.f);
           tj[u] = 0u;
           if (vu[u]) {
@@ -1268,10 +1226,10 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           auto sep = [&](int u, float& fx, float& fy, float& fz) {
             return sep_f32(cxu[u], cyu[u], czu[u], htr->hf, vj[u], hv, fx, fy, fz);
           };
-          bool pass[4];
+          bool pass[TPS_UNROLL];
           bool any = false;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < TPS_UNROLL; ++u) {
             float fx, fy, fz;
             const float rc2u = hrow[__float_as_uint(vj[u].w) & 7u];  // -1 when the types do not react
             pass[u] = vu[u] && sep(u, fx, fy, fz) < rc2u;
@@ -1281,7 +1239,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           }
           if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < TPS_UNROLL; ++u) {
               float fx = 0.f, fy = 0.f, fz = 0.f, f2 = 0.f;
               if (pass[u]) f2 = sep(u, fx, fy, fz);
               push(pass[u], ju[u], fx, fy, fz, f2, 0.0, 0.0, 0.0, 0.0);
@@ -1289,7 +1247,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           }
         } else {
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < TPS_UNROLL; ++u) {
             const uint32_t jj = ju[u];
             bool pass = false;
             double rx1 = 0, ry1 = 0, rz1 = 0, d1sq = 0;
