@@ -145,24 +145,44 @@ __device__ __forceinline__ void set_pair_constants(Train& tr, const Tables& tb, 
 }
 
 // ======================================================================== begin
-// One CTA. Per train: release count, clock step, free-jump decision, hash grid and
-// cutoffs of this step; then the slot offsets of the releases and the step counters.
 struct BeginSmem {
+  Tables tb;                              // the reaction tables, read once per step
   uint32_t rel[MAX_TRAINS];
   double dt[MAX_TRAINS];
   unsigned long long rcmax_bits[MAX_TRAINS];
+  float hf[MAX_TRAINS];                   // this step's cell side
+  int cb0;                                // train 0: key bits per axis of its cells
+  uint32_t base0;                         // train 0: first global cell
   uint32_t any;
 };
 
 // One CTA. (1) per train: release count, clock step and free-jump decision; (2) per
 // (train, reaction) cutoff and bridge constants and per (train, type) step sigma, spread
 // over the threads because FP64 square roots and divisions are long on this part;
-// (3) per train: hash grid of the step; (4) slot offsets of the releases and counters.
+// (3) per train: hash grid of the step; (4) per (train, type pair) cutoff tables; (5) slot
+// offsets of the releases and the step counters. The step is one short chain of
+// dependent loads: the tables, the status and the global counters are read together at
+// the start, and later stages read what earlier ones wrote from shared memory.
 static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
-  const int st = status_of(d);
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) sb.any = 0;
-  const Tables& tb = *d.tables;
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(d.tables);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sb.tb);
+    for (int i = tid; i < static_cast<int>(sizeof(Tables) / 4); i += nt) dst[i] = src[i];
+  }
+  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&d.g->hist[0][0])[i] = 0u;
+  const int st = status_of(d);
+  // the counters thread 0 updates below, read with the tables
+  Global* g = d.g;
+  uint32_t g_total = 0, g_live = 0, g_adaptive = 0, g_home = 0, g_epoch = 0, g_cells = 0;
+  unsigned long long g_incut = 0, g_mark = 0;
+  if (tid == 0) {
+    g_total = g->n_total; g_live = g->n_live; g_adaptive = g->search_adaptive; g_home = g->item_home;
+    g_epoch = g->epoch; g_cells = g->cells_steps; g_incut = g->pairs_in_cutoff; g_mark = g->incut_mark;
+    sb.any = 0;
+  }
+  __syncthreads();
+  const Tables& tb = sb.tb;
   for (uint32_t b = tid; b < d.n_trains; b += nt) {
     Train& tr = d.trains[b];
     // independent loads first: the per-train work below is one short dependency chain
@@ -266,19 +286,13 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     }
   }
   __syncthreads();
-  // the same cutoffs per type pair (the pair search's lookup table)
-  for (uint32_t w = tid; w < d.n_trains * (MAXT * MAXT); w += nt) {
-    const uint32_t b = w / (MAXT * MAXT);
-    const int q = static_cast<int>(w % (MAXT * MAXT));
-    if (sb.dt[b] <= 0.0) continue;
-    Train& tr = d.trains[b];
-    const int r = tb.pair_rxn[q / MAXT][q % MAXT];
-    tr.rc2_tt[q] = r >= 0 ? tr.rc2[r] : -1.0;
-    tr.rc2f_tt[q] = r >= 0 ? tr.rc2f[r] : -1.f;
-  }
   for (uint32_t b = tid; b < d.n_trains; b += nt) {
-    if (sb.dt[b] <= 0.0) continue;
     Train& tr = d.trains[b];
+    if (b == 0) {  // the removed species' key below needs train 0's grid, idle or not
+      sb.cb0 = tr.cb;
+      sb.base0 = tr.cell_base;
+    }
+    if (sb.dt[b] <= 0.0) continue;
     const double L = tr.L, inv_L = tr.inv_L;
     const int n_max = min(tr.n_max, (1 << tr.cb_alloc) - 1), fj = tr.free_jump;
     int n_ref = tr.n_ref;
@@ -330,23 +344,29 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     tr.inv_h = inv_h;
     tr.hf = static_cast<float>(h);
     tr.inv_hf = static_cast<float>(inv_h);
+    sb.hf[b] = static_cast<float>(h);
+    if (b == 0) sb.cb0 = axis_bits(n);
   }
   __syncthreads();
-  // FP32 cutoffs widened past any error of FP32 cell offsets (a few 1e-7 of a cell per
-  // component): a pair the FP32 test rejects is outside the FP64 cutoff
+  // per type pair (the pair search's lookup tables): the squared cutoff, in FP64 and
+  // FP32, and the FP32 one widened past any error of FP32 cell offsets (a few 1e-7 of a
+  // cell per component), so that a pair the FP32 test rejects is outside the FP64 cutoff
   for (uint32_t w = tid; w < d.n_trains * (MAXT * MAXT); w += nt) {
     const uint32_t b = w / (MAXT * MAXT);
     const int q = static_cast<int>(w % (MAXT * MAXT));
     if (sb.dt[b] <= 0.0) continue;
     Train& tr = d.trains[b];
-    const float rc = tr.rc2f_tt[q] >= 0.f ? sqrtf(tr.rc2f_tt[q]) : -1.f;
-    const float rw = rc * 1.00001f + 2e-6f * tr.hf;
+    const int r = tb.pair_rxn[q / MAXT][q % MAXT];
+    const double c2 = r >= 0 ? tr.rc2[r] : -1.0;
+    const float c2f = r >= 0 ? static_cast<float>(c2) : -1.f;
+    tr.rc2_tt[q] = c2;
+    tr.rc2f_tt[q] = c2f;
+    const float rc = c2f >= 0.f ? sqrtf(c2f) : -1.f;
+    const float rw = rc * 1.00001f + 2e-6f * sb.hf[b];
     tr.rc2w_tt[q] = rc >= 0.f ? rw * rw * 1.00001f : -1.f;
   }
-
   if (tid == 0) {
-    Global* g = d.g;
-    uint32_t off = g->n_total;
+    uint32_t off = g_total;
     const uint32_t before = off;
     unsigned long long total = off;
     for (uint32_t b = 0; b < d.n_trains; ++b) {
@@ -369,34 +389,31 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     g->n_events = 0;
     g->n_products = 0;
     g->n_dead = 0;
-    g->epoch += 1;
+    g->epoch = g_epoch + 1u;
     g->any_active = sb.any;
     // Search mapping of this step. Cell tiles amortise the neighbour-cell lookups over
     // the homes of a cell and test a pair only when the types react; one thread per
     // species has the shorter per-item latency chain. Adaptive: cell tiles when the last
     // step found more than 3 pairs inside the cutoffs per live species (the measured
     // crossover on track workloads); results do not depend on the mapping.
-    if (g->search_adaptive) {
-      const unsigned long long inc = g->pairs_in_cutoff - g->incut_mark;
-      g->search_cells_now = inc > 3ull * static_cast<unsigned long long>(g->n_live) ? 1u : 0u;
+    uint32_t cells_now;
+    if (g_adaptive) {
+      const unsigned long long inc = g_incut - g_mark;
+      cells_now = inc > 3ull * static_cast<unsigned long long>(g_live) ? 1u : 0u;
     } else {
-      g->search_cells_now = g->item_home != 0u ? 1u : 0u;
+      cells_now = g_home != 0u ? 1u : 0u;
     }
-    g->incut_mark = g->pairs_in_cutoff;
-    if (g->search_cells_now && sb.any) g->cells_steps += 1;
-  }
-  __syncthreads();  // the grids above are written
-  if (tid == 0) {
+    g->search_cells_now = cells_now;
+    g->incut_mark = g_incut;
+    if (cells_now && sb.any) g->cells_steps = g_cells + 1u;
     // removed species sort after every live one: with one train the all-ones cell index
     // of the grid's width (this step's grid, or the last one when the train is idle; no
     // cell has it, and it stays within the bits the launched passes sort), so the top
     // key bits stay zero and their radix pass is skipped; with several trains, past the
     // last train's cells
-    const Train& t0 = d.trains[0];
-    const int kb = min(3 * t0.cb, 8 * d.passes);
-    d.g->sentinel_step = d.n_trains == 1 ? t0.cell_base + (kb >= 32 ? 0xFFFFFFFFu : (1u << kb) - 1u) : d.sentinel;
+    const int kb = min(3 * sb.cb0, 8 * d.passes);
+    g->sentinel_step = d.n_trains == 1 ? sb.base0 + (kb >= 32 ? 0xFFFFFFFFu : (1u << kb) - 1u) : d.sentinel;
   }
-  for (int i = tid; i < MAX_PASSES * RADIX; i += nt) (&d.g->hist[0][0])[i] = 0u;
   __syncthreads();
 }
 
@@ -1127,6 +1144,24 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       const double hx = xi, hy = yi, hz = zi;
       const T* hrow = rc2;
       const Train* htr = &tr;
+      // enqueue the pairs inside the cutoff (queue pushes are warp-wide)
+      auto push = [&](bool pass, uint32_t jj, float fx, float fy, float fz, float f2, double rx1, double ry1,
+                      double rz1, double d1sq) {
+        const uint32_t bal = __ballot_sync(0xffffffffu, pass);
+        if (bal) {
+          const uint32_t base = q.n;
+          if (pass) {
+            const uint32_t pos = base + __popc(bal & lanemask_lt);
+            q.si[pos] = hs; q.j[pos] = jj; q.tid_i[pos] = htid; q.b[pos] = static_cast<uint32_t>(hb);
+            if constexpr (F32L) { q.fx[pos] = fx; q.fy[pos] = fy; q.fz[pos] = fz; q.f2[pos] = f2; }
+            else { q.rx[pos] = rx1; q.ry[pos] = ry1; q.rz[pos] = rz1; q.d2[pos] = d1sq; }
+          }
+          __syncwarp();
+          if (lane == 0) q.n = base + __popc(bal);
+          __syncwarp();
+          if (q.n > static_cast<uint32_t>(TpsQueue<F32L>::CAP) - 32u) tps_flush<F32L>(d, tb, q, vf, lane);
+        }
+      };
       while (__any_sync(0xffffffffu, sm.km[wib][lane] != 0ull)) {
       int nr = 0;
       // look up only the cells within reach (warp-uniform loop over each lane's set bits)
@@ -1202,24 +1237,6 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             }
           }
         }
-        // enqueue the pairs inside the cutoff (queue pushes are warp-wide)
-        auto push = [&](bool pass, uint32_t jj, float fx, float fy, float fz, float f2, double rx1, double ry1,
-                        double rz1, double d1sq) {
-          const uint32_t bal = __ballot_sync(0xffffffffu, pass);
-          if (bal) {
-            const uint32_t base = q.n;
-            if (pass) {
-              const uint32_t pos = base + __popc(bal & lanemask_lt);
-              q.si[pos] = hs; q.j[pos] = jj; q.tid_i[pos] = htid; q.b[pos] = static_cast<uint32_t>(hb);
-              if constexpr (F32L) { q.fx[pos] = fx; q.fy[pos] = fy; q.fz[pos] = fz; q.f2[pos] = f2; }
-              else { q.rx[pos] = rx1; q.ry[pos] = ry1; q.rz[pos] = rz1; q.d2[pos] = d1sq; }
-            }
-            __syncwarp();
-            if (lane == 0) q.n = base + __popc(bal);
-            __syncwarp();
-            if (q.n > static_cast<uint32_t>(TpsQueue<F32L>::CAP) - 32u) tps_flush<F32L>(d, tb, q, vf, lane);
-          }
-        };
         if constexpr (F32L) {
           // the cutoff test for the four neighbours first; the separation is formed again,
           // identically, for the rare pairs inside the cutoff
