@@ -425,6 +425,8 @@ def run_gpu_arm(args):
     vres = None if args.no_volume else run_volume_scaling(args, chem, W, torch, stream, alloc, rank, world, dev)
     lres = run_large(args, chem, W, torch, stream, alloc) if not args.no_large and rank == 0 else None
     mres = run_multi_pulse(args, chem, W, torch, stream, alloc) if not args.no_multi_pulse and rank == 0 else None
+    rres = (run_replicas(args, chem, W, torch, stream, alloc, flush, r["tuned"])
+            if args.replicas > 1 and rank == 0 else None)
     xres = (run_beyond_l2(args, chem, W, torch, stream, alloc, flush)
             if not args.no_beyond_l2 and rank == 0 else None)
     if rank != 0:
@@ -549,6 +551,10 @@ def run_gpu_arm(args):
         line["large"] = lres
     if mres is not None:
         line["multi_pulse"] = mres
+    if rres is not None:
+        line["batched_replicas"] = rres
+        if "fp64" in line:
+            line["speedup_batched_replicas_over_plain_fp64"] = rres["value"] / line["fp64"]["value"]
     if xres is not None:
         line["beyond_l2"] = xres
     line["cpu_baseline"] = cpu
@@ -878,6 +884,55 @@ def timed_trajectories(chem, torch, wl, precision, seeds, n_warm, stream, alloc,
     return ss, tot, phases, work, g
 
 
+def run_replicas(args, chem, W, torch, stream, alloc, flush, tuned):
+    """The benchmark workload as R independent trajectories (seeds differ) advanced together
+    in one batched context: one hash and one graph for all R pulses, the grid limit and
+    launch form of the single-train run. Species-steps/s over whole trajectories, L2
+    flushed before each."""
+    wl = W.single_pulse_tracks(10_000, n_species=args.species, n_tracks=args.tracks)
+    pulse = wl.pulses[0]
+    s = wl.schedule
+    R = args.replicas
+    cap = int(pulse.n * 1.3) + 4096
+    n_lim = tuned[1] if tuned is not None else 255
+    cfgs, keep = [], []
+    for b in range(R):
+        cfg, k = chem.make_config(wl.L, wl.D, wl.reactions, seed=5 + b, train_id=b,
+                                  precision=chem.CHEM_FP32_LOCAL, dt_min=s.dt_min, dt_max=s.dt_max,
+                                  dt_growth=s.dt_growth, capacity_species=cap, capacity_pending=cap,
+                                  capacity_candidates=max(1 << 16, cap // 4), cells_per_axis_max=n_lim,
+                                  stream=stream.cuda_stream, allocator=alloc)
+        cfgs.append(cfg)
+        keep.append(k)
+    ctx = chem.chem_batch_init(cfgs)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    times, ss = [], 0
+    try:
+        chem.chem_set_tuning(ctx, tuned[0] if tuned is not None else 8, n_lim, -1,
+                             tuned[3] if tuned is not None else chem.CHEM_LAUNCH_PHASES)
+        for rep in range(args.replica_reps + 1):
+            chem.chem_batch_reset(ctx, [20_000 + 100 * rep + b for b in range(R)])
+            for b in range(R):
+                chem.chem_batch_inject(ctx, b, pulse.types, pulse.xyz, pulse.t_arrival, pulse.energy_eV)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[0].record(stream)
+            chem.chem_batch_run_until(ctx, [wl.t_end] * R)
+            with torch.cuda.stream(stream):
+                ev[1].record(stream)
+            ev[1].synchronize()
+            if rep == 0:
+                continue  # warm-up repetition
+            times.append(ev[0].elapsed_time(ev[1]) * 1e-3)
+            ss += sum(chem.chem_batch_tally(ctx, b, 7, 9)["species_steps"] for b in range(R))
+    finally:
+        chem.chem_destroy(ctx)
+    return {"value": ss / sum(times), "unit": UNIT, "replicas": R, "species": int(R * pulse.n),
+            "ms_per_rep": 1e3 * float(np.mean(times)), "reps": len(times),
+            "workload": f"{R} independent trajectories of the benchmark workload (seeds differ) in one "
+                        "batched context, FP32-local, 1 ps -> 1 us"}
+
+
 def run_beyond_l2(args, chem, W, torch, stream, alloc, flush):
     """The benchmark workload at 20x the volume (13.6 um box, same track and species
     density, 2e7 species): state arrays of 320 MB (FP32-local) and 560 MB (FP64), beyond
@@ -1028,6 +1083,9 @@ def main():
     ap.add_argument("--no-large-fp64", action="store_true", help="run it in FP32-local mode only")
     ap.add_argument("--no-multi-pulse", action="store_true", help="skip the 10-pulse build-up (0.1 ms apart)")
     ap.add_argument("--no-beyond-l2", action="store_true", help="skip the 2e7-species workload")
+    ap.add_argument("--replicas", type=int, default=4,
+                    help="trajectories of the benchmark workload batched in one context (1: skip the leg)")
+    ap.add_argument("--replica-reps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference_arm(args)
