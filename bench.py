@@ -446,8 +446,10 @@ def run_gpu_arm(args):
     tuned = list(r["tuned"]) if r["tuned"] is not None else None
 
     def traffic_of(phase):
-        # DRAM bytes per launch from the committed capture of the same tuning and sources
-        kern = {"search": "k_search_tps", "diffuse": "k_diffuse"}.get(phase)
+        # DRAM bytes per phase launch from the committed capture of the same tuning and
+        # sources; the search phase launches both search kernels every step
+        kerns = {"search": ("k_search_tps", "k_search"), "diffuse": ("k_diffuse",),
+                 "sort": ("k_sort_pass",), "gather": ("k_gather",)}.get(phase)
         try:
             with open(TRAFFIC_FILE) as fh:
                 rec_tuning = json.load(fh).get("tuning")
@@ -456,7 +458,10 @@ def run_gpu_arm(args):
         # same search mapping and launch form (the hash limit the autotuner picks varies
         # from run to run and moves the traffic little)
         same = rec_tuning is not None and tuned is not None and rec_tuning[2:] == tuned[2:]
-        return recorded_traffic(kern) if kern and same else None
+        if not kerns or not same:
+            return None
+        vals = [recorded_traffic(k) for k in kerns]
+        return None if any(v is None for v in vals) else sum(vals)
 
     def search_alu_roofline(res):
         # The search is bound by instruction issue, not by memory: its algorithmic work is
