@@ -326,7 +326,12 @@ void init_train_dynamic(Train& t, const chem_config& c, int n_max) {
   t.key1 = static_cast<uint32_t>(c.seed >> 32) ^ c.train_id;
 }
 
-int kernels_per_step(const chem_ctx* ctx) { return ctx->persistent ? 0 : 7 + ctx->d.passes; }
+// Kernels of one captured step: diffusion, the sort passes, gather, the search (one or
+// both mappings), fast matching, the one-CTA reaction kernel, products, and the end (or
+// end-and-next-begin) kernel.
+int kernels_per_step(const chem_ctx* ctx) {
+  return ctx->persistent ? 0 : 6 + ctx->d.passes + (ctx->lc.search_tps == 2 ? 2 : 1);
+}
 
 // Radix passes for the captured graph (see chem_ctx::passes_alloc).
 int sort_passes(const chem_ctx* ctx) {

@@ -126,3 +126,31 @@ def test_profiling_on_then_off_mid_run_leaves_fp64_results_unchanged():
     finally:
         chem.chem_destroy(ctx)
     assert_fp64_parity(g, oracle_run(wl, 53, t_stops=[40e-9, 90e-9]), wl.L)
+
+
+def test_sort_passes_follow_the_grid_limit():
+    # A single-train context sorts only the key bits its runtime grid limit needs: at most
+    # 15 cells per axis -> 12-bit keys, two radix passes; 200 -> 24 bits, three. Ten steps
+    # at each limit differ by ten sort launches, and the results stay the reference's.
+    wl = W.uniform_2000(seed=54, L=200.0, n_steps=30)
+    ctx, keep = _ctx(wl, 54, chem.CHEM_FP64)
+    try:
+        p = wl.pulses[0]
+        chem.chem_inject_pulse(ctx, p.types, p.xyz, p.t_arrival, p.energy_eV)
+        launches = []
+        for lim, t in ((15, 10e-9), (200, 20e-9), (15, wl.t_end)):
+            chem.chem_set_tuning(ctx, 1, lim, -1, chem.CHEM_LAUNCH_PHASES)
+            before = chem.chem_get_stats(ctx)["kernel_launches"]
+            chem.chem_run_until(ctx, t)
+            launches.append(chem.chem_get_stats(ctx)["kernel_launches"] - before)
+        ids, types, xyz = chem.chem_get_state(ctx)
+        o = np.argsort(ids)
+        g = {"tally": chem.chem_tally(ctx, 7, 9), "events": chem.chem_get_events(ctx),
+             "steps": chem.chem_get_step_log(ctx),
+             "state": (ids[o].astype(np.int64), types[o].astype(np.int64), xyz[o])}
+    finally:
+        chem.chem_destroy(ctx)
+    # the third run may keep three passes: its species were last sorted on the finer grid
+    assert launches[1] - launches[0] == 10, launches
+    assert launches[2] in (launches[0], launches[1]), launches
+    assert_fp64_parity(g, oracle_run(wl, 54, t_stops=[10e-9, 20e-9]), wl.L)
