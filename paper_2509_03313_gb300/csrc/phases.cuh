@@ -720,41 +720,86 @@ __device__ void phase_gather(const Dev& d) {
   if (status_of(d)) return;
   const uint32_t* kf = d.g->sort_parity ? d.keys1 : d.keys0;
   const uint32_t* vf = d.g->sort_any ? (d.g->sort_parity ? d.vals1 : d.vals0) : nullptr;
-  const uint32_t n_live = d.g->n_total - d.g->n_dead;
+  const uint32_t n_total = d.g->n_total;
+  const uint32_t n_live = n_total - d.g->n_dead;
   const uint32_t epoch = d.g->epoch;
+  const uint32_t sentinel = d.g->sentinel_step;
   const uint32_t item_home = d.g->item_home;
+  const bool items_now = item_home != 0 && d.g->search_cells_now;
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_live; s += stride) {
-    const uint32_t key = kf[s];
-    const uint32_t i = vf ? vf[s] : s;
-    if (key >= d.g->sentinel_step || i >= d.g->n_total) {  // only after a timed-out sort
-      raise_status(d.g, CHEM_ETIMEOUT);
-      continue;
+  // GATHER_BATCH slots per thread and iteration, their loads in flight together: the
+  // permutation and neighbouring keys first, then the gathered state
+  for (uint32_t s0 = blockIdx.x * blockDim.x + threadIdx.x; s0 < n_live; s0 += stride * GATHER_BATCH) {
+    uint32_t key[GATHER_BATCH], idx[GATHER_BATCH], prv[GATHER_BATCH], nxt[GATHER_BATCH];
+    bool ok[GATHER_BATCH];
+#pragma unroll
+    for (int g = 0; g < GATHER_BATCH; ++g) {
+      const uint32_t s = s0 + static_cast<uint32_t>(g) * stride;
+      ok[g] = s < n_live;
+      key[g] = 0u; idx[g] = 0u; prv[g] = 0u; nxt[g] = 0u;
+      if (ok[g]) {
+        key[g] = kf[s];
+        idx[g] = vf ? vf[s] : s;
+        prv[g] = s > 0 ? kf[s - 1] : 0u;
+        nxt[g] = s + 1 < n_live ? kf[s + 1] : 0u;
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < GATHER_BATCH; ++g) {
+      if (ok[g] && (key[g] >= sentinel || idx[g] >= n_total)) {  // only after a timed-out sort
+        raise_status(d.g, CHEM_ETIMEOUT);
+        ok[g] = false;
+      }
     }
     if (F32L) {
-      d.s4[s] = d.t4[i];
-      if (d.sd4) d.sd4[s] = d.td4[i];
+      float4 a[GATHER_BATCH], b[GATHER_BATCH];
+#pragma unroll
+      for (int g = 0; g < GATHER_BATCH; ++g) {
+        if (ok[g]) {
+          a[g] = d.t4[idx[g]];
+          if (d.sd4) b[g] = d.td4[idx[g]];
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < GATHER_BATCH; ++g) {
+        if (ok[g]) {
+          const uint32_t s = s0 + static_cast<uint32_t>(g) * stride;
+          d.s4[s] = a[g];
+          if (d.sd4) d.sd4[s] = b[g];
+        }
+      }
     } else {
-      d.sx[s] = d.tx[i]; d.sy[s] = d.ty[i]; d.sz[s] = d.tz[i]; d.stid[s] = d.ttid[i];
-      if (d.s4) d.s4[s] = d.t4[i];
+#pragma unroll
+      for (int g = 0; g < GATHER_BATCH; ++g) {
+        if (ok[g]) {
+          const uint32_t s = s0 + static_cast<uint32_t>(g) * stride, i = idx[g];
+          d.sx[s] = d.tx[i]; d.sy[s] = d.ty[i]; d.sz[s] = d.tz[i]; d.stid[s] = d.ttid[i];
+          if (d.s4) d.s4[s] = d.t4[i];
+        }
+      }
     }
-    d.cell_sorted[s] = key;
-    int* ci = reinterpret_cast<int*>(&d.cell_info[key]);
-    const bool first = (s == 0 || kf[s - 1] != key);
-    if (first) {
-      ci[0] = static_cast<int>(s);
-      ci[2] = static_cast<int>(epoch);
-      atomicOr(&d.occ[key >> 5], 1u << (key & 31u));
-    }
-    if (s + 1 == n_live || kf[s + 1] != key) ci[1] = static_cast<int>(s + 1);
-    // pair-search work item: a cell's first slot and every item_home-th slot (none when
-    // the search runs one thread per species)
-    if (item_home != 0 && d.g->search_cells_now && (first || (s % item_home) == 0)) {
-      const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, key);
-      if (d.trains[b].active && !d.trains[b].free_jump) {
-        const uint32_t it = atomicAdd(&d.g->n_items, 1u);
-        if (it < d.cap_items) d.items[it] = make_uint2(s, key);
-        else raise_status(d.g, CHEM_ECAPACITY);
+#pragma unroll
+    for (int g = 0; g < GATHER_BATCH; ++g) {
+      if (!ok[g]) continue;
+      const uint32_t s = s0 + static_cast<uint32_t>(g) * stride, k = key[g];
+      d.cell_sorted[s] = k;
+      int* ci = reinterpret_cast<int*>(&d.cell_info[k]);
+      const bool first = (s == 0 || prv[g] != k);
+      if (first) {
+        ci[0] = static_cast<int>(s);
+        ci[2] = static_cast<int>(epoch);
+        atomicOr(&d.occ[k >> 5], 1u << (k & 31u));
+      }
+      if (s + 1 == n_live || nxt[g] != k) ci[1] = static_cast<int>(s + 1);
+      // pair-search work item: a cell's first slot and every item_home-th slot (none when
+      // the search runs one thread per species)
+      if (items_now && (first || (s % item_home) == 0)) {
+        const int b = (d.n_trains == 1) ? 0 : train_of_cell(d.trains, d.n_trains, k);
+        if (d.trains[b].active && !d.trains[b].free_jump) {
+          const uint32_t it = atomicAdd(&d.g->n_items, 1u);
+          if (it < d.cap_items) d.items[it] = make_uint2(s, k);
+          else raise_status(d.g, CHEM_ECAPACITY);
+        }
       }
     }
   }

@@ -32,6 +32,7 @@ constexpr int MAX_PASSES = 4;
 constexpr int SORT_THREADS = 512;    // threads of the per-pass sort kernel
 constexpr int PERSIST_THREADS = 256; // threads of the persistent step kernel
 constexpr int SORT_ITEMS = 15;
+constexpr int GATHER_BATCH = 4;   // slots per thread and iteration of the gather
 // the smallest sort tile (persistent kernel): sizes the look-back buffer
 constexpr int SORT_TILE_MIN = PERSIST_THREADS * SORT_ITEMS;
 constexpr int REACT_THREADS = 1024;
