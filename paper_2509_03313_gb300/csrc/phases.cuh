@@ -482,8 +482,32 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
   const uint32_t stride = gridDim.x * blockDim.x;
   const uint32_t n_iter = ok ? (n_total + stride - 1) / stride : 0u;
   uint32_t n_dead_local = 0;
+  // the next iteration's state of a stepped slot is loaded while this one is worked on
+  // (released slots read their own sources below)
+  uint32_t pf_cell = 0, pf_prev = 0, pf_tid = 0;
+  bool pf_dead = false;
+  float4 pf_v = make_float4(0.f, 0.f, 0.f, 0.f);
+  double pf_x = 0, pf_y = 0, pf_z = 0;
+  auto prefetch = [&](uint32_t s) {
+    if (s < rel_base) {
+      pf_cell = d.cell_sorted[s];
+      pf_prev = s > 0 ? d.cell_sorted[s - 1] : 0u;
+      pf_dead = d.dead[s] != 0;
+      if (F32L) {
+        pf_v = d.s4[s];
+      } else {
+        pf_x = d.sx[s]; pf_y = d.sy[s]; pf_z = d.sz[s]; pf_tid = d.stid[s];
+      }
+    }
+  };
+  if (n_iter > 0) prefetch(blockIdx.x * blockDim.x + threadIdx.x);
   for (uint32_t it = 0; it < n_iter; ++it) {
     const uint32_t s = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t c_cell = pf_cell, c_prev = pf_prev, c_tid = pf_tid;
+    const bool c_dead = pf_dead;
+    const float4 c_v = pf_v;
+    const double c_x = pf_x, c_y = pf_y, c_z = pf_z;
+    if (it + 1 < n_iter) prefetch(s + stride);
     const bool valid = s < n_total;
     const bool rel = valid && s >= rel_base;
     uint32_t rel_b = 0, rel_type = 0;
@@ -547,18 +571,18 @@ __device__ void phase_diffuse(const Dev& d, uint32_t (*hist)[RADIX]) {
         d.dead[s] = 0;
         }  // unparked or new
       } else {
-        cell = d.cell_sorted[s];
+        cell = c_cell;
         // the occupancy bitmap is rebuilt by this step's gather: clear the words holding
         // the last step's cells (the first slot of each run of equal cells clears its
         // word; the last step's search has finished reading them)
-        if (s == 0 || d.cell_sorted[s - 1] != cell) d.occ[cell >> 5] = 0u;
-        dead = d.dead[s] != 0;
+        if (s == 0 || c_prev != cell) d.occ[cell >> 5] = 0u;
+        dead = c_dead;
         if (dead) {
           d.dead[s] = 0;
         } else if (F32L) {
-          v = d.s4[s];
+          v = c_v;
         } else {
-          px = d.sx[s]; py = d.sy[s]; pz = d.sz[s]; tid = d.stid[s];
+          px = c_x; py = c_y; pz = c_z; tid = c_tid;
         }
       }
       if (dead) {
