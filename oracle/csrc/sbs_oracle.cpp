@@ -437,13 +437,13 @@ void* oracle_new(int32_t n_types, const double* D, int32_t n_rxn, const OracleRe
 void oracle_free(void* h) { delete static_cast<Oracle*>(h); }
 
 // Queue species, merged stably by arrival after those already pending. Returns 0, or -1
-// (nothing queued) for an arrival before the current time, a bad type or a position
-// outside [-L/2, L/2).
+// (nothing queued) for an arrival before the current time or not a number, a bad type or
+// a position outside [-L/2, L/2).
 int32_t oracle_inject(void* h, int64_t n, const int32_t* type, const double* xyz, const double* t_arr,
                       double energy_eV) {
   Oracle& o = *static_cast<Oracle*>(h);
   for (int64_t i = 0; i < n; ++i) {
-    if (t_arr[i] < o.t || type[i] < 0 || type[i] >= o.n_types) return -1;
+    if (!(t_arr[i] >= o.t) || type[i] < 0 || type[i] >= o.n_types) return -1;  // NaN too
     for (int a = 0; a < 3; ++a)
       if (!(xyz[3 * i + a] >= -0.5 * o.L && xyz[3 * i + a] < 0.5 * o.L)) return -1;
   }

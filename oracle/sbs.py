@@ -262,12 +262,12 @@ class SBSOracle:
         types = np.asarray(types, dtype=np.int64)
         xyz = np.asarray(xyz, dtype=np.float64).reshape(-1, 3)
         t_arrival = np.asarray(t_arrival, dtype=np.float64)
-        if np.any(t_arrival < self.t):
-            raise ValueError("arrival before the current time")
+        if np.any(~(t_arrival >= self.t)):
+            raise ValueError("arrival before the current time or not a number")
         if np.any((types < 0) | (types >= self.n_types)):
             raise ValueError("bad species type")
-        if np.any((xyz < -0.5 * self.L) | (xyz >= 0.5 * self.L)):
-            raise ValueError("position outside the box")
+        if np.any(~((xyz >= -0.5 * self.L) & (xyz < 0.5 * self.L))):
+            raise ValueError("position outside the box or not a number")
         self.E_dep += float(energy_eV)
         all_t = np.concatenate([self.p_t, t_arrival])
         order = np.argsort(all_t, kind="stable")

@@ -93,20 +93,26 @@ def test_building_blocks_agree_elementwise():
         assert cxx.reaction_radius(k, D) == sbs.reaction_radius(k, D)
 
 
-def test_bad_inputs_raise():
-    o = cxx.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, 100.0, seed=1)
+@pytest.mark.parametrize("ref", ["numpy", "cxx"])
+def test_bad_inputs_raise(ref):
+    mod = cxx if ref == "cxx" else sbs
+    o = mod.SBSOracle(W.D_NM2_S, W.WATER_REACTIONS, 100.0, seed=1)
     with pytest.raises(ValueError):
         o.inject([7], [[0.0, 0.0, 0.0]], [0.0])           # no type 7
     with pytest.raises(ValueError):
         o.inject([0], [[50.0, 0.0, 0.0]], [0.0])          # x = L/2 is outside [-L/2, L/2)
+    with pytest.raises(ValueError):
+        o.inject([0], [[0.0, 0.0, 0.0]], [float("nan")])  # arrival not a number
+    with pytest.raises(ValueError):
+        o.inject([0], [[float("nan"), 0.0, 0.0]], [0.0])  # position not a number
     o.run_until(2e-9)
     with pytest.raises(ValueError):
         o.inject([0], [[0.0, 0.0, 0.0]], [1e-9])          # arrival in the past
     assert o.n_types == 7 and o.counts().sum() == 0
     with pytest.raises(ValueError):                       # two reactions for one type pair
-        cxx.SBSOracle([1e9, 1e9], [(0, 1, 1e10, (), 0), (1, 0, 2e10, (), 0)], 100.0, seed=1)
+        mod.SBSOracle([1e9, 1e9], [(0, 1, 1e10, (), 0), (1, 0, 2e10, (), 0)], 100.0, seed=1)
     with pytest.raises(ValueError):                       # R >= L/3
-        cxx.SBSOracle([1e9, 1e9], [(0, 1, 1e13, (), 0)], 30.0, seed=1)
+        mod.SBSOracle([1e9, 1e9], [(0, 1, 1e13, (), 0)], 30.0, seed=1)
 
 
 def test_max_steps_stops_early():
