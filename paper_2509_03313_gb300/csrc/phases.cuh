@@ -1266,7 +1266,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       }
       sm.km[wib][lane] = kmask;
       }
-      // walk the ranges as one flattened list, TPS_UNROLL neighbours per iteration whose loads
+      // walk the ranges one after the other, TPS_UNROLL neighbours per iteration whose loads
       // are in flight together; lanes of one cell stay in step (broadcast loads)
       int ri = 0;
       uint32_t j = 0, je = 0;
@@ -1279,17 +1279,20 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       };
       if (nr > 0) open(0);
       while (__any_sync(0xffffffffu, ri < nr)) {
+        // the next TPS_UNROLL neighbours of the lane's current range (one cell offset for
+        // the batch; a range's last batch may be partly empty)
         uint32_t ju[TPS_UNROLL];
         bool vu[TPS_UNROLL];
-        float cxu[TPS_UNROLL], cyu[TPS_UNROLL], czu[TPS_UNROLL];
+        const bool act = ri < nr;
 #pragma unroll
         for (int u = 0; u < TPS_UNROLL; ++u) {
-          vu[u] = ri < nr;
-          ju[u] = j;
-          cxu[u] = cx; cyu[u] = cy; czu[u] = cz;
-          if (vu[u] && ++j == je) {
-            if (++ri < nr) open(ri);
-          }
+          ju[u] = j + static_cast<uint32_t>(u);
+          vu[u] = act && ju[u] < je;
+        }
+        const float bx = cx, by = cy, bz = cz;
+        if (act) {
+          j += TPS_UNROLL;
+          if (j >= je && ++ri < nr) open(ri);
         }
         float4 vj[TPS_UNROLL];
         uint32_t tj[TPS_UNROLL];
@@ -1310,7 +1313,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           // the cutoff test for the four neighbours first; the separation is formed again,
           // identically, for the rare pairs inside the cutoff
           auto sep = [&](int u, float& fx, float& fy, float& fz) {
-            return sep_f32(cxu[u], cyu[u], czu[u], htr->hf, vj[u], hv, fx, fy, fz);
+            return sep_f32(bx, by, bz, htr->hf, vj[u], hv, fx, fy, fz);
           };
           bool pass[TPS_UNROLL];
           bool any = false;
@@ -1343,7 +1346,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
               bool near = cw >= 0.f;
               if (near && pref) {
                 float fx, fy, fz;
-                near = sep_f32(cxu[u], cyu[u], czu[u], htr->hf, vj[u], hv, fx, fy, fz) < cw;
+                near = sep_f32(bx, by, bz, htr->hf, vj[u], hv, fx, fy, fz) < cw;
               }
               if (near) {
                 const double c2 = htr->rc2_tt[tid_type(htid) * MAXT + tjj];
