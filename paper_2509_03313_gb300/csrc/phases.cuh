@@ -1237,30 +1237,48 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
       {
       unsigned long long kmask = sm.km[wib][lane];
       const uint32_t cell = sm.cl[wib][lane];
+      // two cells per iteration, their bitmap words and then their entries loaded together
       while (__any_sync(0xffffffffu, kmask != 0ull && nr < N_FWD)) {
+        int kk[2] = {-1, -1};
         if (kmask != 0ull && nr < N_FWD) {
-          const int k = __ffsll(static_cast<long long>(kmask)) - 1;
+          kk[0] = __ffsll(static_cast<long long>(kmask)) - 1;
           kmask &= kmask - 1ull;
-          if (k == 0) {
+        }
+        if (kmask != 0ull && nr + 1 < N_FWD) {
+          kk[1] = __ffsll(static_cast<long long>(kmask)) - 1;
+          kmask &= kmask - 1ull;
+        }
+        uint32_t nc[2] = {0u, 0u}, word[2] = {0u, 0u};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (kk[q] > 0) {
+            const int k = kk[q], n = tr.n;
+            int ix, iy, iz;
+            cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
+            nc[q] = tr.cell_base + cell_encode(step_cell(ix, c_fwd.x[k], n), step_cell(iy, c_fwd.y[k], n),
+                                               step_cell(iz, c_fwd.z[k], n), tr.cb);
+            word[q] = d.occ[nc[q] >> 5];
+          }
+        }
+        int4 ci[2];
+        bool occ[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          occ[q] = kk[q] > 0 && ((word[q] >> (nc[q] & 31u)) & 1u);
+          ci[q] = occ[q] ? d.cell_info[nc[q]] : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (kk[q] == 0) {
             rs_l[0] = s + 1u;
             re_l[0] = static_cast<uint32_t>(d.cell_info[cell].y);
             rk_l[0] = 0;
             nr = 1;
-          } else {
-            const int n = tr.n;
-            int ix, iy, iz;
-            cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
-            const uint32_t nc = tr.cell_base + cell_encode(step_cell(ix, c_fwd.x[k], n), step_cell(iy, c_fwd.y[k], n),
-                                                           step_cell(iz, c_fwd.z[k], n), tr.cb);
-            if ((d.occ[nc >> 5] >> (nc & 31u)) & 1u) {
-              const int4 ci = d.cell_info[nc];
-              if (static_cast<uint32_t>(ci.z) == epoch && ci.y > ci.x) {
-                rs_l[32 * nr] = static_cast<uint32_t>(ci.x);
-                re_l[32 * nr] = static_cast<uint32_t>(ci.y);
-                rk_l[32 * nr] = static_cast<uint8_t>(k);
-                ++nr;
-              }
-            }
+          } else if (occ[q] && static_cast<uint32_t>(ci[q].z) == epoch && ci[q].y > ci[q].x) {
+            rs_l[32 * nr] = static_cast<uint32_t>(ci[q].x);
+            re_l[32 * nr] = static_cast<uint32_t>(ci[q].y);
+            rk_l[32 * nr] = static_cast<uint8_t>(kk[q]);
+            ++nr;
           }
         }
       }
