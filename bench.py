@@ -821,7 +821,8 @@ def run_volume_scaling(args, chem, W, torch, stream, alloc, rank=0, world=1, dev
     m = np.array([means[L] for L in boxes])
     # species with at least 20 molecules per smallest box (fewer is counting noise)
     big = m.min(axis=0) > 20.0 / (6.02214076e23 * min(boxes) ** 3 * 1e-24)
-    spread = float(((m.max(axis=0) - m.min(axis=0)) / m.mean(axis=0))[big].max()) if big.any() else None
+    mb = m[:, big]
+    spread = float(((mb.max(axis=0) - mb.min(axis=0)) / mb.mean(axis=0)).max()) if big.any() else None
     return {"value": ss_all / wall_all if wall_all > 0 else None, "unit": UNIT, "wall_s": wall_all,
             "boxes_nm": list(boxes), "seeds": list(boxes.values()),
             "conc_1ms_M": {f"{L:g}": [float(v) for v in means[L]] for L in boxes},
