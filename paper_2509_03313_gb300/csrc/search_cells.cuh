@@ -214,15 +214,35 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
           const float g = o > 0 ? static_cast<float>(o) * hf - of : (o < 0 ? of + static_cast<float>(-o - 1) * hf : 0.f);
           return fmaxf(g - eps, 0.f);
         };
-        for (unsigned long long rem = occ_mask & ~1ull; rem != 0ull; rem &= rem - 1ull) {
-          const int k = __ffsll(static_cast<long long>(rem)) - 1;
-          const float gx = gap(c_fwd.x[k], v.x), gy = gap(c_fwd.y[k], v.y), gz = gap(c_fwd.z[k], v.z);
-          if (gx * gx + gy * gy + gz * gz <= rcmax2) km |= 1ull << k;
+        if (tr.reach == 2) {
+          for (unsigned long long rem = occ_mask & ~1ull; rem != 0ull; rem &= rem - 1ull) {
+            const int k = __ffsll(static_cast<long long>(rem)) - 1;
+            const float gx = gap(c_fwd.x[k], v.x), gy = gap(c_fwd.y[k], v.y), gz = gap(c_fwd.z[k], v.z);
+            if (gx * gx + gy * gy + gz * gz <= rcmax2) km |= 1ull << k;
+          }
+        } else {
+          // one cell out: per axis the gap is 0 (same layer), the distance to the lower
+          // face (offset -1) or to the upper face (offset +1); the 13 offsets unrolled
+          const float xm = gap(-1, v.x), xp = gap(1, v.x), ym = gap(-1, v.y), yp = gap(1, v.y);
+          const float zp = gap(1, v.z);
+          const float xm2 = xm * xm, xp2 = xp * xp, ym2 = ym * ym, yp2 = yp * yp, zp2 = zp * zp;
+          unsigned long long kr = 0ull;
+#pragma unroll
+          for (int k = 1; k < N_FWD; ++k) {
+            int dx, dy, dz;
+            fwd_offset(k, dx, dy, dz);
+            const float sx = dx < 0 ? xm2 : (dx > 0 ? xp2 : 0.f);
+            const float sy = dy < 0 ? ym2 : (dy > 0 ? yp2 : 0.f);
+            const float sz = dz > 0 ? zp2 : 0.f;
+            if ((sx + sy) + sz <= rcmax2) kr |= 1ull << k;
+          }
+          km |= kr & occ_mask;
         }
       }
     }
     const uint32_t uni_lo = __reduce_or_sync(FULL, static_cast<uint32_t>(km));
-    const uint32_t uni_hi = __reduce_or_sync(FULL, static_cast<uint32_t>(km >> 32));
+    // (one cell out: no half-shell index reaches 32)
+    const uint32_t uni_hi = n_fwd > 32 ? __reduce_or_sync(FULL, static_cast<uint32_t>(km >> 32)) : 0u;
     const unsigned long long uni = (static_cast<unsigned long long>(uni_hi) << 32) | uni_lo;
 #pragma unroll
     for (int u = 0; u < MAXT; ++u) {
