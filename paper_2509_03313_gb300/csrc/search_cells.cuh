@@ -48,23 +48,32 @@ struct ScWarp {
   int ct_b;
 };
 
+// The half-shell offsets in shared memory: looked up with a different offset number in
+// each lane, the constant-memory table would serialise a warp's access per distinct
+// address.
+struct ScOffsets {
+  float f[3][N_FWD2];       // as the FP32 factors of the cell side
+  int8_t i[3][N_FWD2 + 1];  // as cell steps
+};
+
 template <int W>
 struct ScSmem {
+  ScOffsets fo;
   ScWarp w[W];
 };
 
 // Acceptance of one queued pair (home slot si, neighbour slot j in the forward cell k of
 // the home's cell) and, when accepted, its candidate record.
 template <bool F32L>
-__device__ __forceinline__ void sc_resolve(const Dev& d, const Tables& tb, uint32_t si, uint32_t j, uint32_t kb,
-                                           const uint32_t* vf, uint32_t& n_in_cut) {
+__device__ __forceinline__ void sc_resolve(const Dev& d, const Tables& tb, const ScOffsets& fo, uint32_t si,
+                                           uint32_t j, uint32_t kb, const uint32_t* vf, uint32_t& n_in_cut) {
   const int k = static_cast<int>(kb & 255u), b = static_cast<int>(kb >> 8);
   const Train& tr = d.trains[b];
   if constexpr (F32L) {
     const float4 hv = d.s4[si], vj = d.s4[j];
     // the walk's separation, formed the same way
     float fx, fy, fz;
-    const float f2 = sep_f32(c_fwd.x[k], c_fwd.y[k], c_fwd.z[k], tr.hf, vj, hv, fx, fy, fz);
+    const float f2 = sep_f32(fo.f[0][k], fo.f[1][k], fo.f[2][k], tr.hf, vj, hv, fx, fy, fz);
     const uint32_t tid_i = __float_as_uint(hv.w), tid_j = __float_as_uint(vj.w);
     const int r = tb.pair_rxn[tid_type(tid_i)][tid_type(tid_j)];
     const uint32_t id_i = tid_id(tid_i), id_j = tid_id(tid_j);
@@ -108,10 +117,10 @@ __device__ __forceinline__ void sc_resolve(const Dev& d, const Tables& tb, uint3
 }
 
 template <bool F32L>
-__device__ __forceinline__ void sc_flush(const Dev& d, const Tables& tb, ScWarp& w, const uint32_t* vf, int lane,
-                                         uint32_t& n_in_cut) {
+__device__ __forceinline__ void sc_flush(const Dev& d, const Tables& tb, const ScOffsets& fo, ScWarp& w,
+                                         const uint32_t* vf, int lane, uint32_t& n_in_cut) {
   const uint32_t nq = w.qn;
-  for (uint32_t e = lane; e < nq; e += 32) sc_resolve<F32L>(d, tb, w.qi[e], w.qj[e], w.qk[e], vf, n_in_cut);
+  for (uint32_t e = lane; e < nq; e += 32) sc_resolve<F32L>(d, tb, fo, w.qi[e], w.qj[e], w.qk[e], vf, n_in_cut);
   __syncwarp();
   if (lane == 0) w.qn = 0;
   __syncwarp();
@@ -119,7 +128,7 @@ __device__ __forceinline__ void sc_flush(const Dev& d, const Tables& tb, ScWarp&
 
 template <bool F32L, int W>
 __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
-  if (status_of(d) || !d.g->search_cells_now) return;  // this step runs one thread per species
+  if (!d.g->search_cells_now) return;  // this step runs one thread per species (grid-uniform)
   constexpr uint32_t FULL = 0xffffffffu;
   const uint32_t n_items = min(d.g->n_items, d.cap_items);
   const uint32_t epoch = d.g->epoch;
@@ -129,8 +138,14 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
   ScWarp& w = sm.w[wib];
+  const ScOffsets& fo = sm.fo;
+  for (int k = threadIdx.x; k < N_FWD2; k += blockDim.x) {
+    sm.fo.f[0][k] = c_fwd.x[k]; sm.fo.f[1][k] = c_fwd.y[k]; sm.fo.f[2][k] = c_fwd.z[k];
+    sm.fo.i[0][k] = c_fwd.x[k]; sm.fo.i[1][k] = c_fwd.y[k]; sm.fo.i[2][k] = c_fwd.z[k];
+  }
   if (lane == 0) { w.qn = 0; w.ct_b = -1; }
-  __syncwarp();
+  // one status for the whole CTA (a barrier, which also publishes the offsets)
+  if (!block_status_ok(d)) return;
   uint32_t n_tested = 0, n_in_cut = 0;  // pair-search counters of this lane
   const uint32_t item_home = min(max(d.g->item_home, 1u), static_cast<uint32_t>(SC_HOMES));
   const uint32_t n_live = d.g->n_total - d.g->n_dead;
@@ -177,13 +192,13 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
       const int n = tr.n;
       const int k0 = lane, k1 = lane + 32;
       if (k0 >= 1 && k0 < n_fwd) {
-        nc0 = tr.cell_base + cell_encode(step_cell(cx, c_fwd.x[k0], n), step_cell(cy, c_fwd.y[k0], n),
-                                         step_cell(cz, c_fwd.z[k0], n), tr.cb);
+        nc0 = tr.cell_base + cell_encode(step_cell(cx, fo.i[0][k0], n), step_cell(cy, fo.i[1][k0], n),
+                                         step_cell(cz, fo.i[2][k0], n), tr.cb);
         occ0 = (d.occ[nc0 >> 5] >> (nc0 & 31u)) & 1u;
       }
       if (k1 < n_fwd) {
-        nc1 = tr.cell_base + cell_encode(step_cell(cx, c_fwd.x[k1], n), step_cell(cy, c_fwd.y[k1], n),
-                                         step_cell(cz, c_fwd.z[k1], n), tr.cb);
+        nc1 = tr.cell_base + cell_encode(step_cell(cx, fo.i[0][k1], n), step_cell(cy, fo.i[1][k1], n),
+                                         step_cell(cz, fo.i[2][k1], n), tr.cb);
         occ1 = (d.occ[nc1 >> 5] >> (nc1 & 31u)) & 1u;
       }
     }
@@ -315,8 +330,8 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
         const float4 vj = d.s4[j];
         const uint32_t tj = tid_type(__float_as_uint(vj.w));
         // the neighbour in the home cell's frame; the separation below is sep_f32's
-        const float bx = __fmaf_rn(c_fwd.x[k], hf, vj.x), by = __fmaf_rn(c_fwd.y[k], hf, vj.y),
-                    bz = __fmaf_rn(c_fwd.z[k], hf, vj.z);
+        const float bx = __fmaf_rn(fo.f[0][k], hf, vj.x), by = __fmaf_rn(fo.f[1][k], hf, vj.y),
+                    bz = __fmaf_rn(fo.f[2][k], hf, vj.z);
         uint32_t m = w.reach[k] & w.hm_type[tj] & home_bits;
         if (k == 0u) {  // own cell: only the homes before this slot
           const uint32_t lim = j - s0;
@@ -357,14 +372,14 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
         __syncwarp();
         if (lane == 0) w.qn = min(static_cast<uint32_t>(SC_QCAP), base + want);
         __syncwarp();
-        if (w.qn > static_cast<uint32_t>(SC_QCAP) - 32u) sc_flush<F32L>(d, tb, w, vf, lane, n_in_cut);
+        if (w.qn > static_cast<uint32_t>(SC_QCAP) - 32u) sc_flush<F32L>(d, tb, fo, w, vf, lane, n_in_cut);
       }
     }
     it = it_n1;
     rec = make_uint2(__shfl_sync(FULL, rec_n1.x, 0), __shfl_sync(FULL, rec_n1.y, 0));
     it_n1 = __shfl_sync(FULL, it_n2, 0);
   }
-  sc_flush<F32L>(d, tb, w, vf, lane, n_in_cut);
+  sc_flush<F32L>(d, tb, fo, w, vf, lane, n_in_cut);
   add_pair_counts(d, n_tested, n_in_cut);
 }
 
