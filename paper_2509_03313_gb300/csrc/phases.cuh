@@ -869,6 +869,21 @@ constexpr FwdOffsets make_fwd_offsets() {
 static_assert(make_fwd_offsets().count == N_FWD2, "62 forward cells within two cells");
 static __constant__ FwdOffsets c_fwd = make_fwd_offsets();
 
+// The half-shell offsets in shared memory: looked up with a different offset number in
+// each lane, the constant-memory table would serialise a warp's access per distinct
+// address. Filled by every thread of the CTA (fwd_smem_fill), then a CTA barrier.
+struct FwdSmem {
+  float f[3][N_FWD2];       // as FP32 factors of the cell side
+  int8_t i[3][N_FWD2 + 1];  // as cell steps
+};
+
+__device__ __forceinline__ void fwd_smem_fill(FwdSmem& fo) {
+  for (int k = threadIdx.x; k < N_FWD2; k += blockDim.x) {
+    fo.f[0][k] = c_fwd.x[k]; fo.f[1][k] = c_fwd.y[k]; fo.f[2][k] = c_fwd.z[k];
+    fo.i[0][k] = c_fwd.x[k]; fo.i[1][k] = c_fwd.y[k]; fo.i[2][k] = c_fwd.z[k];
+  }
+}
+
 // Half-shell offsets: 0 = own cell, 1..9 dz = +1, 10..12 (dz, dy) = (0, +1), 13 (0, 0, +1).
 __device__ __forceinline__ void fwd_offset(int k, int& dx, int& dy, int& dz) {
   if (k == 0) { dx = dy = dz = 0; return; }
@@ -1026,6 +1041,7 @@ struct TpsSmem {
   unsigned long long km[W][32];  // per lane: cells still to look up (bit 0 own cell, 1..62 forward)
   uint32_t cl[W][32];         // per lane: its home's cell
   TpsQueue<F32L> q[W];
+  FwdSmem fo;                 // half-shell offsets
 };
 
 // Acceptance of one queued pair (home species given by slot and packed id/type).
@@ -1086,15 +1102,18 @@ __device__ __forceinline__ void tps_flush(const Dev& d, const Tables& tb, TpsQue
 template <bool F32L, int W>
 __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
   using T = typename TpsSmem<F32L, W>::T;
-  if (status_of(d) || d.g->search_cells_now) return;  // this step runs the cell tiles
+  if (d.g->search_cells_now) return;  // this step runs the cell tiles (grid-uniform)
   const uint32_t n_live = d.g->n_total - d.g->n_dead;
   const uint32_t epoch = d.g->epoch;
   const uint32_t* vf = d.g->sort_any ? (d.g->sort_parity ? d.vals1 : d.vals0) : nullptr;
   const Tables& tb = *d.tables;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   TpsQueue<F32L>& q = sm.q[wib];
+  fwd_smem_fill(sm.fo);
   if (lane == 0) { q.n = 0; sm.ct_b[wib] = -1; }
-  __syncwarp();
+  // one status for the whole CTA (a barrier, which also publishes the offsets)
+  if (!block_status_ok(d)) return;
+  const FwdSmem& fo = sm.fo;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
   const uint32_t n_chunks = (n_live + 31u) / 32u;
   uint32_t n_tested = 0, n_in_cut = 0;  // pair-search counters of this lane
@@ -1255,8 +1274,8 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
             const int k = kk[q], n = tr.n;
             int ix, iy, iz;
             cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
-            nc[q] = tr.cell_base + cell_encode(step_cell(ix, c_fwd.x[k], n), step_cell(iy, c_fwd.y[k], n),
-                                               step_cell(iz, c_fwd.z[k], n), tr.cb);
+            nc[q] = tr.cell_base + cell_encode(step_cell(ix, fo.i[0][k], n), step_cell(iy, fo.i[1][k], n),
+                                               step_cell(iz, fo.i[2][k], n), tr.cb);
             word[q] = d.occ[nc[q] >> 5];
           }
         }
@@ -1293,7 +1312,7 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
         j = rs_l[32 * r];
         je = re_l[32 * r];
         const int k = rk_l[32 * r];
-        cx = c_fwd.x[k]; cy = c_fwd.y[k]; cz = c_fwd.z[k];  // in cells
+        cx = fo.f[0][k]; cy = fo.f[1][k]; cz = fo.f[2][k];  // in cells
       };
       if (nr > 0) open(0);
       while (__any_sync(0xffffffffu, ri < nr)) {

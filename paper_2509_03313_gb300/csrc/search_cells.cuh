@@ -48,24 +48,16 @@ struct ScWarp {
   int ct_b;
 };
 
-// The half-shell offsets in shared memory: looked up with a different offset number in
-// each lane, the constant-memory table would serialise a warp's access per distinct
-// address.
-struct ScOffsets {
-  float f[3][N_FWD2];       // as the FP32 factors of the cell side
-  int8_t i[3][N_FWD2 + 1];  // as cell steps
-};
-
 template <int W>
 struct ScSmem {
-  ScOffsets fo;
+  FwdSmem fo;  // half-shell offsets
   ScWarp w[W];
 };
 
 // Acceptance of one queued pair (home slot si, neighbour slot j in the forward cell k of
 // the home's cell) and, when accepted, its candidate record.
 template <bool F32L>
-__device__ __forceinline__ void sc_resolve(const Dev& d, const Tables& tb, const ScOffsets& fo, uint32_t si,
+__device__ __forceinline__ void sc_resolve(const Dev& d, const Tables& tb, const FwdSmem& fo, uint32_t si,
                                            uint32_t j, uint32_t kb, const uint32_t* vf, uint32_t& n_in_cut) {
   const int k = static_cast<int>(kb & 255u), b = static_cast<int>(kb >> 8);
   const Train& tr = d.trains[b];
@@ -117,7 +109,7 @@ __device__ __forceinline__ void sc_resolve(const Dev& d, const Tables& tb, const
 }
 
 template <bool F32L>
-__device__ __forceinline__ void sc_flush(const Dev& d, const Tables& tb, const ScOffsets& fo, ScWarp& w,
+__device__ __forceinline__ void sc_flush(const Dev& d, const Tables& tb, const FwdSmem& fo, ScWarp& w,
                                          const uint32_t* vf, int lane, uint32_t& n_in_cut) {
   const uint32_t nq = w.qn;
   for (uint32_t e = lane; e < nq; e += 32) sc_resolve<F32L>(d, tb, fo, w.qi[e], w.qj[e], w.qk[e], vf, n_in_cut);
@@ -138,11 +130,8 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
   ScWarp& w = sm.w[wib];
-  const ScOffsets& fo = sm.fo;
-  for (int k = threadIdx.x; k < N_FWD2; k += blockDim.x) {
-    sm.fo.f[0][k] = c_fwd.x[k]; sm.fo.f[1][k] = c_fwd.y[k]; sm.fo.f[2][k] = c_fwd.z[k];
-    sm.fo.i[0][k] = c_fwd.x[k]; sm.fo.i[1][k] = c_fwd.y[k]; sm.fo.i[2][k] = c_fwd.z[k];
-  }
+  const FwdSmem& fo = sm.fo;
+  fwd_smem_fill(sm.fo);
   if (lane == 0) { w.qn = 0; w.ct_b = -1; }
   // one status for the whole CTA (a barrier, which also publishes the offsets)
   if (!block_status_ok(d)) return;
