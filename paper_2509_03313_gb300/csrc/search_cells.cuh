@@ -244,19 +244,38 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
         }
       }
     }
-    const uint32_t uni_lo = __reduce_or_sync(FULL, static_cast<uint32_t>(km));
-    // (one cell out: no half-shell index reaches 32)
-    const uint32_t uni_hi = n_fwd > 32 ? __reduce_or_sync(FULL, static_cast<uint32_t>(km >> 32)) : 0u;
-    const unsigned long long uni = (static_cast<unsigned long long>(uni_hi) << 32) | uni_lo;
+    unsigned long long uni;
+    if (n_fwd <= 16) {
+      // one cell out: a 32 x 32 bit transpose of (lane = home; bits 0..13 the half-shell
+      // cells it reaches, bits 16..23 the types it reacts with) leaves in lane k the
+      // homes that reach cell k and in lane 16 + u the homes that react with type u
+      uint32_t x = static_cast<uint32_t>(km) | (rmask << 16);
+      auto stage = [&](int sh, uint32_t msk) {
+        const uint32_t y = __shfl_xor_sync(FULL, x, sh);
+        x = (lane & sh) ? ((x & ~msk) | ((y >> sh) & msk)) : ((x & msk) | ((y & msk) << sh));
+      };
+      stage(16, 0x0000FFFFu);
+      stage(8, 0x00FF00FFu);
+      stage(4, 0x0F0F0F0Fu);
+      stage(2, 0x33333333u);
+      stage(1, 0x55555555u);
+      if (lane < n_fwd) w.reach[lane] = x;
+      if (lane >= 16 && lane < 16 + MAXT) w.hm_type[lane - 16] = x;
+      uni = __ballot_sync(FULL, lane < n_fwd && x != 0u);
+    } else {
+      const uint32_t uni_lo = __reduce_or_sync(FULL, static_cast<uint32_t>(km));
+      const uint32_t uni_hi = __reduce_or_sync(FULL, static_cast<uint32_t>(km >> 32));
+      uni = (static_cast<unsigned long long>(uni_hi) << 32) | uni_lo;
 #pragma unroll
-    for (int u = 0; u < MAXT; ++u) {
-      const uint32_t m = __ballot_sync(FULL, (rmask >> u) & 1u);
-      if (lane == 0) w.hm_type[u] = m;
-    }
-    for (unsigned long long rem = uni; rem != 0ull; rem &= rem - 1ull) {  // warp-uniform
-      const int k = __ffsll(static_cast<long long>(rem)) - 1;
-      const uint32_t m = __ballot_sync(FULL, (km >> k) & 1ull);
-      if (lane == 0) w.reach[k] = m;
+      for (int u = 0; u < MAXT; ++u) {
+        const uint32_t m = __ballot_sync(FULL, (rmask >> u) & 1u);
+        if (lane == 0) w.hm_type[u] = m;
+      }
+      for (unsigned long long rem = uni; rem != 0ull; rem &= rem - 1ull) {  // warp-uniform
+        const int k = __ffsll(static_cast<long long>(rem)) - 1;
+        const uint32_t m = __ballot_sync(FULL, (km >> k) & 1ull);
+        if (lane == 0) w.reach[k] = m;
+      }
     }
     // 2. the reachable cells' ranges, non-empty ones laid end to end in half-shell order
     uint32_t nr = 0;
