@@ -297,16 +297,13 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
     const int n_max = min(tr.n_max, (1 << tr.cb_alloc) - 1), fj = tr.free_jump;
     int n_ref = tr.n_ref;
     const double rcmax = __longlong_as_double(static_cast<long long>(sb.rcmax_bits[b]));
-    // finest admissible grid: cells at least the largest cutoff (with slack), or at least
-    // half of it when the pair search may look two cells out (then at least 5 cells)
-    int n_target = n_max, n_one = n_max;
+    // finest admissible grid: cells at least the largest cutoff (with slack), at least 3
+    // per axis (no cell met twice among a cell's neighbours)
+    int n_target = n_max;
     if (rcmax > 0.0) {
       const float cut = static_cast<float>(rcmax) * CELL_SLACK_F;
       const float nf1 = floorf(static_cast<float>(L) / cut);
-      const float nf2 = floorf(2.f * static_cast<float>(L) / cut);
-      n_one = max(3, min(n_max, static_cast<int>(fminf(nf1, 1048576.f))));
-      const int n_two = min(n_max, static_cast<int>(fminf(nf2, 1048576.f)));
-      n_target = (d.max_reach >= 2 && n_two >= 5) ? n_two : n_one;
+      n_target = max(3, min(n_max, static_cast<int>(fminf(nf1, 1048576.f))));
     }
     if (n_ref == 0) {  // first step after init or reset
       n_ref = n_target;
@@ -321,25 +318,15 @@ static __device__ void phase_begin(const Dev& d, BeginSmem& sb) {
       if (n > n_target) n = max(3, (5 * n_target) / 6);
       else if (2 * n < n_target) n = n_target;
     }
-    // cells the search looks out: 1 when a cell covers the largest cutoff; 2 needs at
-    // least 5 cells per axis (no cell met twice) and cells of half the cutoff
-    int reach = 1;
+    // the search looks one cell out: a cell must cover the largest cutoff
     if (!fj && rcmax > 0.0) {
       const double cut = rcmax * static_cast<double>(CELL_SLACK_F);
-      const double hn = L / static_cast<double>(n);
-      if (hn < cut) {
-        if (d.max_reach >= 2 && n >= 5 && 2.0 * hn >= cut) {
-          reach = 2;
-        } else {
-          n = n_one;
-        }
-      }
+      if (L / static_cast<double>(n) < cut) n = n_target;
     }
     const double h = __ddiv_rn(L, static_cast<double>(n));
     const double inv_h = __dmul_rn(static_cast<double>(n), inv_L);
     tr.n = n;
     tr.cb = axis_bits(n);
-    tr.reach = reach;
     tr.h = h;
     tr.inv_h = inv_h;
     tr.hf = static_cast<float>(h);
@@ -838,11 +825,11 @@ __device__ void phase_gather(const Dev& d) {
 // (search_cells.cuh). With at least 3 cells per axis each unordered pair is visited
 // once: the own cell's later slots and the forward half of the surrounding cells.
 
-// Half-shell offsets within two cells: entry 0 is the own cell, 1..13 the cells one away
-// in fwd_offset's order, 14..62 the cells two away; each keeps the offsets (dz, dy, dx)
-// that are lexicographically positive, so every unordered pair of cells is met once.
+// Half-shell offsets: entry 0 is the own cell, 1..13 the cells one away in fwd_offset's
+// order; each keeps the offsets (dz, dy, dx) that are lexicographically positive, so
+// every unordered pair of cells is met once.
 struct FwdOffsets {
-  signed char x[N_FWD2], y[N_FWD2], z[N_FWD2];
+  signed char x[N_FWD], y[N_FWD], z[N_FWD];
   int count;
 };
 constexpr FwdOffsets make_fwd_offsets() {
@@ -852,33 +839,22 @@ constexpr FwdOffsets make_fwd_offsets() {
     for (int dx = -1; dx <= 1; ++dx) { t.x[k] = static_cast<signed char>(dx); t.y[k] = static_cast<signed char>(dy); t.z[k] = 1; ++k; }
   for (int dx = -1; dx <= 1; ++dx) { t.x[k] = static_cast<signed char>(dx); t.y[k] = 1; t.z[k] = 0; ++k; }
   t.x[k] = 1; t.y[k] = 0; t.z[k] = 0; ++k;
-  for (int dz = 0; dz <= 2; ++dz)
-    for (int dy = -2; dy <= 2; ++dy)
-      for (int dx = -2; dx <= 2; ++dx) {
-        const bool pos = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
-        const int ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy;
-        const int m = ax > ay ? (ax > dz ? ax : dz) : (ay > dz ? ay : dz);
-        if (pos && m == 2) {
-          t.x[k] = static_cast<signed char>(dx); t.y[k] = static_cast<signed char>(dy);
-          t.z[k] = static_cast<signed char>(dz); ++k;
-        }
-      }
   t.count = k;
   return t;
 }
-static_assert(make_fwd_offsets().count == N_FWD2, "62 forward cells within two cells");
+static_assert(make_fwd_offsets().count == N_FWD, "13 forward cells");
 static __constant__ FwdOffsets c_fwd = make_fwd_offsets();
 
 // The half-shell offsets in shared memory: looked up with a different offset number in
 // each lane, the constant-memory table would serialise a warp's access per distinct
 // address. Filled by every thread of the CTA (fwd_smem_fill), then a CTA barrier.
 struct FwdSmem {
-  float f[3][N_FWD2];       // as FP32 factors of the cell side
-  int8_t i[3][N_FWD2 + 1];  // as cell steps
+  float f[3][N_FWD];       // as FP32 factors of the cell side
+  int8_t i[3][N_FWD + 2];  // as cell steps
 };
 
 __device__ __forceinline__ void fwd_smem_fill(FwdSmem& fo) {
-  for (int k = threadIdx.x; k < N_FWD2; k += blockDim.x) {
+  for (int k = threadIdx.x; k < N_FWD; k += blockDim.x) {
     fo.f[0][k] = c_fwd.x[k]; fo.f[1][k] = c_fwd.y[k]; fo.f[2][k] = c_fwd.z[k];
     fo.i[0][k] = c_fwd.x[k]; fo.i[1][k] = c_fwd.y[k]; fo.i[2][k] = c_fwd.z[k];
   }
@@ -1038,8 +1014,6 @@ struct TpsSmem {
   uint32_t rs[W][N_FWD][32];  // per lane: its non-empty neighbour ranges [rs, re) ...
   uint32_t re[W][N_FWD][32];
   uint8_t rk[W][N_FWD][32];   // ... and their half-shell offsets
-  unsigned long long km[W][32];  // per lane: cells still to look up (bit 0 own cell, 1..62 forward)
-  uint32_t cl[W][32];         // per lane: its home's cell
   TpsQueue<F32L> q[W];
   FwdSmem fo;                 // half-shell offsets
 };
@@ -1167,16 +1141,16 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
     if (__any_sync(0xffffffffu, home)) {
       // this lane's non-empty ranges: the own cell's later slots, then the forward cells
       // within reach that are occupied (bit test in the L2-resident bitmap, then their
-      // 16-byte entries), collected and walked in batches of at most N_FWD ranges
+      // 16-byte entries), collected (at most N_FWD ranges) and walked
       uint32_t* rs_l = &sm.rs[wib][0][lane];
       uint32_t* re_l = &sm.re[wib][0][lane];
       uint8_t* rk_l = &sm.rk[wib][0][lane];
-      // bit 0: the own cell's later slots; bits 1..62: forward cells within reach
-      unsigned long long kmask = 0ull;
+      // bit 0: the own cell's later slots; bits 1..13: forward cells within reach
+      uint32_t kmask = 0u;
       if (home) {
         int ix, iy, iz;
         cell_decode(cell - tr.cell_base, tr.cb, ix, iy, iz);
-        if (s + 1u < static_cast<uint32_t>(d.cell_info[cell].y)) kmask = 1ull;
+        if (s + 1u < static_cast<uint32_t>(d.cell_info[cell].y)) kmask = 1u;
         // a forward cell whose nearest point is farther from the home than the largest
         // cutoff of the home's type holds no partner and is not looked up (the gaps are
         // taken 1e-5 of a cell short, which covers every rounding of the offsets)
@@ -1198,31 +1172,21 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
                                 : (o < 0 ? of + static_cast<float>(-o - 1) * hcell : 0.f);
           return fmaxf(g - eps, 0.f);
         };
-        if (tr.reach == 2) {
-          for (int k = 1; k < N_FWD2; ++k) {
-            const float gx = gap(c_fwd.x[k], ofx), gy = gap(c_fwd.y[k], ofy), gz = gap(c_fwd.z[k], ofz);
-            if (gx * gx + gy * gy + gz * gz <= rcmax2) kmask |= 1ull << k;
-          }
-        } else {
-          // one cell out: per axis the gap is 0 (same layer), the distance to the lower
-          // face (offset -1) or to the upper face (offset +1); the 13 offsets unrolled
-          const float xm = gap(-1, ofx), xp = gap(1, ofx), ym = gap(-1, ofy), yp = gap(1, ofy);
-          const float zp = gap(1, ofz);
-          const float xm2 = xm * xm, xp2 = xp * xp, ym2 = ym * ym, yp2 = yp * yp, zp2 = zp * zp;
+        // per axis the gap is 0 (same layer), the distance to the lower face (offset -1)
+        // or to the upper face (offset +1); the 13 offsets unrolled
+        const float xm = gap(-1, ofx), xp = gap(1, ofx), ym = gap(-1, ofy), yp = gap(1, ofy);
+        const float zp = gap(1, ofz);
+        const float xm2 = xm * xm, xp2 = xp * xp, ym2 = ym * ym, yp2 = yp * yp, zp2 = zp * zp;
 #pragma unroll
-          for (int k = 1; k < N_FWD; ++k) {
-            int dx, dy, dz;
-            fwd_offset(k, dx, dy, dz);
-            const float sx = dx < 0 ? xm2 : (dx > 0 ? xp2 : 0.f);
-            const float sy = dy < 0 ? ym2 : (dy > 0 ? yp2 : 0.f);
-            const float sz = dz > 0 ? zp2 : 0.f;
-            if ((sx + sy) + sz <= rcmax2) kmask |= 1ull << k;
-          }
+        for (int k = 1; k < N_FWD; ++k) {
+          int dx, dy, dz;
+          fwd_offset(k, dx, dy, dz);
+          const float sx = dx < 0 ? xm2 : (dx > 0 ? xp2 : 0.f);
+          const float sy = dy < 0 ? ym2 : (dy > 0 ? yp2 : 0.f);
+          const float sz = dz > 0 ? zp2 : 0.f;
+          if ((sx + sy) + sz <= rcmax2) kmask |= 1u << k;
         }
       }
-      // kept in shared memory while the ranges are walked (registers are the walk's)
-      sm.km[wib][lane] = kmask;
-      sm.cl[wib][lane] = cell;
       // the lane's home for the walk (ranges are not moved between lanes: on clustered
       // tracks, taking over half of a busy lane's range cost more issue slots than the
       // idle lanes it saved; dense cells go to the cell-tile mapping instead)
@@ -1250,22 +1214,20 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           if (q.n > static_cast<uint32_t>(TpsQueue<F32L>::CAP) - 32u) tps_flush<F32L>(d, tb, q, vf, lane);
         }
       };
-      while (__any_sync(0xffffffffu, sm.km[wib][lane] != 0ull)) {
       int nr = 0;
-      // look up only the cells within reach (warp-uniform loop over each lane's set bits)
+      // look up only the cells within reach (warp-uniform loop over each lane's set bits:
+      // at most N_FWD of them, so one pass collects them all)
       {
-      unsigned long long kmask = sm.km[wib][lane];
-      const uint32_t cell = sm.cl[wib][lane];
       // two cells per iteration, their bitmap words and then their entries loaded together
-      while (__any_sync(0xffffffffu, kmask != 0ull && nr < N_FWD)) {
+      while (__any_sync(0xffffffffu, kmask != 0u)) {
         int kk[2] = {-1, -1};
-        if (kmask != 0ull && nr < N_FWD) {
-          kk[0] = __ffsll(static_cast<long long>(kmask)) - 1;
-          kmask &= kmask - 1ull;
+        if (kmask != 0u) {
+          kk[0] = __ffs(kmask) - 1;
+          kmask &= kmask - 1u;
         }
-        if (kmask != 0ull && nr + 1 < N_FWD) {
-          kk[1] = __ffsll(static_cast<long long>(kmask)) - 1;
-          kmask &= kmask - 1ull;
+        if (kmask != 0u) {
+          kk[1] = __ffs(kmask) - 1;
+          kmask &= kmask - 1u;
         }
         uint32_t nc[2] = {0u, 0u}, word[2] = {0u, 0u};
 #pragma unroll
@@ -1301,7 +1263,6 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           }
         }
       }
-      sm.km[wib][lane] = kmask;
       }
       // walk the ranges one after the other, TPS_UNROLL neighbours per iteration whose loads
       // are in flight together; lanes of one cell stay in step (broadcast loads)
@@ -1402,7 +1363,6 @@ __device__ void phase_search_tps(const Dev& d, TpsSmem<F32L, W>& sm) {
           }
         }
       }
-      }  // batches of ranges
     }
     c_next = __shfl_sync(0xffffffffu, c_next, 0);
   }
@@ -2043,11 +2003,10 @@ __device__ void phase_products(const Dev& d, ProductsSmem& sm) {
       cell_decode(ca - tr.cell_base, tr.cb, ax_, ay_, az_);
       cell_decode(cc - tr.cell_base, tr.cb, cx_, cy_, cz_);
       int dx = cx_ - ax_, dy = cy_ - ay_, dz = cz_ - az_;
-      // cells of a reacting pair are at most tr.reach apart (with n >= 5 when 2)
-      const int rr = tr.reach;
-      dx = dx > rr ? dx - n : (dx < -rr ? dx + n : dx);
-      dy = dy > rr ? dy - n : (dy < -rr ? dy + n : dy);
-      dz = dz > rr ? dz - n : (dz < -rr ? dz + n : dz);
+      // the cells of a reacting pair are at most one apart per axis (n >= 3)
+      dx = dx > 1 ? dx - n : (dx < -1 ? dx + n : dx);
+      dy = dy > 1 ? dy - n : (dy < -1 ? dy + n : dy);
+      dz = dz > 1 ? dz - n : (dz < -1 ? dz + n : dz);
       const float w = tb.Df[tlo] / (tb.Df[tlo] + tb.Df[thi]);
       const float px = a.x + w * (dx * tr.hf + (c.x - a.x));
       const float py = a.y + w * (dy * tr.hf + (c.y - a.y));

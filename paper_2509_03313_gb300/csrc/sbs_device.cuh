@@ -38,7 +38,6 @@ constexpr int SORT_TILE_MIN = PERSIST_THREADS * SORT_ITEMS;
 constexpr int REACT_THREADS = 1024;
 constexpr int ITEM_HOME = 32;   // most home species per pair-search work item (one cell)
 constexpr int N_FWD = 14;       // own cell + 13 forward neighbour cells (half shell)
-constexpr int N_FWD2 = 63;      // own cell + 62 forward cells within two cells (half shell)
 constexpr double END_SLACK = 1.0 + 1e-6;    // last-step trim slack (relative)
 constexpr float CELL_SLACK_F = 1.0001f;    // hash cell >= cutoff * CELL_SLACK_F
 constexpr long long SPIN_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
@@ -92,7 +91,6 @@ struct Train {
   int active, free_jump;
   double dt, t_next, t_start;
   int n;                   // cells per axis this step
-  int reach;               // cells the pair search looks out (1, or 2 with cells >= cutoff / 2)
   double h, inv_h;
   float hf, inv_hf;
   double rc2[MAXR];
@@ -187,8 +185,6 @@ struct Dev {
   uint32_t cap, cap_cand, cap_ev_log, cap_step_log, cap_pend;
   uint32_t n_trains, total_cells, sentinel;
   int passes, precision;
-  int max_reach;         // 2: the grid may use cells of half the cutoff (pair search reaches
-                         // two cells out); else 1
   int train_bits;        // bits of (n_trains - 1): event key = train << (32 - bits) | id_lo
   double* sx; double* sy; double* sz; uint32_t* stid;
   double* tx; double* ty; double* tz; uint32_t* ttid;

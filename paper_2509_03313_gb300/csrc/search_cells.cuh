@@ -7,9 +7,8 @@
 // One warp per work item: up to SC_HOMES consecutive sorted species ("homes") of one
 // hash cell, one home per bit of a 32-bit mask.
 //  1. Each home lane loads its state and decides, with the box-gap test against the
-//     largest cutoff of its type, which cells of the half shell (13 forward cells, or 62
-//     within two cells when the grid is finer than the cutoff) it can reach; a 64-bit
-//     mask per home. Bit 0 is the own cell's later slots.
+//     largest cutoff of its type, which cells of the half shell (the 13 forward cells) it
+//     can reach; a bit mask per home. Bit 0 is the own cell's later slots.
 //  2. The warp looks up the union of those cells (occupancy bit, then the epoch-stamped
 //     range) and lays the non-empty ranges end to end as one list.
 //  3. Lanes take 32 list entries at a time (coalesced 16-byte loads). For its neighbour
@@ -30,7 +29,7 @@ namespace chem {
 
 constexpr int SC_HOMES = 32;    // home species per work item (one bit each)
 constexpr int SC_QCAP = 128;    // queued pairs per warp
-constexpr int SC_RANGES = N_FWD2;  // own cell + 62 forward cells
+constexpr int SC_RANGES = N_FWD;  // own cell + 13 forward cells
 
 struct ScWarp {
   float4 hv[SC_HOMES];             // homes: FP32 cell offsets and id/type bits
@@ -164,49 +163,38 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
       if (lane == 0) w.ct_b = b;
       __syncwarp();
     }
-    const int n_fwd = tr.reach == 2 ? N_FWD2 : N_FWD;
     const float hf = tr.hf;
     int cx, cy, cz;
     cell_decode(cell - tr.cell_base, tr.cb, cx, cy, cz);
     // independent loads issued together: this lane's home (speculatively, up to the item
-    // size), the own cell's end, and the occupancy bits of the half-shell cells k = lane
-    // and lane + 32
+    // size), the own cell's end, and the occupancy bit of the half-shell cell k = lane
     const uint32_t s_home = s0 + static_cast<uint32_t>(lane);
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (static_cast<uint32_t>(lane) < item_home && s_home < n_live) v = d.s4[s_home];
     const uint32_t own_end = static_cast<uint32_t>(d.cell_info[cell].y);
-    uint32_t nc0 = 0, nc1 = 0;
-    bool occ0 = false, occ1 = false;
-    {
+    uint32_t nc0 = 0;
+    bool occ0 = false;
+    if (lane >= 1 && lane < N_FWD) {
       const int n = tr.n;
-      const int k0 = lane, k1 = lane + 32;
-      if (k0 >= 1 && k0 < n_fwd) {
-        nc0 = tr.cell_base + cell_encode(step_cell(cx, fo.i[0][k0], n), step_cell(cy, fo.i[1][k0], n),
-                                         step_cell(cz, fo.i[2][k0], n), tr.cb);
-        occ0 = (d.occ[nc0 >> 5] >> (nc0 & 31u)) & 1u;
-      }
-      if (k1 < n_fwd) {
-        nc1 = tr.cell_base + cell_encode(step_cell(cx, fo.i[0][k1], n), step_cell(cy, fo.i[1][k1], n),
-                                         step_cell(cz, fo.i[2][k1], n), tr.cb);
-        occ1 = (d.occ[nc1 >> 5] >> (nc1 & 31u)) & 1u;
-      }
+      nc0 = tr.cell_base + cell_encode(step_cell(cx, fo.i[0][lane], n), step_cell(cy, fo.i[1][lane], n),
+                                       step_cell(cz, fo.i[2][lane], n), tr.cb);
+      occ0 = (d.occ[nc0 >> 5] >> (nc0 & 31u)) & 1u;
     }
     // homes: from s0 to the cell's end or the next multiple of the item size, where the
     // gather starts the next item
     const uint32_t item_end = min(own_end, (s0 / item_home + 1u) * item_home);
     const uint32_t nh = item_end - s0;  // 1..32 homes
     // cells worth looking at: the own cell, and forward cells with their occupancy bit set
-    const unsigned long long occ_mask = 1ull | (static_cast<unsigned long long>(__ballot_sync(FULL, occ0))) |
-                                        (static_cast<unsigned long long>(__ballot_sync(FULL, occ1)) << 32);
+    const uint32_t occ_mask = 1u | __ballot_sync(FULL, occ0);
     // 1. homes and the cells each can reach
-    unsigned long long km = 0ull;
+    uint32_t km = 0u;
     uint32_t rmask = 0u;  // partner types of this lane's home
     if (static_cast<uint32_t>(lane) < nh) {
       w.hv[lane] = v;
       const uint32_t t = tid_type(__float_as_uint(v.w));
       rmask = tb.reactive_mask[t];
       if (rmask != 0u) {
-        if (s_home + 1u < own_end) km = 1ull;
+        if (s_home + 1u < own_end) km = 1u;
         float rcmax2 = -1.f;
 #pragma unroll
         for (int u = 0; u < MAXT; ++u) rcmax2 = fmaxf(rcmax2, w.ct[t * MAXT + u]);
@@ -218,107 +206,75 @@ __device__ void phase_search_cells(const Dev& d, ScSmem<W>& sm) {
           const float g = o > 0 ? static_cast<float>(o) * hf - of : (o < 0 ? of + static_cast<float>(-o - 1) * hf : 0.f);
           return fmaxf(g - eps, 0.f);
         };
-        if (tr.reach == 2) {
-          for (unsigned long long rem = occ_mask & ~1ull; rem != 0ull; rem &= rem - 1ull) {
-            const int k = __ffsll(static_cast<long long>(rem)) - 1;
-            const float gx = gap(c_fwd.x[k], v.x), gy = gap(c_fwd.y[k], v.y), gz = gap(c_fwd.z[k], v.z);
-            if (gx * gx + gy * gy + gz * gz <= rcmax2) km |= 1ull << k;
-          }
-        } else {
-          // one cell out: per axis the gap is 0 (same layer), the distance to the lower
-          // face (offset -1) or to the upper face (offset +1); the 13 offsets unrolled
-          const float xm = gap(-1, v.x), xp = gap(1, v.x), ym = gap(-1, v.y), yp = gap(1, v.y);
-          const float zp = gap(1, v.z);
-          const float xm2 = xm * xm, xp2 = xp * xp, ym2 = ym * ym, yp2 = yp * yp, zp2 = zp * zp;
-          unsigned long long kr = 0ull;
+        // per axis the gap is 0 (same layer), the distance to the lower face (offset -1)
+        // or to the upper face (offset +1); the 13 offsets unrolled
+        const float xm = gap(-1, v.x), xp = gap(1, v.x), ym = gap(-1, v.y), yp = gap(1, v.y);
+        const float zp = gap(1, v.z);
+        const float xm2 = xm * xm, xp2 = xp * xp, ym2 = ym * ym, yp2 = yp * yp, zp2 = zp * zp;
+        uint32_t kr = 0u;
 #pragma unroll
-          for (int k = 1; k < N_FWD; ++k) {
-            int dx, dy, dz;
-            fwd_offset(k, dx, dy, dz);
-            const float sx = dx < 0 ? xm2 : (dx > 0 ? xp2 : 0.f);
-            const float sy = dy < 0 ? ym2 : (dy > 0 ? yp2 : 0.f);
-            const float sz = dz > 0 ? zp2 : 0.f;
-            if ((sx + sy) + sz <= rcmax2) kr |= 1ull << k;
-          }
-          km |= kr & occ_mask;
+        for (int k = 1; k < N_FWD; ++k) {
+          int dx, dy, dz;
+          fwd_offset(k, dx, dy, dz);
+          const float sx = dx < 0 ? xm2 : (dx > 0 ? xp2 : 0.f);
+          const float sy = dy < 0 ? ym2 : (dy > 0 ? yp2 : 0.f);
+          const float sz = dz > 0 ? zp2 : 0.f;
+          if ((sx + sy) + sz <= rcmax2) kr |= 1u << k;
+        }
+        km |= kr & occ_mask;
+      }
+    }
+    // a 32 x 32 bit transpose of (lane = home; bits 0..13 the half-shell cells it
+    // reaches, bits 16..23 the types it reacts with) leaves in lane k the homes that
+    // reach cell k and in lane 16 + u the homes that react with type u
+    static_assert(N_FWD <= 16 && MAXT <= 16, "reach and partner-type bits share one word");
+    uint32_t x = km | (rmask << 16);
+    auto stage = [&](int sh, uint32_t msk) {
+      const uint32_t y = __shfl_xor_sync(FULL, x, sh);
+      x = (lane & sh) ? ((x & ~msk) | ((y >> sh) & msk)) : ((x & msk) | ((y & msk) << sh));
+    };
+    stage(16, 0x0000FFFFu);
+    stage(8, 0x00FF00FFu);
+    stage(4, 0x0F0F0F0Fu);
+    stage(2, 0x33333333u);
+    stage(1, 0x55555555u);
+    if (lane < N_FWD) w.reach[lane] = x;
+    if (lane >= 16 && lane < 16 + MAXT) w.hm_type[lane - 16] = x;
+    // 2. the reachable cells' ranges (lane k: half-shell cell k), non-empty ones laid end
+    // to end in half-shell order
+    uint32_t st = 0, len = 0;
+    if (lane < N_FWD && x != 0u) {
+      if (lane == 0) {
+        st = s0 + 1u;
+        len = own_end - st;
+      } else {
+        // occupied (the bit was tested above); the epoch-stamped entry confirms
+        const int4 ci = d.cell_info[nc0];
+        if (static_cast<uint32_t>(ci.z) == epoch && ci.y > ci.x) {
+          st = static_cast<uint32_t>(ci.x);
+          len = static_cast<uint32_t>(ci.y - ci.x);
         }
       }
     }
-    unsigned long long uni;
-    if (n_fwd <= 16) {
-      // one cell out: a 32 x 32 bit transpose of (lane = home; bits 0..13 the half-shell
-      // cells it reaches, bits 16..23 the types it reacts with) leaves in lane k the
-      // homes that reach cell k and in lane 16 + u the homes that react with type u
-      uint32_t x = static_cast<uint32_t>(km) | (rmask << 16);
-      auto stage = [&](int sh, uint32_t msk) {
-        const uint32_t y = __shfl_xor_sync(FULL, x, sh);
-        x = (lane & sh) ? ((x & ~msk) | ((y >> sh) & msk)) : ((x & msk) | ((y & msk) << sh));
-      };
-      stage(16, 0x0000FFFFu);
-      stage(8, 0x00FF00FFu);
-      stage(4, 0x0F0F0F0Fu);
-      stage(2, 0x33333333u);
-      stage(1, 0x55555555u);
-      if (lane < n_fwd) w.reach[lane] = x;
-      if (lane >= 16 && lane < 16 + MAXT) w.hm_type[lane - 16] = x;
-      uni = __ballot_sync(FULL, lane < n_fwd && x != 0u);
-    } else {
-      const uint32_t uni_lo = __reduce_or_sync(FULL, static_cast<uint32_t>(km));
-      const uint32_t uni_hi = __reduce_or_sync(FULL, static_cast<uint32_t>(km >> 32));
-      uni = (static_cast<unsigned long long>(uni_hi) << 32) | uni_lo;
-#pragma unroll
-      for (int u = 0; u < MAXT; ++u) {
-        const uint32_t m = __ballot_sync(FULL, (rmask >> u) & 1u);
-        if (lane == 0) w.hm_type[u] = m;
-      }
-      for (unsigned long long rem = uni; rem != 0ull; rem &= rem - 1ull) {  // warp-uniform
-        const int k = __ffsll(static_cast<long long>(rem)) - 1;
-        const uint32_t m = __ballot_sync(FULL, (km >> k) & 1ull);
-        if (lane == 0) w.reach[k] = m;
-      }
-    }
-    // 2. the reachable cells' ranges, non-empty ones laid end to end in half-shell order
-    uint32_t nr = 0;
-#pragma unroll
-    for (int round = 0; round < 2; ++round) {
-      const int k = lane + 32 * round;
-      uint32_t st = 0, len = 0;
-      if (k < n_fwd && ((uni >> k) & 1ull)) {
-        if (k == 0) {
-          st = s0 + 1u;
-          len = own_end - st;
-        } else {
-          // occupied (the bit was tested above); the epoch-stamped entry confirms
-          const int4 ci = d.cell_info[round == 0 ? nc0 : nc1];
-          if (static_cast<uint32_t>(ci.z) == epoch && ci.y > ci.x) {
-            st = static_cast<uint32_t>(ci.x);
-            len = static_cast<uint32_t>(ci.y - ci.x);
-          }
-        }
-      }
-      const uint32_t bal = __ballot_sync(FULL, len > 0u);
-      if (len > 0u) {
-        const uint32_t pos = nr + __popc(bal & lanemask_lt);
-        w.rs[pos] = st;
-        w.rlen[pos] = len;
-        w.rk[pos] = static_cast<uint8_t>(k);
-      }
-      nr += __popc(bal);
+    const uint32_t bal = __ballot_sync(FULL, len > 0u);
+    const uint32_t nr = __popc(bal);
+    if (len > 0u) {
+      const uint32_t pos = __popc(bal & lanemask_lt);
+      w.rs[pos] = st;
+      w.rlen[pos] = len;
+      w.rk[pos] = static_cast<uint8_t>(lane);
     }
     __syncwarp();
-    {  // exclusive offsets of the ranges (up to 63: two per lane)
+    {  // exclusive offsets of the ranges (at most N_FWD <= 16: lanes 0..15)
       const uint32_t x0 = static_cast<uint32_t>(lane) < nr ? w.rlen[lane] : 0u;
-      const uint32_t x1 = static_cast<uint32_t>(lane) + 32u < nr ? w.rlen[lane + 32] : 0u;
-      uint32_t a = x0, c = x1;
+      uint32_t a = x0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t ya = __shfl_up_sync(FULL, a, o), yc = __shfl_up_sync(FULL, c, o);
-        if (lane >= o) { a += ya; c += yc; }
+      for (int o = 1; o < 16; o <<= 1) {
+        const uint32_t ya = __shfl_up_sync(FULL, a, o);
+        if (lane >= o) a += ya;
       }
-      const uint32_t tot0 = __shfl_sync(FULL, a, 31);
       if (static_cast<uint32_t>(lane) < nr) w.roff[lane] = a - x0;
-      if (static_cast<uint32_t>(lane) + 32u < nr) w.roff[lane + 32] = tot0 + c - x1;
-      if (lane == 31) w.roff[nr] = tot0 + c;
+      if (lane == 15) w.roff[nr] = a;
     }
     __syncwarp();
     const uint32_t total = w.roff[nr];
