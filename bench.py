@@ -389,6 +389,13 @@ def run_gpu_arm(args):
                 tal = chem.chem_tally(ctx, 7, 9)
                 e2e_t.append(time.perf_counter() - t0)
                 e2e_ss += tal["species_steps"]
+            # untimed trajectories on further seeds for the G comparison of the two modes
+            for k in range(max(0, args.g_seeds - len(g_h2o2))):
+                chem.chem_reset(ctx, seed0 + 2000 + k)
+                chem.chem_inject_pulse(ctx, pulse.types, pulse.xyz, pulse.t_arrival, pulse.energy_eV)
+                chem.chem_run_until(ctx, wl.t_end)
+                tal = chem.chem_tally(ctx, 7, 9)
+                g_h2o2.append(tal["G"][W.H2O2]); g_oh.append(tal["G"][W.OH]); g_e.append(tal["G"][W.E_AQ])
             # profiled trajectories: CUDA events around every phase on the library's stream
             prof_times, prof_ss, stp0, stp1 = [], 0, st1, st1
             if not args.no_phase_events:
@@ -542,7 +549,8 @@ def run_gpu_arm(args):
                                         "e_aq": float(np.mean(f["G_e"]))}}
         line["speedup_fp32l_over_fp64"] = value / v64
         g32, g64 = np.array(r["G_H2O2"]), np.array(f["G_H2O2"])
-        line["G_H2O2_match"] = {"fp32l_mean": float(g32.mean()), "fp64_mean": float(g64.mean()),
+        line["G_H2O2_match"] = {"seeds": [len(g32), len(g64)],
+                                "fp32l_mean": float(g32.mean()), "fp64_mean": float(g64.mean()),
                                 "rel_diff": float(abs(g32.mean() - g64.mean()) / g64.mean()),
                                 "sigma_rel": float(math.sqrt(g32.var(ddof=1) / len(g32) + g64.var(ddof=1) / len(g64)) / g64.mean())
                                 if len(g32) > 1 and len(g64) > 1 else None}
@@ -1074,6 +1082,9 @@ def main():
     ap.add_argument("--no-phase-events", action="store_true")
     ap.add_argument("--profiled", type=int, default=3,
                     help="trajectories with phase events after the timed ones (phase times, rooflines)")
+    ap.add_argument("--g-seeds", type=int, default=32,
+                    help="seeds per precision for the FP32-local / FP64 G comparison (untimed "
+                         "trajectories on other seeds make up the difference)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--autotune-ms", type=float, default=1500.0)
     ap.add_argument("--tuned", default="",
