@@ -61,15 +61,20 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_tracks_1e6_fp32l.json")
 def sources_digest():
     """SHA-256 over the device-code sources and the C header, to tell whether a recorded
     ncu measurement still describes the kernels that run (chem_api.cu holds host code
-    only and is left out)."""
+    only and is left out). Comments and white space are dropped first: editing them
+    changes no kernel."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2509_03313_gb300", "csrc")
     files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
                    if f.endswith((".cu", ".cuh", ".h")) and f != "chem_api.cu")
     for f in files + [os.path.join(ROOT, "include", "chem.h")]:
-        with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode() + b"\0" + fh.read())
+        with open(f, encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(os.path.basename(f).encode() + b"\0" + " ".join(text.split()).encode())
     return h.hexdigest()
 
 

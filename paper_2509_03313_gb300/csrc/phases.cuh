@@ -981,11 +981,13 @@ __device__ __forceinline__ bool accept_f64(double d0sq, double d1sq, int r, cons
 constexpr int TPS_UNROLL = 4;
 
 // ---- one thread per home species
-// One thread per home species: each lane takes one home species
-// (warps take 32 consecutive sorted slots by work stealing) and walks its own cell's later
-// slots and its 13 forward cells. Lanes of one cell walk the same ranges in step, so their
-// neighbour loads are broadcasts; the loops are warp-uniform (trip count = the longest
-// range among the lanes) and pairs inside the cutoff go to the warp's pair queue.
+// Each lane takes one home species (warps take 32 consecutive sorted slots by work
+// stealing), keeps the forward cells its largest cutoff can reach (a 13-bit mask from
+// per-axis face gaps), collects their non-empty ranges after its own cell's later slots,
+// and walks them one range at a time, TPS_UNROLL neighbours per iteration. Lanes of one
+// cell walk the same ranges in step, so their neighbour loads are broadcasts; the loops
+// are warp-uniform (trip count = the longest walk among the lanes) and pairs inside the
+// cutoff go to the warp's pair queue.
 
 template <bool F32L>
 struct TpsQueue;
