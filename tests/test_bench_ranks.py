@@ -160,3 +160,25 @@ def test_recorded_traffic_only_while_the_sources_match(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.json"))
     assert bench.recorded_traffic("k_search_tps") is None
 
+
+
+def test_sources_digest_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    """The traffic record stays valid across comment and layout edits of the device
+    sources and is dropped by any change to the code itself."""
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(ROOT, "paper_2509_03313_gb300", "csrc"), root / "paper_2509_03313_gb300" / "csrc")
+    shutil.copytree(os.path.join(ROOT, "include"), root / "include")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    base = bench.sources_digest()
+    f = root / "paper_2509_03313_gb300" / "csrc" / "phases.cuh"
+    text = f.read_text()
+    f.write_text("// a new comment line\n/* and a block\n   comment */\n" + text.replace("\n\n", "\n\n\n", 3))
+    assert bench.sources_digest() == base
+    f.write_text(text.replace("constexpr int TPS_UNROLL = 4;", "constexpr int TPS_UNROLL = 2;"))
+    assert bench.sources_digest() != base
+    f.write_text(text)
+    (root / "paper_2509_03313_gb300" / "csrc" / "chem_api.cu").write_text("// host code only\n")
+    assert bench.sources_digest() == base  # host-only unit left out
